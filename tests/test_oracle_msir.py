@@ -1,0 +1,189 @@
+"""Pins for the oracle's stage controller and whole MSIR runs (Algorithm 4)."""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import formats as F
+from oracle import msir as M
+from oracle import metrics as X
+from synth import randsvd_system
+
+HSD = (F.FP16, F.FP32, F.FP64)
+SDQ = (F.FP32, F.FP64, F.DD)
+
+
+def _ctl(n=100, **kw):
+    return M.Controller(n, F.FP32, M.Params(**kw))
+
+
+def test_geometric_convergence_is_detected():
+    c = _ctl()
+    acts = []
+    for i, delta in enumerate([1e-2, 1e-4, 1e-6, 1e-8]):
+        a, reset, z, v, phi = c.step(1.0, delta, 1.0, F.FP32, nbe_new=1e-8 if i == 3 else 1e-3)
+        acts.append(a)
+    assert acts == ["continue", "continue", "continue", "converged"]
+    assert c.phi0 == pytest.approx(1e-2)
+
+
+def test_slow_ratio_switches_after_two_steps():
+    # Sec. 2.1.1: the ratio test needs two corrections, so a stage runs >= 2 steps
+    c = _ctl()
+    a1 = c.step(1.0, 1e-1, 1.0, F.FP32, 1e-3)[0]
+    a2, reset, z, v, phi = c.step(1.0, 0.6e-1, 1.0, F.FP32, 1e-3)
+    assert (a1, a2) == ("continue", "switch")
+    assert v == pytest.approx(0.6)
+    assert phi == pytest.approx(0.06 / 0.4) and reset  # phi > phi_0 = 0.1: x reset to x_0
+    assert c.advance() is False and c.alg == M.SGMRES and c.it == 0 and c.rho_max == 0.0
+
+
+def test_ratio_exactly_at_threshold_switches():
+    # Sec. 2.1.1 lists the criterion as ||d_{i+1}|| / ||d_i|| >= rho_thresh
+    c = _ctl()
+    c.step(1.0, 2.0 ** -4, 1.0, F.FP32, 1e-3)
+    a, reset, z, v, phi = c.step(1.0, 2.0 ** -5, 1.0, F.FP32, 1e-3)
+    assert v == 0.5 and a == "switch"
+
+
+def test_divergence_resets_x():
+    c = _ctl()
+    c.step(1.0, 1e-2, 1.0, F.FP32, 1e-3)
+    a, reset, z, v, phi = c.step(1.0, 3e-2, 1.0, F.FP32, 1e-3)
+    assert a == "switch" and v == pytest.approx(3.0) and phi == math.inf and reset
+
+
+def test_imax_and_small_correction_triggers():
+    c = _ctl(i_max=3)
+    acts = [c.step(1.0, 0.4 ** k, 1.0, F.FP32, 1e-3)[0] for k in range(1, 4)]
+    assert acts == ["continue", "continue", "switch"]
+    c = _ctl()
+    a = c.step(1.0, 1e-9, 1.0, F.FP32, 1e-3)[0]  # z = 1e-9 <= u but nbe too large
+    assert a == "switch"
+
+
+def test_kmax_switches_gmres_stage_immediately():
+    c = _ctl(n=100)
+    c.advance()
+    a = c.step(1.0, 1e-1, 1.0, F.FP32, 1e-3, kg=10)[0]  # k_max = 0.1 n = 10
+    assert a == "switch"
+    c2 = _ctl(n=100)
+    a = c2.step(1.0, 1e-1, 1.0, F.FP32, 1e-3, kg=10)[0]  # SIR ignores k
+    assert a == "continue"
+    c3 = _ctl(n=66)  # k_max = 6.6: 7 iterations (the cap) trigger, 6 do not
+    c3.advance()
+    assert c3.step(1.0, 1e-1, 1.0, F.FP32, 1e-3, kg=6)[0] == "continue"
+    assert c3.step(1.0, 1e-2, 1.0, F.FP32, 1e-3, kg=7)[0] == "switch"
+
+
+def test_stage_ladder():
+    c = _ctl()
+    assert [c.advance() for _ in range(3)] == [False, False, True]
+    assert c.alg == M.SIR
+
+
+def _stages(spec):
+    out = []
+    uf = 0
+    for level in spec:
+        uf += 1
+        sir, *gm = level
+        out.append(M.Stage(uf, 0, 0, M.SIR, steps=sir))
+        for alg, its in zip((M.SGMRES, M.GMRES), gm):
+            out.append(M.Stage(uf, 0, 0, alg, steps=len(its), gmres_iters=list(its)))
+    return out
+
+
+def test_notation_matches_paper_tables():
+    # Table 6 (mode 2, half/single/double), kappa_2 = 1e9 and 1e7 rows
+    assert M.stage_string(_stages([(2, (5, 9), (10,)), (2, (2, 2, 2), (2, 3, 3))])) == \
+        "2, (5,9), (10); 2, (2,2,2), (2,3,3)"
+    assert M.stage_string(_stages([(2, (5, 10), (10,))])) == "2, (5,10), (10)"
+    # Table 9 (mode 3, half/single/double), kappa_2 = 1e5 row
+    assert M.stage_string(_stages([(0, (10,), (10,)), (3,)])) == "0, (10), (10); 3"
+
+
+def _run(n, kappa, triple, seed=0, graded=False, **kw):
+    A, B, _ = randsvd_system(n, kappa, seed, graded=graded)
+    res = M.msir(A, B[:, 0], triple, M.Params(**kw))
+    u0 = triple[1]
+    A_u = F.fl(A, u0).astype(np.float64)
+    b_u = F.fl(B[:, 0], u0).astype(np.float64)
+    xr = X.x_ref(A_u, b_u)
+    return res, A_u, b_u, xr
+
+
+@pytest.mark.parametrize("kappa", [1e1, 1e2, 1e3])
+def test_converges_below_sir_limit_half_single_double(kappa):
+    # Table 4: SIR converges for kappa_inf < 2e3 at (half, single, double)
+    res, A_u, b_u, xr = _run(80, kappa, HSD, nb=32)
+    assert res.cged
+    u0 = F.u_of(F.FP32)
+    assert res.nbe <= 2 * u0
+    assert X.nbe(A_u, b_u, res.x) <= 2 * u0
+    assert X.ferr(res.x, xr) <= 50 * u0
+    assert res.stages[0].alg == M.SIR and res.stages[0].steps >= 1
+
+
+def test_fixed_precision_double_reduces_to_textbook_ir():
+    res, A_u, b_u, xr = _run(64, 1e4, (F.FP64, F.FP64, F.DD), nb=16)
+    assert res.cged and M.stage_string(res.stages) in ("1", "2")
+    assert X.ferr(res.x, xr) <= 1e3 * F.u_of(F.FP64)
+
+
+def test_single_double_quad_ill_conditioned_converges():
+    res, A_u, b_u, xr = _run(100, 1e10, SDQ, nb=32)
+    assert res.cged
+    assert X.nbe(A_u, b_u, res.x) <= 2 * F.u_of(F.FP64)
+    assert X.ferr(res.x, xr) <= 1e-12
+
+
+def test_half_precision_inf_case_matches_paper_pattern():
+    """Sec. 3.1.2 / Table 9: for kappa_2 >= 1e5 at (half, single, double),
+    the first SIR correction overflows half precision (||A^-1||_2 = kappa
+    exceeds 65504 since ||A||_2 = 1), so MSIR records 0 SIR steps; with
+    k_max = 0.1 n = 10 both GMRES stages stop at the cap and u_f is raised.
+    The paper prints '0, (10), (10); 3' for this row (soft: other RNG)."""
+    res, A_u, b_u, xr = _run(100, 1e5, HSD, nb=32)
+    s = M.stage_string(res.stages)
+    assert s.startswith("0, (10), (10); ")
+    assert res.stages[-1].uf == F.FP32 and res.stages[-1].u == F.FP32
+    assert res.cged and res.nbe <= 2 * F.u_of(F.FP32)
+
+
+def test_escalation_ladder_follows_section2_example():
+    # Sec. 2: (half,single,double) -> (single,single,double) -> (double,double,quad)
+    res, *_ = _run(60, 1e12, HSD, nb=16, i_max=3)
+    seen = []
+    for st in res.stages:
+        t = (st.uf, st.u, st.ur)
+        if not seen or seen[-1] != t:
+            seen.append(t)
+    assert seen[0] == (F.FP16, F.FP32, F.FP64)
+    if len(seen) > 1:
+        assert seen[1] == (F.FP32, F.FP32, F.FP64)
+    if len(seen) > 2:
+        assert seen[2] == (F.FP64, F.FP64, F.DD)
+
+
+def test_brute_force_tiny_systems():
+    rng = np.random.default_rng(21)
+    for n in range(1, 8):
+        A = rng.standard_normal((n, n)) + 3 * np.eye(n)
+        b = rng.standard_normal(n)
+        res = M.msir(A, b, HSD, M.Params(nb=2))
+        A_u = F.fl(A, F.FP32).astype(np.float64)
+        b_u = F.fl(b, F.FP32).astype(np.float64)
+        x_exact = np.linalg.solve(A_u, b_u)
+        assert res.cged
+        assert np.max(np.abs(res.x - x_exact)) <= 1e-5 * np.max(np.abs(x_exact))
+
+
+def test_zero_rhs_and_exact_start():
+    A = np.eye(5) * 2.0
+    res = M.msir(A, np.zeros(5), HSD)
+    assert res.cged and np.all(res.x == 0)
+    res = M.msir(A, np.ones(5), HSD)  # x0 = 0.5 exactly: residual 0
+    assert res.cged and np.all(res.x == 0.5)
