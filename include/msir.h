@@ -1,0 +1,244 @@
+/*
+ * msir.h -- C interface of libmsir, a GB300 (sm_103a) implementation of
+ * multistage mixed-precision iterative refinement (MSIR) for dense A x = b
+ * (Oktay & Carson, "Multistage Mixed Precision Iterative Refinement").
+ *
+ * The method (Algorithm 4 of the paper): factor A = LU by Gaussian
+ * elimination with partial pivoting in the factorisation precision u_f;
+ * solve A x_0 = b with the factors in u_f; then refine.  Each step computes
+ * r = b - A x in the residual precision u_r, scales it by ||r||_inf
+ * (Sec. 2.1.2) and solves the correction equation either with the factors
+ * (SIR, Algorithm 1), by GMRES preconditioned with the factors whose
+ * operator is applied in the working precision u (SGMRES-IR, Algorithm 3),
+ * or by the same GMRES with the operator applied in u^2 (GMRES-IR,
+ * Algorithm 2).  The stopping criteria of Sec. 2.1.1 switch SIR ->
+ * SGMRES-IR -> GMRES-IR; after GMRES-IR the factorisation precision is
+ * raised (half/bfloat16 -> single -> double), the matrix refactored and SIR
+ * restarts.  The paper's quad residual precision is stood in for by
+ * double-double (MSIR_DD).
+ *
+ * Conventions for every entry point
+ *   - Matrices passed in are fp64, column-major with a leading dimension
+ *     (LAPACK style).  Vectors are fp64.  "_dev" pointers are CUDA device
+ *     pointers on the context's device; "_host" pointers are host memory.
+ *   - The caller owns every buffer it passes; the library never frees them
+ *     and keeps no pointer to them after the call returns.  The library owns
+ *     contexts, factor objects and servers; each has a destroy call.
+ *   - Work is ordered on the context's CUDA stream.  Calls that return a
+ *     report synchronise that stream before returning.
+ *   - No call throws across this interface.  Every call returns an
+ *     msir_status; on error nothing is written to the caller's outputs
+ *     except where a call says otherwise.
+ *   - One context may be used by one host thread at a time.  A server is
+ *     internally synchronised and may be called from several threads.
+ */
+#ifndef MSIR_H
+#define MSIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Number formats.  Unit roundoffs (Table 3 of the paper, bf16 and dd added):
+ * bf16 2^-8, fp16 2^-11, fp32 2^-24, fp64 2^-53, dd 2^-106. */
+typedef enum {
+  MSIR_BF16 = 1,
+  MSIR_FP16 = 2,
+  MSIR_FP32 = 3,
+  MSIR_FP64 = 4,
+  MSIR_DD = 5
+} msir_prec;
+
+/* Initial precisions (u_f, u, u_r) of Algorithm 4, as msir_prec values.
+ * Requirements (Sec. 1 assumes u_f >= u >= u_r; Sec. 2 enforces u_r <= u^2):
+ * u in {FP32, FP64}; u_r = FP64 when u = FP32 and DD when u = FP64;
+ * u_f in {BF16, FP16, FP32, FP64} and not more precise than u. */
+typedef struct {
+  int uf;
+  int u;
+  int ur;
+} msir_triple;
+
+/* Convergence test applied after every refinement step (Sec. 2.1.1). */
+typedef enum {
+  /* 0 <= phi <= gamma*u0 and nbe(x_{i+1}) <= 2*u0 (default) */
+  MSIR_CONV_COMBINED = 0,
+  /* 0 <= phi <= gamma*u0 only (Eq. (1) estimate, Algorithm 4 literally) */
+  MSIR_CONV_EST = 1
+} msir_conv;
+
+typedef enum {
+  MSIR_OK = 0,
+  MSIR_NOT_CONVERGED = 1,   /* x holds the iterate of smallest nbe */
+  MSIR_ERR_INVALID = -1,    /* bad argument (sizes, triple, params) */
+  MSIR_ERR_NOMEM = -2,      /* device allocation failed */
+  MSIR_ERR_SINGULAR = -3,   /* exact zero pivot with u_f = fp64 */
+  MSIR_ERR_TIMEOUT = -4,    /* a device-side wait hit its deadline */
+  MSIR_ERR_CUDA = -5,       /* a CUDA runtime call failed */
+  MSIR_ERR_UNSUPPORTED = -6 /* device is not sm_103 or lacks a feature */
+} msir_status;
+
+/* Parameters of Algorithm 4.  msir_params_default() fills the paper's
+ * values: i_max = 10, rho_thresh = 0.5 (the "cautious" setting of
+ * Sec. 2.1.1), k_max = 0.1 n (Sec. 3), tau by u (1e-6 single, 1e-10
+ * double, Sec. 3), gamma = sqrt(n) (Algorithm 4). */
+typedef struct {
+  int i_max;            /* maximum steps of each variant (Sec. 2.1)          */
+  double rho_thresh;    /* ratio threshold of successive corrections          */
+  double kmax_frac;     /* k_max = kmax_frac * n GMRES iterations per step    */
+  double tau;           /* GMRES tolerance; <= 0 picks 1e-6 / 1e-10 by u      */
+  double gamma;         /* convergence factor; <= 0 picks sqrt(n)             */
+  int conv;             /* msir_conv                                          */
+  int nb;               /* panel width of the LU (numeric parameter); 0: default */
+  int nbo;              /* outer block width of the LU (multiple of nb); 0: default */
+  int allow_escalation; /* 0: stop after GMRES-IR instead of raising u_f      */
+} msir_params;
+
+#define MSIR_MAX_STAGES 24
+#define MSIR_MAX_STEPS 48
+
+typedef enum { MSIR_ALG_SIR = 0, MSIR_ALG_SGMRES = 1, MSIR_ALG_GMRES = 2 } msir_alg;
+
+/* One stage: a run of one variant at one precision triple. */
+typedef struct {
+  int uf, u, ur;       /* precisions in effect                              */
+  int alg;             /* msir_alg                                          */
+  int steps;           /* counted refinement steps of this stage            */
+  int nonfinite;       /* 1 if the stage ended on an Inf/NaN correction     */
+  int gmres_iters[MSIR_MAX_STEPS]; /* GMRES iterations per step (GMRES stages) */
+} msir_stage;
+
+/* Written by the library, owned by the caller. */
+typedef struct {
+  int status;            /* msir_status of this system                       */
+  int cged;              /* Algorithm 4's cged                               */
+  int n_stages;
+  int n_factorizations;
+  int scaled;            /* 1 if a squeezed (two-sided scaled) LU was used    */
+  int lu_info;           /* first zero pivot of the last LU (1-based), 0 none */
+  int nb, nbo;           /* LU blocking actually used                        */
+  int total_steps;       /* refinement steps of all stages                   */
+  int total_gmres_iters;
+  double nbe;            /* normwise backward error of x (infinity norms)    */
+  double phi;            /* last convergence estimate phi_i                  */
+  double t_factor_ms;    /* device time in LU factorisations                 */
+  double t_refine_ms;    /* device time in refinement                        */
+  msir_stage stage[MSIR_MAX_STAGES];
+} msir_report;
+
+typedef struct msir_ctx msir_ctx;
+typedef struct msir_factors msir_factors;
+typedef struct msir_server msir_server;
+
+/* Fills *p with the defaults listed above.  Returns MSIR_ERR_INVALID on NULL. */
+msir_status msir_params_default(msir_params* p);
+
+/* Creates a context on CUDA device `device` whose work is ordered on
+ * `cuda_stream` (a cudaStream_t; NULL = a stream the library creates).
+ * Fails with MSIR_ERR_UNSUPPORTED if the device is not compute capability
+ * 10.3.  The context owns a device workspace that grows on demand. */
+msir_status msir_create(msir_ctx** out, int device, void* cuda_stream);
+msir_status msir_destroy(msir_ctx* ctx);
+
+/* Factor the n x n matrix A (fp64, column-major, leading dimension lda,
+ * device memory) in precision uf: the working copy is A_u = fl_u(A) and the
+ * factors are those of fl_uf(A_u) by blocked right-looking GEPP (Algorithm 4,
+ * first step).  The factor object is owned by the library.  On success
+ * *info receives the first exactly-zero pivot (1-based) or 0, and
+ * *nonfinite 1 if L or U contain Inf or NaN (neither is an error here).
+ * u must be FP32 or FP64, uf one of BF16/FP16/FP32/FP64 not finer than u. */
+msir_status msir_factor(msir_ctx* ctx, int n, const double* A_dev, int lda, int u, int uf,
+                        const msir_params* params, msir_factors** out, int* info,
+                        int* nonfinite);
+msir_status msir_factors_destroy(msir_factors* f);
+
+/* Copies the packed factors of f to host memory: F_host (n*n doubles,
+ * row-major: strictly lower part = L without its unit diagonal, upper part
+ * = U, each value exactly the stored u_f value) and ipiv_host (n ints,
+ * 0-based LAPACK-style row interchanges: row j was swapped with ipiv[j] at
+ * step j).  Either pointer may be NULL. */
+msir_status msir_factors_export(msir_ctx* ctx, const msir_factors* f, double* F_host,
+                                int* ipiv_host);
+
+/* Applies M^{-1} = U^{-1} L^{-1} P of f to nrhs vectors: X = M^{-1} B, with
+ * the substitutions carried out in `arith` (FP32, FP64 or DD) and every
+ * computed component rounded to `store` (BF16/FP16/FP32/FP64; ignored for
+ * DD).  B_dev, X_dev: device, column-major n x nrhs with leading dimension
+ * ldb / ldx.  This is the correction solve of SIR (arith FP32, store u_f)
+ * and the preconditioner of SGMRES-IR / GMRES-IR (arith u or u^2). */
+msir_status msir_factors_apply(msir_ctx* ctx, const msir_factors* f, int nrhs,
+                               const double* B_dev, int ldb, double* X_dev, int ldx,
+                               int arith, int store);
+
+/* Residual of Algorithm 4 for one vector: r = b - A_u x in precision ur
+ * (FP64 or DD) with A_u = fl_u0(A), and s = ||r||_inf.  A_dev as in
+ * msir_factor; x_dev, b_dev: n doubles (b is rounded to u0 first, x is used
+ * as given).  r_dev: n doubles (FP64) or 2n doubles (DD: high words then low
+ * words).  *s_host receives ||r||_inf (fp64). */
+msir_status msir_residual(msir_ctx* ctx, int n, const double* A_dev, int lda, int u0,
+                          const double* x_dev, const double* b_dev, int ur, double* r_dev,
+                          double* s_host);
+
+/* Solves A X = B for nrhs right-hand sides with MSIR (Algorithm 4) from the
+ * initial precisions t.  A_dev: fp64 column-major n x n (lda >= n); B_dev,
+ * X_dev: fp64 column-major n x nrhs (ldb, ldx >= n); 1 <= nrhs <= 16.
+ * Each column runs its own stage controller (factors are shared per u_f).
+ * rep: nrhs reports (may be NULL).  Returns MSIR_OK if every column
+ * converged, MSIR_NOT_CONVERGED if some did not (their X columns hold the
+ * iterate of smallest nbe), or an error. */
+msir_status msir_solve(msir_ctx* ctx, int n, int nrhs, const double* A_dev, int lda,
+                       const double* B_dev, int ldb, double* X_dev, int ldx, msir_triple t,
+                       const msir_params* params, msir_report* rep);
+
+/* Same as msir_solve for one right-hand side with host buffers: A_host
+ * (column-major), b_host, x_host.  Copies in and out on the context stream. */
+msir_status msir_solve_host(msir_ctx* ctx, int n, const double* A_host, int lda,
+                            const double* b_host, double* x_host, msir_triple t,
+                            const msir_params* params, msir_report* rep);
+
+/* Solves `count` independent systems of possibly different sizes.  n[i],
+ * A_dev[i] (n[i] x n[i], column-major, lda = n[i]), b_dev[i], x_dev[i]
+ * (n[i] doubles) and t[i] are host arrays of device pointers / values;
+ * reps: count reports (may be NULL).  Systems are grouped and their
+ * refinement runs as persistent launches over groups of SMs.  Returns
+ * MSIR_OK if all converged, MSIR_NOT_CONVERGED if some did not. */
+msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n,
+                               const double* const* A_dev, const double* const* b_dev,
+                               double* const* x_dev, const msir_triple* t,
+                               const msir_params* params, msir_report* reps);
+
+/* Continuous-batching solve server on the context's device.
+ * hbm_budget_bytes: device memory the server may hold for admitted
+ * requests (0 = 90% of the free memory).  max_slots: requests in flight on
+ * the device at once.  A worker thread admits queued requests when their
+ * footprint (A in u, L/U in the largest u_f it may need, Krylov basis)
+ * fits the budget and a slot is free, and runs each on its own stream. */
+msir_status msir_server_create(msir_ctx* ctx, size_t hbm_budget_bytes, int max_slots,
+                               msir_server** out);
+
+/* Queues one request.  A_host (column-major, lda) and b_host are host
+ * memory, copied before the call returns.  *ticket receives an id. */
+msir_status msir_server_submit(msir_server* s, int n, const double* A_host, int lda,
+                               const double* b_host, msir_triple t, const msir_params* params,
+                               uint64_t* ticket);
+
+/* Non-blocking poll.  *state: 0 queued, 1 running, 2 done.  When done, x_host
+ * (n doubles, may be NULL) and *rep (may be NULL) are filled and the ticket
+ * is released; *latency_ms (may be NULL) receives submit-to-done wall time.
+ * MSIR_ERR_INVALID for an unknown ticket. */
+msir_status msir_server_poll(msir_server* s, uint64_t ticket, int* state, double* x_host,
+                             msir_report* rep, double* latency_ms);
+
+/* Stops the worker after the requests in flight finish; frees everything. */
+msir_status msir_server_destroy(msir_server* s);
+
+/* Short text for a status code (static storage). */
+const char* msir_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MSIR_H */

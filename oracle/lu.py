@@ -12,7 +12,8 @@ arithmetic precision T and whose matrix is stored in u_f between blocks
 
 * T = fp32 for u_f in {bf16, fp16, fp32}; T = fp64 for u_f = fp64.
 * The n x n matrix is stored as A_f = fl_f(A) (row-major, packed L\\U).
-* For each panel of nb columns starting at column k:
+* Two-level blocking (outer blocks of nbo columns split into panels of nb
+  columns; see ``lu_factor``).  For each panel of nb columns at column k:
   - the (n-k) x w panel is widened to T; for each column j: the pivot is
     the row with the largest |a_ij| (i >= j) in T; ties go to the smallest
     row index; NaN is never chosen unless every candidate is NaN;
@@ -36,7 +37,7 @@ with row j at step j.
 
 import numpy as np
 
-from .formats import FP64, fl, arith_dtype
+from .formats import BF16, FP16, FP32, FP64, fl, arith_dtype
 
 
 def _argmax_abs(col):
@@ -45,57 +46,114 @@ def _argmax_abs(col):
     return int(np.argmax(a))  # first occurrence -> smallest row on ties
 
 
-def lu_factor(A, fmt_f, nb=64):
+def default_blocking(fmt_f):
+    """Default (nb, nbo): inner panel width and outer block width.
+
+    The panel is held in the arithmetic precision while it is factored, so it
+    is narrower when that precision is fp64."""
+    if fmt_f in (BF16, FP16):
+        return 32, 256
+    if fmt_f == FP32:
+        return 32, 128
+    return 16, 64
+
+
+def _panel(F, kk, w, T, fmt_f, ipiv):
+    """Factor the (n-kk) x w panel at column kk in T; store fl_f.  Returns the
+    first zero-pivot column (1-based) or 0."""
+    info = 0
+    P = F[kk:, kk:kk + w].astype(T)
+    for j in range(w):
+        p = j + _argmax_abs(P[j:, j])
+        ipiv[kk + j] = kk + p
+        if p != j:
+            P[[j, p], :] = P[[p, j], :]
+        piv = P[j, j]
+        if piv != 0:
+            P[j + 1:, j] = P[j + 1:, j] / piv
+            if j + 1 < w:
+                prod = P[j + 1:, j:j + 1] * P[j:j + 1, j + 1:]
+                P[j + 1:, j + 1:] = P[j + 1:, j + 1:] - prod
+        elif info == 0:
+            info = kk + j + 1
+    F[kk:, kk:kk + w] = fl(P, fmt_f).astype(np.float64)
+    return info
+
+
+def _swap_cols(F, ipiv, r0, w, c0, c1):
+    """Apply the interchanges of rows r0..r0+w-1 to columns [c0, c1)."""
+    if c1 <= c0:
+        return
+    for j in range(r0, r0 + w):
+        p = ipiv[j]
+        if p != j:
+            F[[j, p], c0:c1] = F[[p, j], c0:c1]
+
+
+def _trsm(F, r0, w, c0, c1, T, fmt_f):
+    """X = L11^{-1} X for rows r0..r0+w-1, columns [c0, c1), in T; store fl_f."""
+    if c1 <= c0:
+        return
+    L11 = F[r0:r0 + w, r0:r0 + w].astype(T)
+    X = F[r0:r0 + w, c0:c1].astype(T)
+    for m in range(w - 1):
+        prod = L11[m + 1:, m:m + 1] * X[m:m + 1, :]
+        X[m + 1:, :] = X[m + 1:, :] - prod
+    F[r0:r0 + w, c0:c1] = fl(X, fmt_f).astype(np.float64)
+
+
+def _update(F, r0, w, c0, c1, fmt_f):
+    """A[r0+w:, c0:c1] <- fl_f(fl_T(A - L21 U12)), the sum over w in fp64."""
+    if c1 <= c0 or r0 + w >= F.shape[0]:
+        return
+    L21 = F[r0 + w:, r0:r0 + w]
+    U12 = F[r0:r0 + w, c0:c1]
+    upd = F[r0 + w:, c0:c1] - L21 @ U12
+    if fmt_f == FP64:
+        F[r0 + w:, c0:c1] = upd
+    else:
+        F[r0 + w:, c0:c1] = fl(upd.astype(np.float32), fmt_f).astype(np.float64)
+
+
+def lu_factor(A, fmt_f, nb=None, nbo=None):
     """Factor A (float32/float64 array of working-precision values).
+
+    Two-level right-looking blocking: outer blocks of nbo columns, each
+    factored as panels of nb columns (inner swaps, substitution and update
+    restricted to the outer block), then the outer block's interchanges are
+    applied to the other columns, U12 is formed by substitution with the
+    nbo x nbo unit lower block and the trailing matrix is updated with K =
+    nbo.  nbo = nb gives the one-level algorithm.
 
     Returns (F, ipiv, info): F float64 n x n holding the stored u_f values of
     L (strictly lower, unit diagonal implied) and U; ipiv int64; info = 1-based
     index of the first exactly-zero pivot, 0 if none."""
     A = np.asarray(A)
     n = A.shape[0]
+    dnb, dnbo = default_blocking(fmt_f)
+    nb = nb or dnb
+    nbo = nbo or nb * -(-dnbo // nb)
+    if nbo % nb:
+        raise ValueError("nbo must be a multiple of nb")
     T = arith_dtype(fmt_f)
     F = fl(A.astype(np.float64), fmt_f).astype(np.float64)
     ipiv = np.arange(n, dtype=np.int64)
     info = 0
     with np.errstate(all="ignore"):
-        for k in range(0, n, nb):
-            w = min(nb, n - k)
-            P = F[k:, k:k + w].astype(T)
-            for j in range(w):
-                p = j + _argmax_abs(P[j:, j])
-                ipiv[k + j] = k + p
-                if p != j:
-                    P[[j, p], :] = P[[p, j], :]
-                piv = P[j, j]
-                if piv != 0:
-                    P[j + 1:, j] = P[j + 1:, j] / piv
-                    if j + 1 < w:
-                        prod = P[j + 1:, j:j + 1] * P[j:j + 1, j + 1:]
-                        P[j + 1:, j + 1:] = P[j + 1:, j + 1:] - prod
-                elif info == 0:
-                    info = k + j + 1
-            F[k:, k:k + w] = fl(P, fmt_f).astype(np.float64)
-            # apply this panel's swaps to the columns left and right of it
-            for j in range(w):
-                p = ipiv[k + j]
-                if p != k + j:
-                    F[[k + j, p], :k] = F[[p, k + j], :k]
-                    F[[k + j, p], k + w:] = F[[p, k + j], k + w:]
-            if k + w < n:
-                L11 = F[k:k + w, k:k + w].astype(T)
-                X = F[k:k + w, k + w:].astype(T)
-                for m in range(w - 1):
-                    prod = L11[m + 1:, m:m + 1] * X[m:m + 1, :]
-                    X[m + 1:, :] = X[m + 1:, :] - prod
-                F[k:k + w, k + w:] = fl(X, fmt_f).astype(np.float64)
-                L21 = F[k + w:, k:k + w]
-                U12 = F[k:k + w, k + w:]
-                S = L21 @ U12
-                upd = F[k + w:, k + w:] - S
-                if fmt_f == FP64:
-                    F[k + w:, k + w:] = upd
-                else:
-                    F[k + w:, k + w:] = fl(upd.astype(np.float32), fmt_f).astype(np.float64)
+        for k in range(0, n, nbo):
+            W = min(nbo, n - k)
+            for kk in range(k, k + W, nb):
+                w = min(nb, k + W - kk)
+                i = _panel(F, kk, w, T, fmt_f, ipiv)
+                info = info or i
+                _swap_cols(F, ipiv, kk, w, k, kk)
+                _swap_cols(F, ipiv, kk, w, kk + w, k + W)
+                _trsm(F, kk, w, kk + w, k + W, T, fmt_f)
+                _update(F, kk, w, kk + w, k + W, fmt_f)
+            _swap_cols(F, ipiv, k, W, 0, k)
+            _swap_cols(F, ipiv, k, W, k + W, n)
+            _trsm(F, k, W, k + W, n, T, fmt_f)
+            _update(F, k, W, k + W, n, fmt_f)
     return F, ipiv, info
 
 

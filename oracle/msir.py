@@ -76,7 +76,8 @@ class Params:
     tau: float = 0.0          # <= 0: by u (R13)
     gamma: float = 0.0        # <= 0: sqrt(n)
     conv: int = CONV_COMBINED
-    nb: int = 64
+    nb: int = 0               # <= 0: default for u_f (lu.default_blocking)
+    nbo: int = 0
     allow_escalation: bool = True
 
 
@@ -119,18 +120,18 @@ class Result:
     history: list
 
 
-def factorize(A_u, fmt_f, nb):
+def factorize(A_u, fmt_f, nb=0, nbo=0):
     """LU in u_f with the factor check and one squeezed retry (R10).
 
     Returns (Factorization or None, scaled_flag)."""
-    F, ipiv, info = lu_mod.lu_factor(A_u, fmt_f, nb)
+    F, ipiv, info = lu_mod.lu_factor(A_u, fmt_f, nb or None, nbo or None)
     if lu_mod.factors_finite(F) and info == 0:
         return Factorization(fmt_f, F, ipiv, lu_mod.ipiv_to_perm(ipiv), info), False
     if fmt_f == FP64:
         return None, False
     R, S, mu = sq_mod.scalings(A_u, fmt_f)
     B = sq_mod.scaled_matrix(A_u, R, S, mu)
-    F, ipiv, info = lu_mod.lu_factor(B.astype(np.float32), fmt_f, nb)
+    F, ipiv, info = lu_mod.lu_factor(B.astype(np.float32), fmt_f, nb or None, nbo or None)
     if lu_mod.factors_finite(F) and info == 0:
         return Factorization(fmt_f, F, ipiv, lu_mod.ipiv_to_perm(ipiv), info, R, S, mu), True
     return None, True
@@ -255,7 +256,7 @@ def msir(A_in, b_in, triple, params=None, x_ref=None):
         nonlocal nfact
         while fmt is not None:
             nfact += 1
-            fac, sc = factorize(A_u.astype(arith_dtype(u0)), fmt, p.nb)
+            fac, sc = factorize(A_u.astype(arith_dtype(u0)), fmt, p.nb, p.nbo)
             scaled_flags.append(sc)
             if fac is not None:
                 return fac

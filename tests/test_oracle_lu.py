@@ -24,14 +24,14 @@ def _exact_lu_matrix(n, seed, perm=None):
 
 
 @pytest.mark.parametrize("fmt", [F.FP16, F.BF16, F.FP32, F.FP64])
-@pytest.mark.parametrize("nb", [1, 2, 3, 8])
-def test_exactly_representable_lu_is_recovered(fmt, nb):
+@pytest.mark.parametrize("nb,nbo", [(1, 1), (2, 2), (3, 3), (8, 8), (2, 4), (2, 6), (3, 6)])
+def test_exactly_representable_lu_is_recovered(fmt, nb, nbo):
     n = 8
     A, Lm, U = _exact_lu_matrix(n, seed=nb + 10 * fmt)
     if fmt == F.BF16:  # keep every product inside 8 significant bits
         A, Lm, U = _exact_lu_matrix(n, seed=1)
         assert np.array_equal(F.flbf16(A.astype(np.float32)), A.astype(np.float32))
-    Fm, ipiv, info = L.lu_factor(A.astype(np.float32), fmt, nb)
+    Fm, ipiv, info = L.lu_factor(A.astype(np.float32), fmt, nb, nbo)
     assert info == 0
     assert np.array_equal(ipiv, np.arange(n))
     assert np.array_equal(np.tril(Fm, -1), np.tril(Lm, -1))
@@ -43,7 +43,7 @@ def test_permuted_exact_lu_recovers_permutation():
     perm = np.array([3, 0, 6, 1, 5, 2, 4])
     A, Lm, U = _exact_lu_matrix(n, seed=3, perm=perm)
     assert np.array_equal(A[perm], Lm @ U)
-    Fm, ipiv, info = L.lu_factor(A.astype(np.float32), F.FP16, 3)
+    Fm, ipiv, info = L.lu_factor(A.astype(np.float32), F.FP16, 2, 4)
     got = L.ipiv_to_perm(ipiv)
     assert np.array_equal(got, perm)
     assert np.array_equal(np.triu(Fm), U)
@@ -62,25 +62,26 @@ def test_ties_go_to_smallest_row_and_zero_pivot_info():
     assert ipiv[0] == 1  # NaN never chosen while a number is available
 
 
-@pytest.mark.parametrize("nb", [7, 32, 64])
-def test_fp64_matches_lapack_getrf(nb):
+@pytest.mark.parametrize("nb,nbo", [(7, 7), (32, 32), (64, 64), (8, 32), (16, 64)])
+def test_fp64_matches_lapack_getrf(nb, nbo):
     rng = np.random.default_rng(11)
     n = 96
     A = rng.standard_normal((n, n))
-    Fm, ipiv, info = L.lu_factor(A, F.FP64, nb)
+    Fm, ipiv, info = L.lu_factor(A, F.FP64, nb, nbo)
     lu, piv = sla.lu_factor(A)
     assert info == 0
     assert np.array_equal(ipiv, piv)
     assert np.max(np.abs(Fm - lu)) <= 1e-12 * np.max(np.abs(lu))
 
 
-@pytest.mark.parametrize("fmt,n,nb", [(F.FP16, 150, 64), (F.BF16, 150, 32), (F.FP16, 200, 200),
-                                      (F.FP32, 130, 64)])
-def test_backward_error_bound_and_multiplier_bound(fmt, n, nb):
+@pytest.mark.parametrize("fmt,n,nb,nbo", [(F.FP16, 150, 64, 64), (F.BF16, 150, 32, 32),
+                                          (F.FP16, 200, 200, 200), (F.FP32, 130, 64, 64),
+                                          (F.FP16, 300, 32, 128), (F.BF16, 260, 16, 64)])
+def test_backward_error_bound_and_multiplier_bound(fmt, n, nb, nbo):
     """|P A_f - L U| <= c (ceil(n/nb) + 2) u_f |L||U| elementwise, |l_ij| <= 1."""
     A, _, _ = randsvd_system(n, 1e3, seed=5)
     A32 = A.astype(np.float32)
-    Fm, ipiv, info = L.lu_factor(A32, fmt, nb)
+    Fm, ipiv, info = L.lu_factor(A32, fmt, nb, nbo)
     assert info == 0
     perm = L.ipiv_to_perm(ipiv)
     Lm, U = L.unpack(Fm)
