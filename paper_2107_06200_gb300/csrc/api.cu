@@ -1,0 +1,1363 @@
+// Host side of libmsir: the C interface declared in include/msir.h.
+//
+// A *slot* is one CUDA stream with a device workspace; it runs one system
+// at a time through the steps of Algorithm 4 that need the host:
+//   ingest -> LU in u_f (retried with the squeezing scaling, or u_f raised,
+//   when the factors hold Inf/NaN or a zero pivot, Sec. 2.1.2) -> one
+//   persistent refinement launch -> [if it asks for a finer u_f: LU at the
+//   next precision -> refinement launch again] -> copy x out.
+// Each step is enqueued asynchronously and followed by an event; a runner
+// polls the events of all slots, so several systems overlap on the device.
+// msir_solve uses one slot, msir_solve_batched several, and the server a
+// worker thread that admits queued requests into free slots (continuous
+// batching).
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "../../include/msir.h"
+#include "ingest.h"
+#include "kernels.h"
+#include "refine.h"
+
+using namespace msir;
+
+// ------------------------------------------------------------ utilities
+
+static int elem_size(int fmt) {
+  switch (fmt) {
+    case MSIR_BF16:
+    case MSIR_FP16: return 2;
+    case MSIR_FP32: return 4;
+    default: return 8;
+  }
+}
+static double unit_roundoff_h(int f) {
+  switch (f) {
+    case MSIR_BF16: return std::ldexp(1.0, -8);
+    case MSIR_FP16: return std::ldexp(1.0, -11);
+    case MSIR_FP32: return std::ldexp(1.0, -24);
+    case MSIR_FP64: return std::ldexp(1.0, -53);
+    default: return std::ldexp(1.0, -106);
+  }
+}
+static int next_uf(int f) {
+  if (f == MSIR_BF16 || f == MSIR_FP16) return MSIR_FP32;
+  if (f == MSIR_FP32) return MSIR_FP64;
+  return 0;
+}
+static int square_of_h(int u) { return u == MSIR_FP32 ? MSIR_FP64 : MSIR_DD; }
+static double xmax_of(int f) {
+  switch (f) {
+    case MSIR_FP16: return 65504.0;
+    case MSIR_BF16: return 3.3895313892515355e38;
+    case MSIR_FP32: return 3.4028234663852886e38;
+    default: return 1.7976931348623157e308;
+  }
+}
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static msir_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return MSIR_OK;
+  if (e == cudaErrorMemoryAllocation) return MSIR_ERR_NOMEM;
+  return MSIR_ERR_CUDA;
+}
+#define CK(x)                                  \
+  do {                                         \
+    cudaError_t _e = (x);                      \
+    if (_e != cudaSuccess) return cuda_status(_e); \
+  } while (0)
+
+static bool valid_triple(msir_triple t) {
+  if (t.u != MSIR_FP32 && t.u != MSIR_FP64) return false;
+  if (t.ur != square_of_h(t.u)) return false;
+  if (t.uf < MSIR_BF16 || t.uf > MSIR_FP64) return false;
+  if (unit_roundoff_h(t.uf) < unit_roundoff_h(t.u)) return false;
+  return true;
+}
+
+static void default_blocking(int fmt, int* nb, int* nbo) {
+  if (fmt == MSIR_BF16 || fmt == MSIR_FP16) { *nb = 32; *nbo = 256; }
+  else if (fmt == MSIR_FP32) { *nb = 32; *nbo = 128; }
+  else { *nb = 16; *nbo = 64; }
+}
+
+// ------------------------------------------------------------ TMA maps
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+// 2-D map over a row-major 16-bit matrix: box of 64 columns x 128 rows,
+// 128-byte swizzle (the canonical K-major operand layout of tcgen05).
+static bool make_tmap(CUtensorMap* m, void* base, int fmt, uint64_t cols, uint64_t rows,
+                      uint64_t row_bytes) {
+  EncodeTiledFn fn = get_encode();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {row_bytes};
+  cuuint32_t box[2] = {64, 128};
+  cuuint32_t es[2] = {1, 1};
+  CUresult r = fn(m, fmt == MSIR_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
+                  2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------ context
+
+struct Slot;
+struct msir_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int num_sms = 0;
+  int max_dyn_smem = 0;
+  std::vector<Slot*> pool;  // slots kept across calls (streams, pinned buffers, workspaces)
+};
+
+struct Level {  // one factorisation of the current matrix
+  int fmt = 0;
+  bool valid = false, failed = false;
+  int scaled = 0;
+  int info = 0, nonfinite = 0;
+  int nb = 0, nbo = 0;
+  void* F = nullptr;
+  int* ipiv = nullptr;
+  int* perm = nullptr;
+  double* R = nullptr;
+  double* S = nullptr;
+  double mu = 1.0;
+};
+
+// Device workspace of one slot, sized for systems up to nmax.
+struct Workspace {
+  int nmax = 0, kcapmax = 0, G = 0;
+  char* base = nullptr;
+  size_t bytes = 0;
+  int ldu = 0;
+  void* Au = nullptr;
+  double* b_u = nullptr;
+  double* rowsum = nullptr;
+  double* rowmax = nullptr;
+  double* colmax = nullptr;
+  double* scal = nullptr;   // scalar outputs
+  void* Fbuf[3] = {nullptr, nullptr, nullptr};
+  int* ipiv[3] = {};
+  int* perm[3] = {};
+  double* R[3] = {};
+  double* S[3] = {};
+  void* Ut = nullptr;
+  int* map = nullptr;       // map_pos | map_val | map_cnt
+  int* iflags = nullptr;    // info, nonfinite, err
+  double *x, *xn, *x0, *xbest, *r_hi, *r_lo, *c_hi, *c_lo, *y_hi, *y_lo, *z_hi, *z_lo, *d, *w;
+  double* V = nullptr;
+  int ldv = 0;
+  double *H, *yv, *red, *hred, *hvec;
+  unsigned* flags = nullptr;
+  unsigned* bar = nullptr;
+  RefState* st = nullptr;
+  msir_report* rep = nullptr;
+  int* ident = nullptr;
+};
+
+static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_level, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    off = round_up(off, 256);
+    char* p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
+  };
+  const size_t ldu = round_up((size_t)n, 64);
+  w.ldu = (int)ldu;
+  w.Au = take(ldu * n * 8);
+  w.b_u = (double*)take(n * 8);
+  w.rowsum = (double*)take(n * 8);
+  w.rowmax = (double*)take(n * 8);
+  w.colmax = (double*)take(n * 8);
+  w.scal = (double*)take(16 * 8);
+  const size_t lvl_bytes[3] = {ldu * n * 4, ldu * n * 4, alloc_f64_level ? ldu * n * 8 : 0};
+  for (int l = 0; l < 3; ++l) {
+    w.Fbuf[l] = lvl_bytes[l] ? take(lvl_bytes[l]) : nullptr;
+    w.ipiv[l] = (int*)take(n * 4);
+    w.perm[l] = (int*)take(n * 4);
+    w.R[l] = (double*)take(n * 8);
+    w.S[l] = (double*)take(n * 8);
+  }
+  w.Ut = take((size_t)n * 256 * 2);
+  w.map = (int*)take((4 * 256 + 8) * 4);
+  w.iflags = (int*)take(16 * 4);
+  double** vecs[] = {&w.x, &w.xn, &w.x0, &w.xbest, &w.r_hi, &w.r_lo, &w.c_hi,
+                     &w.c_lo, &w.y_hi, &w.y_lo, &w.z_hi, &w.z_lo, &w.d, &w.w};
+  for (double** v : vecs) *v = (double*)take(n * 8);
+  w.ldv = (int)round_up((size_t)n, 32);
+  w.V = (double*)take((size_t)(kcap + 1) * w.ldv * 8);
+  w.H = (double*)take((size_t)(kcap + 1) * kcap * 8);
+  w.yv = (double*)take((size_t)(kcap + 1) * 8);
+  w.red = (double*)take((size_t)2 * G * kRedW * 8);
+  w.hred = (double*)take((size_t)G * (kcap + 1) * 8);
+  w.hvec = (double*)take((size_t)(kcap + 1) * 8);
+  w.flags = (unsigned*)take(((size_t)(n + kBlk - 1) / kBlk + 1) * 4);
+  w.bar = (unsigned*)take(64);
+  w.st = (RefState*)take(sizeof(RefState));
+  w.rep = (msir_report*)take(sizeof(msir_report));
+  w.ident = (int*)take(n * 4);
+  return off + 256;
+}
+
+static int kcap_of(int n, double kmax_frac) {
+  int k = (int)std::ceil(kmax_frac * n);
+  return std::max(1, std::min(k, kMaxKcap));
+}
+
+// grid of the refinement kernel for size n
+static int refine_grid(msir_ctx* ctx, int n, int share) {
+  const int nblk = (n + kBlk - 1) / kBlk;
+  int g = std::min(nblk, ctx->num_sms);
+  if (share > 1) g = std::max(1, std::min(g, ctx->num_sms / share));
+  return g;
+}
+
+static msir_status ws_alloc(Workspace& w, int nmax, int kcapmax, int G, cudaStream_t st) {
+  Workspace probe;
+  size_t bytes = ws_layout(probe, nmax, kcapmax, G, true, nullptr);
+  if (w.base && w.bytes >= bytes && w.nmax >= nmax && w.kcapmax >= kcapmax && w.G >= G) return MSIR_OK;
+  if (w.base) { cudaFreeAsync(w.base, st); w.base = nullptr; }
+  char* base = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&base, bytes, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  w = Workspace();
+  w.base = base;
+  w.bytes = bytes;
+  w.nmax = nmax;
+  w.kcapmax = kcapmax;
+  w.G = G;
+  ws_layout(w, nmax, kcapmax, G, true, base);
+  return MSIR_OK;
+}
+
+static void ws_free(Workspace& w, cudaStream_t st) {
+  if (w.base) cudaFreeAsync(w.base, st);
+  w = Workspace();
+}
+
+static size_t ws_bytes_for(int n, int kcap, int G) {
+  Workspace probe;
+  return ws_layout(probe, n, kcap, G, true, nullptr);
+}
+
+// ------------------------------------------------------------ LU driver
+
+// Enqueue the LU of fl_fmt(A_u) (optionally squeezed) into level slot l.
+// The host reads info / nonfinite after the stream reaches the end.
+static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l, int fmt, int nb,
+                              int nbo, bool squeeze, Level& L, cudaStream_t st) {
+  const int ldf = w.ldu;
+  L = Level();
+  L.fmt = fmt;
+  L.nb = nb;
+  L.nbo = nbo;
+  L.F = w.Fbuf[l];
+  L.ipiv = w.ipiv[l];
+  L.perm = w.perm[l];
+  if (!L.F) return MSIR_ERR_INVALID;
+  const double* R = nullptr;
+  const double* S = nullptr;
+  if (squeeze) {
+    CK(squeeze_scalings(w.Au, w.ldu, n, u0, w.rowmax, w.R[l], w.colmax, w.S[l], st));
+    R = w.R[l];
+    S = w.S[l];
+    L.R = w.R[l];
+    L.S = w.S[l];
+    L.mu = std::ldexp(1.0, (int)std::floor(std::log2(0.1 * xmax_of(fmt))));
+    L.scaled = 1;
+  }
+  CK(make_factor_matrix(w.Au, w.ldu, n, u0, fmt, L.F, ldf, R, S, L.mu, st));
+  CK(cudaMemsetAsync(w.iflags, 0, 16 * sizeof(int), st));
+  const bool tc = fmt == MSIR_FP16 || fmt == MSIR_BF16;
+  CUtensorMap tmA, tmB;
+  if (tc && n > nbo) {
+    if (!make_tmap(&tmA, L.F, fmt, (uint64_t)n, (uint64_t)n, (uint64_t)ldf * 2) ||
+        !make_tmap(&tmB, w.Ut, fmt, (uint64_t)nbo, (uint64_t)n, (uint64_t)nbo * 2))
+      return MSIR_ERR_UNSUPPORTED;
+  }
+  const int ts = fmt == MSIR_FP64 ? 8 : 4;
+  const size_t fixed = panel_smem_bytes(fmt, 0, nb, nbo);
+  const size_t budget = std::min<size_t>((size_t)ctx->max_dyn_smem, 220 * 1024);
+  const int Rmax = (int)((budget - fixed) / ((size_t)(nb + 1) * ts));
+  for (int k = 0; k < n; k += nbo) {
+    const int W = std::min(nbo, n - k);
+    const int m = n - k;
+    int C = (m + Rmax - 1) / Rmax;
+    if (C > 16) return MSIR_ERR_UNSUPPORTED;
+    C = std::max(C, std::min(8, (m + 191) / 192));
+    C = std::max(1, std::min(C, 16));
+    PanelArgs pa;
+    pa.A = L.F;
+    pa.lda = ldf;
+    pa.n = n;
+    pa.k = k;
+    pa.W = W;
+    pa.nb = nb;
+    pa.R_cap = (m + C - 1) / C;
+    pa.ipiv = L.ipiv;
+    pa.info = w.iflags + 0;
+    pa.nonfinite = w.iflags + 1;
+    pa.map_pos = w.map;
+    pa.map_val = w.map + 2 * nbo;
+    pa.map_cnt = w.map + 4 * nbo;
+    CK(launch_panel(fmt, pa, C, st));
+    const int nright = n - k - W;
+    if (k > 0 || nright > 0) {
+      SwapTrsmArgs sa;
+      sa.A = L.F;
+      sa.lda = ldf;
+      sa.n = n;
+      sa.k = k;
+      sa.W = W;
+      sa.map_pos = pa.map_pos;
+      sa.map_val = pa.map_val;
+      sa.map_cnt = pa.map_cnt;
+      sa.Ut = (tc && nright > 0) ? w.Ut : nullptr;
+      sa.ldut = nbo;
+      sa.nonfinite = w.iflags + 1;
+      const int tiles = (k + 31) / 32 + (nright + 31) / 32;
+      CK(launch_swap_trsm(fmt, sa, std::max(1, std::min(tiles, ctx->num_sms)), st));
+    }
+    if (nright > 0) {
+      if (tc) {
+        TcUpdateArgs ta;
+        ta.C = (char*)L.F + ((size_t)(k + W) * ldf + (k + W)) * 2;
+        ta.ldc = ldf;
+        ta.M = nright;
+        ta.N = nright;
+        ta.a_row0 = k + W;
+        ta.a_col0 = k;
+        ta.K = W;
+        ta.err = w.iflags + 2;
+        CK(launch_update_tc(fmt, &tmA, &tmB, ta, ctx->num_sms, st));
+      } else {
+        UpdateArgs ua;
+        ua.A = L.F;
+        ua.lda = ldf;
+        ua.n = n;
+        ua.k = k;
+        ua.W = W;
+        CK(launch_update_simt(fmt, ua, st));
+      }
+    }
+  }
+  CK(ipiv_to_perm(L.ipiv, n, L.perm, st));
+  return MSIR_OK;
+}
+
+// ------------------------------------------------------------ jobs/slots
+
+struct Job {
+  int n = 0;
+  const double* A = nullptr;  // device, column-major
+  int lda = 0;
+  const double* b = nullptr;  // device
+  double* x = nullptr;        // device output
+  msir_triple t{};
+  msir_params p{};
+  uint64_t matrix_id = 0;     // jobs with equal ids share the ingest and factors
+  msir_report rep{};
+  int status = MSIR_OK;
+  bool done = false;
+  std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+enum SlotStep { S_IDLE, S_FACTOR, S_REFINE, S_FINISH };
+
+struct Slot {
+  cudaStream_t st = nullptr;
+  Workspace w;
+  Job* job = nullptr;
+  SlotStep step = S_IDLE;
+  cudaEvent_t ev = nullptr, e0 = nullptr, e1 = nullptr;
+  int* h_flags = nullptr;     // pinned: info, nonfinite, err
+  RefState* h_state = nullptr;  // pinned
+  msir_report* h_rep = nullptr; // pinned
+  uint64_t loaded_id = 0;
+  int u0 = 0;
+  Level lv[3];
+  int cur = 0;                // level in use
+  int try_fmt = 0;            // format being factored
+  bool try_squeeze = false;
+  int try_level = 0;
+  int G = 1;
+  double normA = 0, normb = 0;
+  float t_factor = 0, t_refine = 0;
+  bool factoring_initial = true;
+  int nfact = 0;
+  RefState state{};
+};
+
+static int level_index(int fmt) {
+  if (fmt == MSIR_FP16 || fmt == MSIR_BF16) return 0;
+  if (fmt == MSIR_FP32) return 1;
+  return 2;
+}
+
+static msir_status slot_init(Slot& s, int device) {
+  CK(cudaSetDevice(device));
+  CK(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
+  CK(cudaEventCreate(&s.e0));
+  CK(cudaEventCreate(&s.e1));
+  CK(cudaMallocHost((void**)&s.h_flags, 16 * sizeof(int)));
+  CK(cudaMallocHost((void**)&s.h_state, sizeof(RefState)));
+  CK(cudaMallocHost((void**)&s.h_rep, sizeof(msir_report)));
+  return MSIR_OK;
+}
+
+static void slot_destroy(Slot& s) {
+  if (s.st) {
+    cudaStreamSynchronize(s.st);
+    ws_free(s.w, s.st);
+    cudaStreamSynchronize(s.st);
+    cudaStreamDestroy(s.st);
+  }
+  if (s.ev) cudaEventDestroy(s.ev);
+  if (s.e0) cudaEventDestroy(s.e0);
+  if (s.e1) cudaEventDestroy(s.e1);
+  if (s.h_flags) cudaFreeHost(s.h_flags);
+  if (s.h_state) cudaFreeHost(s.h_state);
+  if (s.h_rep) cudaFreeHost(s.h_rep);
+  s = Slot();
+}
+
+static msir_status pooled_slots(msir_ctx* ctx, int k, std::vector<Slot*>& out) {
+  while ((int)ctx->pool.size() < k) {
+    Slot* s = new Slot();
+    msir_status r = slot_init(*s, ctx->device);
+    if (r != MSIR_OK) {
+      slot_destroy(*s);
+      delete s;
+      return r;
+    }
+    ctx->pool.push_back(s);
+  }
+  out.assign(ctx->pool.begin(), ctx->pool.begin() + k);
+  return MSIR_OK;
+}
+
+static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
+  Job& j = *s.job;
+  Workspace& w = s.w;
+  Level& L = s.lv[s.cur];
+  memset(&a, 0, sizeof(a));
+  a.mode = mode;
+  a.n = j.n;
+  a.a_fmt = s.u0;
+  a.A = w.Au;
+  a.lda = w.ldu;
+  a.b = w.b_u;
+  a.LU = L.F;
+  a.ldf = w.ldu;
+  a.perm = L.perm;
+  a.Rsc = L.scaled ? L.R : nullptr;
+  a.Ssc = L.scaled ? L.S : nullptr;
+  a.mu = L.scaled ? L.mu : 1.0;
+  a.normA = s.normA;
+  a.normb = s.normb;
+  a.x = w.x; a.xn = w.xn; a.x0 = w.x0; a.xbest = w.xbest;
+  a.r_hi = w.r_hi; a.r_lo = w.r_lo; a.c_hi = w.c_hi; a.c_lo = w.c_lo;
+  a.y_hi = w.y_hi; a.y_lo = w.y_lo; a.z_hi = w.z_hi; a.z_lo = w.z_lo;
+  a.d = w.d; a.w = w.w; a.V = w.V; a.ldv = w.ldv;
+  a.H = w.H; a.yv = w.yv; a.red = w.red; a.hred = w.hred; a.hvec = w.hvec;
+  a.flags = w.flags; a.bar = w.bar; a.err = w.iflags + 2; a.st = w.st; a.rep = w.rep;
+  a.i_max = j.p.i_max;
+  a.rho_thresh = j.p.rho_thresh;
+  a.kmax = j.p.kmax_frac * j.n;
+  a.kcap = kcap_of(j.n, j.p.kmax_frac);
+  a.tau = j.p.tau;
+  a.gamma = j.p.gamma;
+  a.conv = j.p.conv;
+  a.allow_escalation = j.p.allow_escalation;
+  a.u0 = j.t.u;
+  (void)ctx;
+}
+
+// Enqueue one factorisation attempt of the slot's current job.
+static msir_status slot_enqueue_factor(msir_ctx* ctx, Slot& s, int fmt, bool squeeze) {
+  Job& j = *s.job;
+  int nb = j.p.nb, nbo = j.p.nbo;
+  int dnb, dnbo;
+  default_blocking(fmt, &dnb, &dnbo);
+  if (nb <= 0) nb = dnb;
+  if (nbo <= 0) nbo = dnbo;
+  const int nbmax = fmt == MSIR_FP64 ? 16 : 32;
+  if (nb > nbmax || nbo % nb != 0 || nbo > 256) return MSIR_ERR_INVALID;
+  if ((fmt == MSIR_FP16 || fmt == MSIR_BF16) && nbo % 64 != 0 && j.n > nbo) return MSIR_ERR_INVALID;
+  s.try_fmt = fmt;
+  s.try_squeeze = squeeze;
+  s.try_level = level_index(fmt);
+  s.nfact += squeeze ? 0 : 1;
+  CK(cudaEventRecord(s.e0, s.st));
+  msir_status r = enqueue_lu(ctx, s.w, j.n, s.u0, s.try_level, fmt, nb, nbo, squeeze, s.lv[s.try_level], s.st);
+  if (r != MSIR_OK) return r;
+  CK(cudaMemcpyAsync(s.h_flags, s.w.iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, s.st));
+  CK(cudaEventRecord(s.e1, s.st));
+  CK(cudaEventRecord(s.ev, s.st));
+  s.step = S_FACTOR;
+  return MSIR_OK;
+}
+
+static msir_status slot_enqueue_refine(msir_ctx* ctx, Slot& s) {
+  RefineArgs a;
+  fill_args(ctx, s, a, MODE_SOLVE);
+  CK(cudaMemcpyAsync(s.w.st, &s.state, sizeof(RefState), cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemsetAsync(s.w.bar, 0, 64, s.st));
+  CK(cudaEventRecord(s.e0, s.st));
+  CK(launch_refine(s.u0, s.lv[s.cur].fmt, a, s.G, s.st));
+  CK(cudaEventRecord(s.e1, s.st));
+  CK(cudaMemcpyAsync(s.h_state, s.w.st, sizeof(RefState), cudaMemcpyDeviceToHost, s.st));
+  CK(cudaMemcpyAsync(s.h_rep, s.w.rep, sizeof(msir_report), cudaMemcpyDeviceToHost, s.st));
+  CK(cudaMemcpyAsync(s.h_flags, s.w.iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, s.st));
+  CK(cudaEventRecord(s.ev, s.st));
+  s.step = S_REFINE;
+  return MSIR_OK;
+}
+
+static void slot_finish(Slot& s, int status) {
+  Job& j = *s.job;
+  j.status = status;
+  s.step = S_FINISH;
+  cudaMemcpyAsync(j.x, s.w.x, (size_t)j.n * sizeof(double), cudaMemcpyDeviceToDevice, s.st);
+  cudaEventRecord(s.ev, s.st);
+}
+
+// Start a job in a slot: ingest (unless the matrix is already loaded) and
+// the first factorisation.
+static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
+  s.job = job;
+  Job& j = *job;
+  s.u0 = j.t.u;
+  s.G = refine_grid(ctx, j.n, share);
+  const int kcap = kcap_of(j.n, j.p.kmax_frac);
+  msir_status r = ws_alloc(s.w, std::max(j.n, s.w.nmax), std::max(kcap, s.w.kcapmax),
+                           std::max(s.G, s.w.G), s.st);
+  if (r != MSIR_OK) return r;
+  s.t_factor = s.t_refine = 0;
+  s.nfact = 0;
+  memset(&j.rep, 0, sizeof(j.rep));
+  const bool same = j.matrix_id != 0 && j.matrix_id == s.loaded_id;
+  if (!same) {
+    for (auto& L : s.lv) L = Level();
+    CK(ingest_matrix(j.A, j.lda, j.n, s.u0, s.w.Au, s.w.ldu, s.st));
+    CK(row_stats(s.w.Au, s.w.ldu, j.n, s.u0, s.w.rowsum, nullptr, s.st));
+    CK(max_abs(s.w.rowsum, j.n, 0, s.w.scal + 0, s.st));
+    CK(iota(s.w.ident, j.n, s.st));
+    s.loaded_id = j.matrix_id;
+  }
+  CK(round_vec(j.b, j.n, s.u0, s.w.b_u, s.st));
+  CK(max_abs(s.w.b_u, j.n, 1, s.w.scal + 1, s.st));
+  double hs[2];
+  CK(cudaMemcpyAsync(hs, s.w.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s.st));
+  CK(cudaStreamSynchronize(s.st));
+  s.normA = hs[0];
+  s.normb = hs[1];
+  memset(&s.state, 0, sizeof(s.state));
+  s.state.phase = PH_START;
+  s.state.uf = j.t.uf;
+  s.state.u = j.t.u;
+  s.state.ur = j.t.ur;
+  s.state.delta_prev = INFINITY;
+  CK(cudaMemsetAsync(s.w.rep, 0, sizeof(msir_report), s.st));
+  CK(cudaMemsetAsync(s.w.flags, 0, ((size_t)(j.n + kBlk - 1) / kBlk + 1) * 4, s.st));
+  s.factoring_initial = true;
+  const int li = level_index(j.t.uf);
+  if (same && s.lv[li].valid && s.lv[li].fmt == j.t.uf) {
+    s.cur = li;
+    return slot_enqueue_refine(ctx, s);
+  }
+  return slot_enqueue_factor(ctx, s, j.t.uf, false);
+}
+
+static void fill_report(Slot& s) {
+  Job& j = *s.job;
+  msir_report& R = j.rep;
+  memcpy(&R, s.h_rep, sizeof(msir_report));
+  R.status = j.status;
+  R.cged = s.h_state->cged;
+  R.n_stages = std::min(s.h_state->nstages, MSIR_MAX_STAGES);
+  R.n_factorizations = s.nfact;
+  R.scaled = s.lv[s.cur].scaled;
+  R.lu_info = s.lv[s.cur].info;
+  R.nb = s.lv[s.cur].nb;
+  R.nbo = s.lv[s.cur].nbo;
+  R.total_steps = s.h_state->total_steps;
+  R.total_gmres_iters = s.h_state->total_gmres;
+  R.nbe = s.h_state->cged ? s.h_state->nbe : s.h_state->best_nbe;
+  R.phi = s.h_state->phi;
+  R.t_factor_ms = s.t_factor;
+  R.t_refine_ms = s.t_refine;
+}
+
+// Advance a slot whose event has completed.  Returns true when its job is done.
+static bool slot_advance(msir_ctx* ctx, Slot& s) {
+  Job& j = *s.job;
+  float ms = 0;
+  if (s.step == S_FACTOR) {
+    cudaEventElapsedTime(&ms, s.e0, s.e1);
+    s.t_factor += ms;
+    Level& L = s.lv[s.try_level];
+    L.info = s.h_flags[0];
+    L.nonfinite = s.h_flags[1];
+    const int err = s.h_flags[2];
+    if (err) { slot_finish(s, err); return false; }
+    const bool good = L.info == 0 && L.nonfinite == 0;
+    if (good) {
+      L.valid = true;
+      s.cur = s.try_level;
+      if (s.try_fmt != s.state.uf) {  // precision was raised
+        s.state.uf = s.try_fmt;
+        if (unit_roundoff_h(s.state.uf) < unit_roundoff_h(s.state.u)) s.state.u = s.state.uf;
+        if (unit_roundoff_h(s.state.ur) > unit_roundoff_h(s.state.u) * unit_roundoff_h(s.state.u))
+          s.state.ur = square_of_h(s.state.u);
+        if (!s.factoring_initial) s.state.phase = PH_ESCALATED;
+      }
+      msir_status r = slot_enqueue_refine(ctx, s);
+      if (r != MSIR_OK) slot_finish(s, r);
+      return false;
+    }
+    L.valid = false;
+    L.failed = true;
+    msir_status r;
+    if (!s.try_squeeze && s.try_fmt != MSIR_FP64) {
+      r = slot_enqueue_factor(ctx, s, s.try_fmt, true);
+    } else {
+      const int nx = next_uf(s.try_fmt);
+      if (!nx || !j.p.allow_escalation) {
+        slot_finish(s, s.try_fmt == MSIR_FP64 ? MSIR_ERR_SINGULAR : MSIR_NOT_CONVERGED);
+        return false;
+      }
+      r = slot_enqueue_factor(ctx, s, nx, false);
+    }
+    if (r != MSIR_OK) slot_finish(s, r);
+    return false;
+  }
+  if (s.step == S_REFINE) {
+    cudaEventElapsedTime(&ms, s.e0, s.e1);
+    s.t_refine += ms;
+    s.state = *s.h_state;
+    const int err = s.h_flags[2];
+    if (err || s.state.phase == PH_ERROR) { slot_finish(s, err ? err : MSIR_ERR_TIMEOUT); return false; }
+    if (s.state.phase == PH_NEED_ESC) {
+      const int nx = next_uf(s.state.uf);
+      if (!nx || !j.p.allow_escalation) {
+        // nothing left: return the best iterate
+        cudaMemcpyAsync(s.w.x, s.w.xbest, (size_t)j.n * 8, cudaMemcpyDeviceToDevice, s.st);
+        s.state.nbe = s.state.best_nbe;
+        *s.h_state = s.state;
+        slot_finish(s, MSIR_NOT_CONVERGED);
+        return false;
+      }
+      s.factoring_initial = false;
+      const int li = level_index(nx);
+      if (s.lv[li].valid && s.lv[li].fmt == nx && j.matrix_id != 0) {
+        s.cur = li;
+        s.state.uf = nx;
+        if (unit_roundoff_h(nx) < unit_roundoff_h(s.state.u)) s.state.u = nx;
+        if (unit_roundoff_h(s.state.ur) > unit_roundoff_h(s.state.u) * unit_roundoff_h(s.state.u))
+          s.state.ur = square_of_h(s.state.u);
+        s.state.phase = PH_ESCALATED;
+        msir_status r = slot_enqueue_refine(ctx, s);
+        if (r != MSIR_OK) slot_finish(s, r);
+        return false;
+      }
+      msir_status r = slot_enqueue_factor(ctx, s, nx, false);
+      if (r != MSIR_OK) slot_finish(s, r);
+      return false;
+    }
+    slot_finish(s, s.state.cged ? MSIR_OK : MSIR_NOT_CONVERGED);
+    return false;
+  }
+  if (s.step == S_FINISH) {
+    fill_report(s);
+    j.t_done = std::chrono::steady_clock::now();
+    j.done = true;
+    s.step = S_IDLE;
+    s.job = nullptr;
+    return true;
+  }
+  return false;
+}
+
+// Run jobs over nslots slots until all are done (used by solve and batched).
+static msir_status run_jobs(msir_ctx* ctx, std::vector<Job*>& jobs, std::vector<Slot*>& slots) {
+  size_t next = 0, done = 0;
+  const int share = (int)slots.size();
+  for (Slot* s : slots) {
+    s->loaded_id = 0;
+    if (next < jobs.size()) {
+      msir_status r = slot_start(ctx, *s, jobs[next++], share);
+      if (r != MSIR_OK) return r;
+    }
+  }
+  while (done < jobs.size()) {
+    bool progressed = false;
+    for (Slot* s : slots) {
+      if (!s->job) continue;
+      cudaError_t q = cudaEventQuery(s->ev);
+      if (q == cudaErrorNotReady) continue;
+      if (q != cudaSuccess) return cuda_status(q);
+      progressed = true;
+      if (slot_advance(ctx, *s)) {
+        ++done;
+        if (next < jobs.size()) {
+          msir_status r = slot_start(ctx, *s, jobs[next++], share);
+          if (r != MSIR_OK) return r;
+        }
+      }
+    }
+    if (!progressed) std::this_thread::yield();
+  }
+  return MSIR_OK;
+}
+
+// ------------------------------------------------------------ C ABI
+
+extern "C" {
+
+const char* msir_status_string(int s) {
+  switch (s) {
+    case MSIR_OK: return "ok";
+    case MSIR_NOT_CONVERGED: return "not converged";
+    case MSIR_ERR_INVALID: return "invalid argument";
+    case MSIR_ERR_NOMEM: return "out of device memory";
+    case MSIR_ERR_SINGULAR: return "singular (zero pivot in fp64)";
+    case MSIR_ERR_TIMEOUT: return "device wait timed out";
+    case MSIR_ERR_CUDA: return "CUDA error";
+    case MSIR_ERR_UNSUPPORTED: return "unsupported device or size";
+  }
+  return "unknown";
+}
+
+msir_status msir_params_default(msir_params* p) {
+  if (!p) return MSIR_ERR_INVALID;
+  p->i_max = 10;
+  p->rho_thresh = 0.5;
+  p->kmax_frac = 0.1;
+  p->tau = 0.0;
+  p->gamma = 0.0;
+  p->conv = MSIR_CONV_COMBINED;
+  p->nb = 0;
+  p->nbo = 0;
+  p->allow_escalation = 1;
+  return MSIR_OK;
+}
+
+static msir_params resolve_params(const msir_params* p) {
+  msir_params q;
+  msir_params_default(&q);
+  return p ? *p : q;
+}
+
+static bool valid_params(const msir_params& p) {
+  return p.i_max >= 1 && p.rho_thresh > 0 && p.kmax_frac > 0 &&
+         (p.conv == MSIR_CONV_COMBINED || p.conv == MSIR_CONV_EST) && p.nb >= 0 && p.nbo >= 0;
+}
+
+msir_status msir_create(msir_ctx** out, int device, void* stream) {
+  if (!out) return MSIR_ERR_INVALID;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return MSIR_ERR_CUDA;
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, device));
+  if (prop.major != 10 || prop.minor != 3) return MSIR_ERR_UNSUPPORTED;
+  CK(cudaSetDevice(device));
+  {
+    cudaMemPool_t mp;
+    if (cudaDeviceGetDefaultMemPool(&mp, device) == cudaSuccess) {
+      uint64_t thr = UINT64_MAX;
+      cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  msir_ctx* c = new msir_ctx();
+  c->device = device;
+  c->num_sms = prop.multiProcessorCount;
+  c->max_dyn_smem = (int)prop.sharedMemPerBlockOptin;
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete c;
+      return MSIR_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  *out = c;
+  return MSIR_OK;
+}
+
+msir_status msir_destroy(msir_ctx* ctx) {
+  if (!ctx) return MSIR_ERR_INVALID;
+  cudaSetDevice(ctx->device);
+  for (Slot* s : ctx->pool) {
+    slot_destroy(*s);
+    delete s;
+  }
+  ctx->pool.clear();
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+  return MSIR_OK;
+}
+
+struct msir_factors {
+  msir_ctx* ctx = nullptr;
+  Slot slot;
+  Job job;
+};
+
+msir_status msir_factor(msir_ctx* ctx, int n, const double* A_dev, int lda, int u, int uf,
+                        const msir_params* params, msir_factors** out, int* info, int* nonfinite) {
+  if (!ctx || !out || n <= 0 || lda < n || !A_dev) return MSIR_ERR_INVALID;
+  msir_triple t{uf, u, u == MSIR_FP32 ? MSIR_FP64 : MSIR_DD};
+  if (!valid_triple(t)) return MSIR_ERR_INVALID;
+  msir_params p = resolve_params(params);
+  if (!valid_params(p)) return MSIR_ERR_INVALID;
+  CK(cudaSetDevice(ctx->device));
+  auto* f = new msir_factors();
+  f->ctx = ctx;
+  msir_status r = slot_init(f->slot, ctx->device);
+  if (r != MSIR_OK) { slot_destroy(f->slot); delete f; return r; }
+  f->job.n = n;
+  f->job.A = A_dev;
+  f->job.lda = lda;
+  f->job.t = t;
+  f->job.p = p;
+  Slot& s = f->slot;
+  s.job = &f->job;
+  s.u0 = u;
+  s.G = refine_grid(ctx, n, 1);
+  r = ws_alloc(s.w, n, kcap_of(n, p.kmax_frac), s.G, s.st);
+  if (r == MSIR_OK) r = cuda_status(ingest_matrix(A_dev, lda, n, u, s.w.Au, s.w.ldu, s.st));
+  if (r == MSIR_OK) r = slot_enqueue_factor(ctx, s, uf, false);
+  if (r == MSIR_OK) r = cuda_status(cudaStreamSynchronize(s.st));
+  if (r != MSIR_OK) { slot_destroy(s); delete f; return r; }
+  Level& L = s.lv[s.try_level];
+  L.info = s.h_flags[0];
+  L.nonfinite = s.h_flags[1];
+  L.valid = true;
+  s.cur = s.try_level;
+  if (s.h_flags[2]) { int e = s.h_flags[2]; slot_destroy(s); delete f; return (msir_status)e; }
+  if (info) *info = L.info;
+  if (nonfinite) *nonfinite = L.nonfinite;
+  *out = f;
+  return MSIR_OK;
+}
+
+msir_status msir_factors_destroy(msir_factors* f) {
+  if (!f) return MSIR_ERR_INVALID;
+  cudaSetDevice(f->ctx->device);
+  slot_destroy(f->slot);
+  delete f;
+  return MSIR_OK;
+}
+
+msir_status msir_factors_export(msir_ctx* ctx, const msir_factors* fc, double* F_host, int* ipiv_host) {
+  if (!ctx || !fc) return MSIR_ERR_INVALID;
+  const Slot& s = fc->slot;
+  const Level& L = s.lv[s.cur];
+  const int n = fc->job.n;
+  CK(cudaSetDevice(ctx->device));
+  if (ipiv_host) CK(cudaMemcpy(ipiv_host, L.ipiv, (size_t)n * 4, cudaMemcpyDeviceToHost));
+  if (F_host) {
+    const int es = elem_size(L.fmt);
+    std::vector<unsigned char> raw((size_t)n * s.w.ldu * es);
+    CK(cudaMemcpy(raw.data(), L.F, raw.size(), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const unsigned char* p = raw.data() + ((size_t)i * s.w.ldu + j) * es;
+        double v;
+        if (L.fmt == MSIR_FP64) {
+          memcpy(&v, p, 8);
+        } else if (L.fmt == MSIR_FP32) {
+          float f;
+          memcpy(&f, p, 4);
+          v = f;
+        } else {
+          uint16_t h;
+          memcpy(&h, p, 2);
+          uint32_t bits;
+          if (L.fmt == MSIR_BF16) {
+            bits = (uint32_t)h << 16;
+          } else {  // IEEE half -> single, exact
+            const uint32_t sgn = (uint32_t)(h & 0x8000) << 16;
+            int e = (h >> 10) & 0x1f;
+            uint32_t m = h & 0x3ff;
+            if (e == 0x1f) {
+              bits = sgn | 0x7f800000u | (m << 13);
+            } else if (e == 0) {
+              if (m == 0) {
+                bits = sgn;
+              } else {
+                e = 1;
+                while (!(m & 0x400)) { m <<= 1; --e; }
+                m &= 0x3ff;
+                bits = sgn | ((uint32_t)(e + 112) << 23) | (m << 13);
+              }
+            } else {
+              bits = sgn | ((uint32_t)(e + 112) << 23) | (m << 13);
+            }
+          }
+          float f;
+          memcpy(&f, &bits, 4);
+          v = f;
+        }
+        F_host[(size_t)i * n + j] = v;
+      }
+  }
+  return MSIR_OK;
+}
+
+msir_status msir_factors_apply(msir_ctx* ctx, const msir_factors* fc, int nrhs, const double* B_dev,
+                               int ldb, double* X_dev, int ldx, int arith, int store) {
+  if (!ctx || !fc || nrhs < 1 || !B_dev || !X_dev) return MSIR_ERR_INVALID;
+  const int n = fc->job.n;
+  if (ldb < n || ldx < n) return MSIR_ERR_INVALID;
+  if (arith != MSIR_FP32 && arith != MSIR_FP64 && arith != MSIR_DD) return MSIR_ERR_INVALID;
+  if (arith != MSIR_DD && (store < MSIR_BF16 || store > MSIR_FP64)) return MSIR_ERR_INVALID;
+  CK(cudaSetDevice(ctx->device));
+  Slot& s = const_cast<Slot&>(fc->slot);
+  CK(cudaMemsetAsync(s.w.flags, 0, ((size_t)(n + kBlk - 1) / kBlk + 1) * 4, s.st));
+  RefState st0;
+  memset(&st0, 0, sizeof(st0));
+  for (int c = 0; c < nrhs; ++c) {
+    RefineArgs a;
+    fill_args(ctx, s, a, MODE_APPLY);
+    a.ap_arith = arith;
+    a.ap_store = store;
+    a.ap_in = B_dev + (size_t)c * ldb;
+    a.ap_out = X_dev + (size_t)c * ldx;
+    st0.epoch = (unsigned)(2 * c);
+    CK(cudaMemcpyAsync(s.w.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s.st));
+    CK(cudaMemsetAsync(s.w.bar, 0, 64, s.st));
+    CK(launch_refine(s.u0, s.lv[s.cur].fmt, a, s.G, s.st));
+    CK(cudaStreamSynchronize(s.st));
+  }
+  int flags[16];
+  CK(cudaMemcpy(flags, s.w.iflags, sizeof(flags), cudaMemcpyDeviceToHost));
+  if (flags[2]) return (msir_status)flags[2];
+  return MSIR_OK;
+}
+
+msir_status msir_residual(msir_ctx* ctx, int n, const double* A_dev, int lda, int u0,
+                          const double* x_dev, const double* b_dev, int ur, double* r_dev,
+                          double* s_host) {
+  if (!ctx || n <= 0 || lda < n || !A_dev || !x_dev || !b_dev || !r_dev) return MSIR_ERR_INVALID;
+  if ((u0 != MSIR_FP32 && u0 != MSIR_FP64) || (ur != MSIR_FP64 && ur != MSIR_DD)) return MSIR_ERR_INVALID;
+  CK(cudaSetDevice(ctx->device));
+  Slot s;
+  msir_status r = slot_init(s, ctx->device);
+  Job j;
+  j.n = n;
+  j.p = resolve_params(nullptr);
+  j.t = msir_triple{MSIR_FP64, u0, ur};
+  s.job = &j;
+  s.u0 = u0;
+  s.G = refine_grid(ctx, n, 1);
+  if (r == MSIR_OK) r = ws_alloc(s.w, n, 1, s.G, s.st);
+  if (r == MSIR_OK) {
+    ingest_matrix(A_dev, lda, n, u0, s.w.Au, s.w.ldu, s.st);
+    round_vec(b_dev, n, u0, s.w.b_u, s.st);
+    iota(s.w.ident, n, s.st);
+    copy_vec(x_dev, n, s.w.x, s.st);
+    cudaMemsetAsync(s.w.iflags, 0, 64, s.st);
+    s.lv[0].perm = s.w.ident;
+    s.cur = 0;
+    RefineArgs a;
+    fill_args(ctx, s, a, MODE_RESIDUAL);
+    a.ap_arith = ur;
+    a.res_s = s.w.scal + 2;
+    RefState st0;
+    memset(&st0, 0, sizeof(st0));
+    cudaMemcpyAsync(s.w.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s.st);
+    cudaMemsetAsync(s.w.bar, 0, 64, s.st);
+    r = cuda_status(launch_refine(u0, MSIR_FP64, a, s.G, s.st));
+    if (r == MSIR_OK) {
+      cudaMemcpyAsync(r_dev, s.w.r_hi, (size_t)n * 8, cudaMemcpyDeviceToDevice, s.st);
+      if (ur == MSIR_DD) cudaMemcpyAsync(r_dev + n, s.w.r_lo, (size_t)n * 8, cudaMemcpyDeviceToDevice, s.st);
+      double sv = 0;
+      cudaMemcpyAsync(&sv, s.w.scal + 2, 8, cudaMemcpyDeviceToHost, s.st);
+      r = cuda_status(cudaStreamSynchronize(s.st));
+      if (s_host) *s_host = sv;
+    }
+  }
+  slot_destroy(s);
+  return r;
+}
+
+msir_status msir_solve(msir_ctx* ctx, int n, int nrhs, const double* A_dev, int lda, const double* B_dev,
+                       int ldb, double* X_dev, int ldx, msir_triple t, const msir_params* params,
+                       msir_report* rep) {
+  if (!ctx || n <= 0 || nrhs < 1 || nrhs > 16 || lda < n || ldb < n || ldx < n || !A_dev || !B_dev ||
+      !X_dev)
+    return MSIR_ERR_INVALID;
+  if (!valid_triple(t)) return MSIR_ERR_INVALID;
+  msir_params p = resolve_params(params);
+  if (!valid_params(p)) return MSIR_ERR_INVALID;
+  CK(cudaSetDevice(ctx->device));
+  static std::atomic<uint64_t> ids{1};
+  const uint64_t id = ids++;
+  std::vector<Job> jobs(nrhs);
+  std::vector<Job*> jp;
+  for (int c = 0; c < nrhs; ++c) {
+    jobs[c].n = n;
+    jobs[c].A = A_dev;
+    jobs[c].lda = lda;
+    jobs[c].b = B_dev + (size_t)c * ldb;
+    jobs[c].x = X_dev + (size_t)c * ldx;
+    jobs[c].t = t;
+    jobs[c].p = p;
+    jobs[c].matrix_id = id;
+    jp.push_back(&jobs[c]);
+  }
+  std::vector<Slot*> slots;
+  msir_status r = pooled_slots(ctx, 1, slots);
+  // order the slot's work after the caller's stream
+  if (r == MSIR_OK) {
+    cudaEventRecord(slots[0]->e0, ctx->stream);
+    cudaStreamWaitEvent(slots[0]->st, slots[0]->e0, 0);
+  }
+  if (r == MSIR_OK) r = run_jobs(ctx, jp, slots);
+  if (r == MSIR_OK) cudaStreamSynchronize(slots[0]->st);
+  if (r != MSIR_OK) return r;
+  msir_status agg = MSIR_OK;
+  for (int c = 0; c < nrhs; ++c) {
+    if (rep) rep[c] = jobs[c].rep;
+    if (jobs[c].status < 0) agg = (msir_status)jobs[c].status;
+    else if (jobs[c].status == MSIR_NOT_CONVERGED && agg == MSIR_OK) agg = MSIR_NOT_CONVERGED;
+  }
+  return agg;
+}
+
+msir_status msir_solve_host(msir_ctx* ctx, int n, const double* A_host, int lda, const double* b_host,
+                            double* x_host, msir_triple t, const msir_params* params, msir_report* rep) {
+  if (!ctx || n <= 0 || lda < n || !A_host || !b_host || !x_host) return MSIR_ERR_INVALID;
+  CK(cudaSetDevice(ctx->device));
+  double *A = nullptr, *b = nullptr, *x = nullptr;
+  CK(cudaMallocAsync((void**)&A, (size_t)lda * n * 8, ctx->stream));
+  CK(cudaMallocAsync((void**)&b, (size_t)n * 8, ctx->stream));
+  CK(cudaMallocAsync((void**)&x, (size_t)n * 8, ctx->stream));
+  cudaMemcpyAsync(A, A_host, (size_t)lda * n * 8, cudaMemcpyHostToDevice, ctx->stream);
+  cudaMemcpyAsync(b, b_host, (size_t)n * 8, cudaMemcpyHostToDevice, ctx->stream);
+  msir_status r = msir_solve(ctx, n, 1, A, lda, b, n, x, n, t, params, rep);
+  if (r >= 0) cudaMemcpyAsync(x_host, x, (size_t)n * 8, cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(A, ctx->stream);
+  cudaFreeAsync(b, ctx->stream);
+  cudaFreeAsync(x, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
+  return r;
+}
+
+msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n, const double* const* A_dev,
+                               const double* const* b_dev, double* const* x_dev, const msir_triple* t,
+                               const msir_params* params, msir_report* reps) {
+  if (!ctx || count < 0 || (count > 0 && (!n || !A_dev || !b_dev || !x_dev || !t))) return MSIR_ERR_INVALID;
+  msir_params p = resolve_params(params);
+  if (!valid_params(p)) return MSIR_ERR_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (n[i] <= 0 || !valid_triple(t[i]) || !A_dev[i] || !b_dev[i] || !x_dev[i]) return MSIR_ERR_INVALID;
+  if (count == 0) return MSIR_OK;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<Job> jobs(count);
+  std::vector<Job*> jp(count);
+  // largest systems first (longest-processing-time order)
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  for (int q = 0; q < count; ++q) {
+    const int i = order[q];
+    jobs[i].n = n[i];
+    jobs[i].A = A_dev[i];
+    jobs[i].lda = n[i];
+    jobs[i].b = b_dev[i];
+    jobs[i].x = x_dev[i];
+    jobs[i].t = t[i];
+    jobs[i].p = p;
+    jp[q] = &jobs[i];
+  }
+  int nmax = 0;
+  for (int i = 0; i < count; ++i) nmax = std::max(nmax, n[i]);
+  const int nslots = std::max(1, std::min(count, std::min(32, ctx->num_sms / std::max(1, (nmax + kBlk - 1) / kBlk / 4 + 1))));
+  std::vector<Slot*> slots;
+  msir_status r = pooled_slots(ctx, nslots, slots);
+  if (r == MSIR_OK) {
+    for (Slot* s : slots) {
+      cudaEventRecord(s->e0, ctx->stream);
+      cudaStreamWaitEvent(s->st, s->e0, 0);
+    }
+    r = run_jobs(ctx, jp, slots);
+  }
+  for (Slot* s : slots) cudaStreamSynchronize(s->st);
+  if (r != MSIR_OK) return r;
+  msir_status agg = MSIR_OK;
+  for (int i = 0; i < count; ++i) {
+    if (reps) reps[i] = jobs[i].rep;
+    if (jobs[i].status < 0) agg = (msir_status)jobs[i].status;
+    else if (jobs[i].status == MSIR_NOT_CONVERGED && agg == MSIR_OK) agg = MSIR_NOT_CONVERGED;
+  }
+  return agg;
+}
+
+// ------------------------------------------------------------ server
+
+struct Request {
+  uint64_t ticket;
+  Job job;
+  double* dA = nullptr;  // device copies owned by the server
+  double* db = nullptr;
+  double* dx = nullptr;
+  std::vector<double> x_host;
+  int state = 0;         // 0 queued, 1 running, 2 done
+  size_t footprint = 0;
+};
+
+struct msir_server {
+  msir_ctx* ctx = nullptr;
+  size_t budget = 0, in_use = 0;
+  int max_slots = 1;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Request*> queue;
+  std::map<uint64_t, Request*> all;
+  uint64_t next_ticket = 1;
+  std::atomic<bool> stop{false};
+  std::thread worker;
+  std::vector<Slot> slots;
+  std::vector<Request*> running;
+};
+
+static size_t request_footprint(int n, const msir_params& p, int u) {
+  const size_t nn = (size_t)n * n;
+  const size_t ws = ws_bytes_for(n, kcap_of(n, p.kmax_frac), std::min(256, (n + kBlk - 1) / kBlk));
+  (void)u;
+  return ws + nn * 8 + (size_t)n * 16;
+}
+
+static void server_loop(msir_server* S) {
+  cudaSetDevice(S->ctx->device);
+  const int share = S->max_slots;
+  while (true) {
+    // admit
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      for (size_t si = 0; si < S->slots.size(); ++si) {
+        if (S->running[si] || S->queue.empty()) continue;
+        Request* q = S->queue.front();
+        if (S->in_use + q->footprint > S->budget && S->in_use > 0) break;
+        S->queue.pop_front();
+        S->in_use += q->footprint;
+        q->state = 1;
+        S->running[si] = q;
+        lk.unlock();
+        Slot& s = S->slots[si];
+        ws_free(s.w, s.st);
+        s.loaded_id = 0;
+        msir_status r = slot_start(S->ctx, s, &q->job, share);
+        lk.lock();
+        if (r != MSIR_OK) {
+          q->job.status = r;
+          q->state = 2;
+          q->job.t_done = std::chrono::steady_clock::now();
+          S->in_use -= q->footprint;
+          S->running[si] = nullptr;
+          s.job = nullptr;
+          s.step = S_IDLE;
+        }
+      }
+      if (S->stop && S->queue.empty()) {
+        bool any = false;
+        for (auto* q : S->running) any = any || q;
+        if (!any) break;
+      }
+    }
+    bool progressed = false;
+    for (size_t si = 0; si < S->slots.size(); ++si) {
+      Slot& s = S->slots[si];
+      Request* q = S->running[si];
+      if (!q || !s.job) continue;
+      cudaError_t e = cudaEventQuery(s.ev);
+      if (e == cudaErrorNotReady) continue;
+      progressed = true;
+      bool done = false;
+      if (e != cudaSuccess) {
+        q->job.status = MSIR_ERR_CUDA;
+        done = true;
+        s.job = nullptr;
+        s.step = S_IDLE;
+      } else {
+        done = slot_advance(S->ctx, s);
+      }
+      if (done) {
+        cudaMemcpyAsync(q->x_host.data(), q->dx, (size_t)q->job.n * 8, cudaMemcpyDeviceToHost, s.st);
+        cudaStreamSynchronize(s.st);
+        ws_free(s.w, s.st);
+        cudaFreeAsync(q->dA, s.st);
+        cudaFreeAsync(q->db, s.st);
+        cudaFreeAsync(q->dx, s.st);
+        cudaStreamSynchronize(s.st);
+        std::lock_guard<std::mutex> lk(S->mu);
+        q->dA = q->db = q->dx = nullptr;
+        q->job.t_done = std::chrono::steady_clock::now();
+        q->state = 2;
+        S->in_use -= q->footprint;
+        S->running[si] = nullptr;
+      }
+    }
+    if (!progressed) {
+      std::unique_lock<std::mutex> lk(S->mu);
+      bool idle = S->queue.empty();
+      for (auto* q : S->running) idle = idle && !q;
+      if (idle && !S->stop)
+        S->cv.wait_for(lk, std::chrono::milliseconds(2));
+      else
+        S->cv.wait_for(lk, std::chrono::microseconds(50));
+    }
+  }
+}
+
+msir_status msir_server_create(msir_ctx* ctx, size_t hbm_budget_bytes, int max_slots, msir_server** out) {
+  if (!ctx || !out || max_slots < 1 || max_slots > 64) return MSIR_ERR_INVALID;
+  CK(cudaSetDevice(ctx->device));
+  auto* S = new msir_server();
+  S->ctx = ctx;
+  if (hbm_budget_bytes == 0) {
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    hbm_budget_bytes = (size_t)(0.9 * (double)fr);
+  }
+  S->budget = hbm_budget_bytes;
+  S->max_slots = max_slots;
+  S->slots.resize(max_slots);
+  S->running.assign(max_slots, nullptr);
+  for (auto& s : S->slots) {
+    msir_status r = slot_init(s, ctx->device);
+    if (r != MSIR_OK) {
+      for (auto& s2 : S->slots) slot_destroy(s2);
+      delete S;
+      return r;
+    }
+  }
+  S->worker = std::thread(server_loop, S);
+  *out = S;
+  return MSIR_OK;
+}
+
+msir_status msir_server_submit(msir_server* S, int n, const double* A_host, int lda, const double* b_host,
+                               msir_triple t, const msir_params* params, uint64_t* ticket) {
+  if (!S || n <= 0 || lda < n || !A_host || !b_host || !ticket) return MSIR_ERR_INVALID;
+  if (!valid_triple(t)) return MSIR_ERR_INVALID;
+  msir_params p = resolve_params(params);
+  if (!valid_params(p)) return MSIR_ERR_INVALID;
+  cudaSetDevice(S->ctx->device);
+  auto* q = new Request();
+  q->job.n = n;
+  q->job.lda = n;
+  q->job.t = t;
+  q->job.p = p;
+  q->footprint = request_footprint(n, p, t.u);
+  q->x_host.assign(n, 0.0);
+  // copy in now: the caller may free its buffers when submit returns
+  cudaStream_t cs;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { delete q; return MSIR_ERR_CUDA; }
+  cudaError_t e = cudaMallocAsync((void**)&q->dA, (size_t)n * n * 8, cs);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&q->db, (size_t)n * 8, cs);
+  if (e == cudaSuccess) e = cudaMallocAsync((void**)&q->dx, (size_t)n * 8, cs);
+  if (e == cudaSuccess) e = cudaMemcpy2DAsync(q->dA, (size_t)n * 8, A_host, (size_t)lda * 8, (size_t)n * 8, n,
+                                              cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(q->db, b_host, (size_t)n * 8, cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) {
+    if (q->dA) cudaFree(q->dA);
+    if (q->db) cudaFree(q->db);
+    if (q->dx) cudaFree(q->dx);
+    delete q;
+    return cuda_status(e);
+  }
+  q->job.A = q->dA;
+  q->job.b = q->db;
+  q->job.x = q->dx;
+  q->job.t_submit = std::chrono::steady_clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    q->ticket = S->next_ticket++;
+    S->all[q->ticket] = q;
+    S->queue.push_back(q);
+  }
+  S->cv.notify_all();
+  *ticket = q->ticket;
+  return MSIR_OK;
+}
+
+msir_status msir_server_poll(msir_server* S, uint64_t ticket, int* state, double* x_host, msir_report* rep,
+                             double* latency_ms) {
+  if (!S || !state) return MSIR_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->all.find(ticket);
+  if (it == S->all.end()) return MSIR_ERR_INVALID;
+  Request* q = it->second;
+  *state = q->state;
+  if (q->state != 2) return MSIR_OK;
+  if (x_host) memcpy(x_host, q->x_host.data(), (size_t)q->job.n * 8);
+  if (rep) *rep = q->job.rep;
+  if (latency_ms)
+    *latency_ms = std::chrono::duration<double, std::milli>(q->job.t_done - q->job.t_submit).count();
+  const int st = q->job.status;
+  S->all.erase(it);
+  delete q;
+  return st < 0 ? (msir_status)st : MSIR_OK;
+}
+
+msir_status msir_server_destroy(msir_server* S) {
+  if (!S) return MSIR_ERR_INVALID;
+  S->stop = true;
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  for (auto& s : S->slots) slot_destroy(s);
+  for (auto& kv : S->all) {
+    Request* q = kv.second;
+    if (q->dA) cudaFree(q->dA);
+    if (q->db) cudaFree(q->db);
+    if (q->dx) cudaFree(q->dx);
+    delete q;
+  }
+  delete S;
+  return MSIR_OK;
+}
+
+}  // extern "C"

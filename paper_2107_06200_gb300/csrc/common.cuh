@@ -1,0 +1,239 @@
+// Device-side helpers shared by the MSIR kernels: number formats, explicit
+// IEEE rounding, double-double arithmetic, bounded waits and the grid
+// barrier of the persistent kernels.
+//
+// Every arithmetic step whose rounding the method fixes uses an explicitly
+// rounded intrinsic (__fmul_rn, __fsub_rn, __dadd_rn, ...), which the
+// compiler never contracts into a fused multiply-add.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/msir.h"
+
+namespace msir {
+
+// ------------------------------------------------------------------ formats
+
+template <typename F> struct Fmt;
+template <> struct Fmt<__half> {
+  using T = float;  // arithmetic precision of the panel and the u_f solves
+  static constexpr int code = MSIR_FP16;
+};
+template <> struct Fmt<__nv_bfloat16> {
+  using T = float;
+  static constexpr int code = MSIR_BF16;
+};
+template <> struct Fmt<float> {
+  using T = float;
+  static constexpr int code = MSIR_FP32;
+};
+template <> struct Fmt<double> {
+  using T = double;
+  static constexpr int code = MSIR_FP64;
+};
+
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ double to_f(double v) { return v; }
+
+template <typename F> __device__ __forceinline__ F from_t(float v);
+template <> __device__ __forceinline__ __half from_t<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 from_t<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ float from_t<float>(float v) { return v; }
+template <typename F> __device__ __forceinline__ F from_d(double v);
+template <> __device__ __forceinline__ double from_d<double>(double v) { return v; }
+template <> __device__ __forceinline__ float from_d<float>(double v) { return __double2float_rn(v); }
+template <> __device__ __forceinline__ __half from_d<__half>(double v) {
+  return __float2half_rn(__double2float_rn(v));  // 16-bit formats round from fp32
+}
+template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(double v) {
+  return __float2bfloat16_rn(__double2float_rn(v));
+}
+
+// Round a double to the format with code `fmt` and return it as a double.
+__device__ __forceinline__ double round_to(double v, int fmt) {
+  switch (fmt) {
+    case MSIR_FP32: return (double)__double2float_rn(v);
+    case MSIR_FP16: return (double)__half2float(__float2half_rn(__double2float_rn(v)));
+    case MSIR_BF16: return (double)__bfloat162float(__float2bfloat16_rn(__double2float_rn(v)));
+    default: return v;
+  }
+}
+__device__ __forceinline__ float round_f(float v, int fmt) {
+  switch (fmt) {
+    case MSIR_FP16: return __half2float(__float2half_rn(v));
+    case MSIR_BF16: return __bfloat162float(__float2bfloat16_rn(v));
+    default: return v;
+  }
+}
+
+__device__ __forceinline__ bool finite_d(double v) { return isfinite(v); }
+
+// ------------------------------------------------------------ double-double
+// Knuth TwoSum, Dekker FastTwoSum, TwoProduct via fma, and the accurate dd
+// addition of Hida, Li and Bailey's QD library (restated from its paper).
+
+struct dd_t {
+  double hi, lo;
+};
+
+__device__ __forceinline__ dd_t two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double bb = __dsub_rn(s, a);
+  double e = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dd_t fast_two_sum(double a, double b) {
+  double s = __dadd_rn(a, b);
+  double e = __dsub_rn(b, __dsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ dd_t two_prod(double a, double b) {
+  double p = __dmul_rn(a, b);
+  double e = __fma_rn(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ dd_t dd_add(dd_t a, dd_t b) {
+  dd_t s = two_sum(a.hi, b.hi);
+  dd_t t = two_sum(a.lo, b.lo);
+  double e = __dadd_rn(s.lo, t.hi);
+  dd_t u = fast_two_sum(s.hi, e);
+  e = __dadd_rn(u.lo, t.lo);
+  return fast_two_sum(u.hi, e);
+}
+__device__ __forceinline__ dd_t dd_neg(dd_t a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dd_t dd_sub(dd_t a, dd_t b) { return dd_add(a, dd_neg(b)); }
+__device__ __forceinline__ dd_t dd_mul_d(dd_t a, double d) {
+  dd_t p = two_prod(a.hi, d);
+  double e = __dadd_rn(p.lo, __dmul_rn(a.lo, d));
+  return fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ dd_t dd_div_d(dd_t a, double d) {
+  double q1 = __ddiv_rn(a.hi, d);
+  dd_t r = dd_sub(a, dd_mul_d(dd_t{d, 0.0}, q1));
+  double q2 = __ddiv_rn(r.hi, d);
+  r = dd_sub(r, dd_mul_d(dd_t{d, 0.0}, q2));
+  double q3 = __ddiv_rn(r.hi, d);
+  dd_t q = fast_two_sum(q1, q2);
+  return dd_add(q, dd_t{q3, 0.0});
+}
+__device__ __forceinline__ dd_t dd_shfl_xor(dd_t a, int m) {
+  return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
+}
+
+// ------------------------------------------------------------ waits
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_release_u32(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ int ld_volatile_i32(const int* p) {
+  return *(const volatile int*)p;
+}
+
+// Deadline of every device-side wait.  A legitimate wait lasts micro- to
+// milliseconds; after this the waiter records MSIR_ERR_TIMEOUT and returns.
+constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;
+
+// Grid-wide barrier for a cooperative launch of G blocks.  `count` grows by
+// G per episode and is zeroed by the host before the launch.  Returns false
+// (after recording the error) on timeout or if another block failed.
+__device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned G) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    __threadfence();
+    unsigned old = atom_add_release_u32(count, 1u);
+    unsigned target = (old / G + 1u) * G;
+    unsigned long long t0 = gtimer();
+    unsigned spins = 0;
+    while ((int)(ld_acquire_u32(count) - target) < 0) {
+      if ((++spins & 63u) == 0u) {
+        if (ld_volatile_i32(err) != 0) { ok = 0; break; }
+        if (gtimer() - t0 > kWaitTimeoutNs) {
+          atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Spin (all lanes of the calling warp) until *flag >= epoch.  Bounded.
+__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned epoch, int* err) {
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  while ((int)(ld_acquire_u32(flag) - epoch) < 0) {
+    if ((++spins & 255u) == 0u) {
+      if (t0 == 0) t0 = gtimer();
+      if (ld_volatile_i32(err) != 0) return false;
+      if (gtimer() - t0 > kWaitTimeoutNs) {
+        atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+// ------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = __dadd_rn(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = __fadd_rn(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+__device__ __forceinline__ dd_t warp_sum_dd(dd_t v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = dd_add(v, dd_shfl_xor(v, m));
+  return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+
+// max that propagates NaN (an Inf/NaN anywhere must reach the controller)
+__device__ __forceinline__ double nanmax(double a, double b) {
+  if (isnan(a) || isnan(b)) return __longlong_as_double(0x7ff8000000000000ll);
+  return a > b ? a : b;
+}
+__device__ __forceinline__ double warp_nanmax_d(double v) {
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) v = nanmax(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+
+}  // namespace msir

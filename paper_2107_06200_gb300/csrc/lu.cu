@@ -1,0 +1,596 @@
+// Blocked right-looking GEPP in the factorisation precision u_f
+// (Algorithm 4, first step; partial pivoting as in Sec. 1).
+//
+// The matrix lives in device memory in its storage format F (bf16, fp16,
+// fp32 or fp64), row-major with leading dimension lda.  Arithmetic of the
+// panel and of the triangular solves is carried out in T = fp32 (fp64 when
+// F is fp64), with every product and every difference explicitly rounded,
+// so those steps are bit-for-bit reproducible; values are rounded back to F
+// when they are stored.  Two-level blocking: outer blocks of W = nbo
+// columns, factored as panels of nb columns.
+//
+//   lu_outer_panel      one thread-block cluster factors an (n-k) x W outer
+//                       block: for each nb-column panel, the pivot search,
+//                       interchange, scaling and rank-1 updates run with the
+//                       panel in shared memory; pivot candidates and the
+//                       pivot row are pushed to every CTA of the cluster
+//                       through distributed shared memory, so each column
+//                       costs one cluster barrier.  The inner interchanges,
+//                       substitution and update of the outer block follow.
+//   lu_outer_swap_trsm  applies the outer block's interchanges to the other
+//                       columns, forms U12 = L11^{-1} A12 by substitution and
+//                       (for the tensor-core update) writes U12^T.
+//   lu_update_simt      A22 <- fl_F(fl_T(A22 - L21 U12)) for fp32/fp64
+//                       factors (the bf16/fp16 update is in lu_tc.cu).
+#include <cooperative_groups.h>
+#include <climits>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace cg = cooperative_groups;
+
+namespace msir {
+
+template <typename T> __device__ __forceinline__ T mul_rn(T a, T b);
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+template <typename T> __device__ __forceinline__ T sub_rn(T a, T b);
+template <> __device__ __forceinline__ float sub_rn<float>(float a, float b) { return __fsub_rn(a, b); }
+template <> __device__ __forceinline__ double sub_rn<double>(double a, double b) { return __dsub_rn(a, b); }
+template <typename T> __device__ __forceinline__ T div_rn(T a, T b);
+template <> __device__ __forceinline__ float div_rn<float>(float a, float b) { return __fdiv_rn(a, b); }
+template <> __device__ __forceinline__ double div_rn<double>(double a, double b) { return __ddiv_rn(a, b); }
+template <typename T> __device__ __forceinline__ T fma_rn(T a, T b, T c);
+template <> __device__ __forceinline__ float fma_rn<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+template <> __device__ __forceinline__ double fma_rn<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+template <typename F> __device__ __forceinline__ F store_rn(typename Fmt<F>::T v);
+template <> __device__ __forceinline__ __half store_rn<__half>(float v) { return __float2half_rn(v); }
+template <> __device__ __forceinline__ __nv_bfloat16 store_rn<__nv_bfloat16>(float v) {
+  return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ float store_rn<float>(float v) { return v; }
+template <> __device__ __forceinline__ double store_rn<double>(double v) { return v; }
+
+// Panel width limit per arithmetic precision (also the register arrays).
+template <typename T> struct PanelNB { static constexpr int v = 32; };
+template <> struct PanelNB<double> { static constexpr int v = 16; };
+
+// Pivot order: larger |a| first; NaN (mapped to -1) only if nothing else;
+// equal magnitudes -> smaller row index.
+__device__ __forceinline__ bool better(double av, int ai, double bv, int bi) {
+  return av > bv || (av == bv && ai < bi);
+}
+
+// ------------------------------------------------------------------ panel
+
+template <typename F>
+__global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) {
+  using T = typename Fmt<F>::T;
+  constexpr int NBM = PanelNB<T>::v;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks();
+  const int rank = (int)cl.block_rank();
+  const int tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kPanelThreads / 32;
+  F* A = (F*)a.A;
+  const int lda = a.lda, n = a.n, k = a.k, W = a.W, nb = a.nb;
+  const int ldp = nb + 1;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* P = (T*)smem_raw;                                        // R_cap x ldp
+  T* cand_row = P + (size_t)a.R_cap * ldp;                    // [2][16][NBM]
+  T* jrow = cand_row + 2 * 16 * NBM;                          // [2][NBM]
+  T* L11 = jrow + 2 * NBM;                                    // NBM x NBM
+  T* U12 = L11 + NBM * NBM;                                   // NBM x W
+  size_t off = sizeof(T) * ((size_t)a.R_cap * ldp + 2 * 16 * NBM + 2 * NBM + NBM * NBM +
+                            (size_t)NBM * W);
+  off = (off + 7) & ~(size_t)7;
+  double* cand_v = (double*)(smem_raw + off);                 // [2][16]
+  int* cand_i = (int*)(cand_v + 32);                          // [2][16]
+  int* s_piv = cand_i + 32;                                   // [NBM]
+  int* mpos = s_piv + NBM;                                    // inner map positions [2*NBM]
+  int* mval = mpos + 2 * NBM;                                 // inner map sources
+  int* opos = mval + 2 * NBM;                                 // outer map (rank 0) [2*W]
+  int* oval = opos + 2 * W;
+  __shared__ double s_wv[NW];
+  __shared__ int s_wi[NW];
+  __shared__ int s_cnt, s_ocnt, s_nf;
+
+  if (tid == 0) { s_ocnt = W; s_nf = 0; }
+  for (int s = tid; s < W; s += blockDim.x) { opos[s] = s; oval[s] = s; }
+  __syncthreads();
+
+  for (int kk = k; kk < k + W; kk += nb) {
+    const int w = min(nb, k + W - kk);
+    const int m = n - kk;
+    const int R = (m + C - 1) / C;
+    const int my0 = rank * R;
+    const int nloc = max(0, min(m, my0 + R) - my0);
+
+    for (int li = tid; li < nloc; li += blockDim.x) {
+      const F* src = A + (size_t)(kk + my0 + li) * lda + kk;
+      for (int c = 0; c < w; ++c) P[li * ldp + c] = (T)to_f(src[c]);
+    }
+    __syncthreads();
+
+    for (int j = 0; j < w; ++j) {
+      const int buf = j & 1;
+      // local pivot candidate among my rows with panel index >= j
+      double bv = -2.0;
+      int bi = INT_MAX;
+      for (int li = tid; li < nloc; li += blockDim.x) {
+        const int gi = my0 + li;
+        if (gi >= j) {
+          double av = fabs((double)P[li * ldp + j]);
+          if (isnan(av)) av = -1.0;
+          if (better(av, gi, bv, bi)) { bv = av; bi = gi; }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
+        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
+      }
+      if (lane == 0) { s_wv[warp] = bv; s_wi[warp] = bi; }
+      __syncthreads();
+      bv = s_wv[0];
+      bi = s_wi[0];
+      for (int q = 1; q < NW; ++q)
+        if (better(s_wv[q], s_wi[q], bv, bi)) { bv = s_wv[q]; bi = s_wi[q]; }
+      // push my candidate (value, index, row) and, if I own row j, row j
+      if (tid < C) {
+        double* rv = cl.map_shared_rank(cand_v, tid);
+        int* ri = cl.map_shared_rank(cand_i, tid);
+        rv[buf * 16 + rank] = bv;
+        ri[buf * 16 + rank] = bi;
+      }
+      const bool valid = bi != INT_MAX;
+      const int lb = bi - my0;
+      for (int idx = tid; idx < C * w; idx += blockDim.x) {
+        const int d = idx / w, c = idx % w;
+        T* rr = cl.map_shared_rank(cand_row, d);
+        rr[(buf * 16 + rank) * NBM + c] = valid ? P[lb * ldp + c] : (T)0;
+      }
+      const int ownj = j / R;
+      if (ownj == rank) {
+        for (int idx = tid; idx < C * w; idx += blockDim.x) {
+          const int d = idx / w, c = idx % w;
+          T* rj = cl.map_shared_rank(jrow, d);
+          rj[buf * NBM + c] = P[(j - my0) * ldp + c];
+        }
+      }
+      cl.sync();
+      // every thread reduces the C candidates from local shared memory
+      double pv = cand_v[buf * 16];
+      int p = cand_i[buf * 16];
+      for (int q = 1; q < C; ++q) {
+        double qv = cand_v[buf * 16 + q];
+        int qi = cand_i[buf * 16 + q];
+        if (better(qv, qi, pv, p)) { pv = qv; p = qi; }
+      }
+      const int ownp = p / R;
+      const T* prow = cand_row + (buf * 16 + ownp) * NBM;
+      const T* jr = jrow + buf * NBM;
+      if (tid < w) {
+        if (ownj == rank) P[(j - my0) * ldp + tid] = prow[tid];
+        if (p != j && ownp == rank) P[(p - my0) * ldp + tid] = jr[tid];
+      }
+      if (tid == 0) s_piv[j] = p;
+      __syncthreads();
+      const T piv = prow[j];
+      if (piv != (T)0) {
+        for (int li = tid; li < nloc; li += blockDim.x) {
+          const int gi = my0 + li;
+          if (gi > j) {
+            T* row = P + li * ldp;
+            const T l = div_rn(row[j], piv);
+            row[j] = l;
+            for (int c = j + 1; c < w; ++c) row[c] = sub_rn(row[c], mul_rn(l, prow[c]));
+          }
+        }
+      } else if (rank == 0 && tid == 0) {
+        atomicCAS(a.info, 0, kk + j + 1);
+      }
+      __syncthreads();
+    }
+
+    // store the panel (rounded to F) and its pivots
+    int nf = 0;
+    for (int li = tid; li < nloc; li += blockDim.x) {
+      F* dst = A + (size_t)(kk + my0 + li) * lda + kk;
+      for (int c = 0; c < w; ++c) {
+        F v = store_rn<F>(P[li * ldp + c]);
+        dst[c] = v;
+        if (!isfinite((double)to_f(v))) nf = 1;
+      }
+    }
+    if (nf) s_nf = 1;
+    if (rank == 0 && tid < w) a.ipiv[kk + tid] = kk + s_piv[tid];
+
+    // composite permutation of this panel's interchanges (positions
+    // relative to kk; positions < w are slots 0..w-1), and of the outer
+    // block's (relative to k, kept by rank 0).  Built by warp 0.
+    if (warp == 0) {
+      if (lane == 0) s_cnt = w;
+      for (int s = lane; s < 2 * NBM; s += 32) { mpos[s] = s < w ? s : -1; mval[s] = s < w ? s : -1; }
+      __syncwarp();
+      for (int j = 0; j < w; ++j) {
+        const int q = s_piv[j];
+        int sq;
+        if (q < w) {
+          sq = q;
+        } else {
+          int cnt = s_cnt;
+          unsigned hit = __ballot_sync(0xffffffffu, lane + w < cnt && mpos[lane + w] == q);
+          if (hit) {
+            sq = w + __ffs(hit) - 1;
+          } else {
+            sq = cnt;
+            if (lane == 0) { mpos[cnt] = q; mval[cnt] = q; s_cnt = cnt + 1; }
+          }
+          __syncwarp();
+        }
+        if (lane == 0 && sq != j) {
+          int t = mval[j];
+          mval[j] = mval[sq];
+          mval[sq] = t;
+        }
+        __syncwarp();
+      }
+      if (rank == 0) {
+        const int base = kk - k;
+        for (int j = 0; j < w; ++j) {
+          const int pa = base + j, pb = base + s_piv[j];
+          int sb;
+          if (pb < W) {
+            sb = pb;
+          } else {
+            int cnt = s_ocnt;
+            int found = -1;
+            for (int s0 = W; s0 < cnt; s0 += 32) {
+              unsigned hit = __ballot_sync(0xffffffffu, s0 + lane < cnt && opos[s0 + lane] == pb);
+              if (hit) { found = s0 + __ffs(hit) - 1; break; }
+            }
+            if (found < 0) {
+              found = cnt;
+              if (lane == 0) { opos[cnt] = pb; oval[cnt] = pb; s_ocnt = cnt + 1; }
+            }
+            sb = found;
+            __syncwarp();
+          }
+          if (lane == 0 && sb != pa) {
+            int t = oval[pa];
+            oval[pa] = oval[sb];
+            oval[sb] = t;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    __syncthreads();
+    cl.sync();  // panel values visible to the whole cluster
+
+    // inner interchanges on [k, kk) and [kk+w, k+W), then U12 = L11^{-1} A12
+    const int nleft = kk - k, nright = k + W - kk - w;
+    if (nright > 0) {
+      for (int idx = tid; idx < w * w; idx += blockDim.x) {
+        const int i = idx / w, c = idx % w;
+        L11[i * NBM + c] = (T)to_f(A[(size_t)(kk + i) * lda + kk + c]);
+      }
+    }
+    __syncthreads();
+    const int cnt = s_cnt;
+    for (int g = rank * blockDim.x + tid; g < nleft + nright; g += C * blockDim.x) {
+      const int c = g < nleft ? k + g : kk + w + (g - nleft);
+      T x[2 * NBM];
+#pragma unroll
+      for (int s = 0; s < 2 * NBM; ++s)
+        if (s < cnt) x[s] = (T)to_f(A[(size_t)(kk + mval[s]) * lda + c]);
+#pragma unroll
+      for (int s = 0; s < 2 * NBM; ++s)
+        if (s >= w && s < cnt) A[(size_t)(kk + mpos[s]) * lda + c] = store_rn<F>(x[s]);
+      if (g < nleft) {
+#pragma unroll
+        for (int s = 0; s < NBM; ++s)
+          if (s < w) A[(size_t)(kk + s) * lda + c] = store_rn<F>(x[s]);
+      } else {
+#pragma unroll
+        for (int mm = 0; mm < NBM - 1; ++mm) {
+          if (mm < w - 1) {
+#pragma unroll
+            for (int i = mm + 1; i < NBM; ++i)
+              if (i < w) x[i] = sub_rn(x[i], mul_rn(L11[i * NBM + mm], x[mm]));
+          }
+        }
+        int nf2 = 0;
+#pragma unroll
+        for (int s = 0; s < NBM; ++s)
+          if (s < w) {
+            F v = store_rn<F>(x[s]);
+            A[(size_t)(kk + s) * lda + c] = v;
+            if (!isfinite((double)to_f(v))) nf2 = 1;
+          }
+        if (nf2) s_nf = 1;
+      }
+    }
+    cl.sync();
+
+    // inner update: rows [kk+w, n), columns [kk+w, k+W)
+    if (nright > 0 && kk + w < n) {
+      for (int idx = tid; idx < w * nright; idx += blockDim.x) {
+        const int i = idx / nright, c = idx % nright;
+        U12[i * W + c] = (T)to_f(A[(size_t)(kk + i) * lda + kk + w + c]);
+      }
+      __syncthreads();
+      const int rows = n - kk - w;
+      const int Rr = (rows + C - 1) / C;
+      const int r0 = rank * Rr, r1 = min(rows, r0 + Rr);
+      for (int r = r0 + warp; r < r1; r += NW) {
+        const size_t row = (size_t)(kk + w + r);
+        T lv = lane < w ? (T)to_f(A[row * lda + kk + lane]) : (T)0;
+        for (int c0 = 0; c0 < nright; c0 += 32) {
+          const int c = c0 + lane;
+          T acc = 0;
+          for (int mm = 0; mm < w; ++mm) {
+            T l = __shfl_sync(0xffffffffu, lv, mm);
+            if (c < nright) acc = fma_rn(l, U12[mm * W + c], acc);
+          }
+          if (c < nright) {
+            F* dst = A + row * lda + kk + w + c;
+            *dst = store_rn<F>(sub_rn((T)to_f(*dst), acc));
+          }
+        }
+      }
+    }
+    cl.sync();
+  }
+
+  if (s_nf) atomicExch(a.nonfinite, 1);
+  if (rank == 0) {
+    const int oc = s_ocnt;
+    for (int s = tid; s < oc; s += blockDim.x) {
+      a.map_pos[s] = opos[s];
+      a.map_val[s] = oval[s];
+    }
+    if (tid == 0) *a.map_cnt = oc;
+  }
+}
+
+// ------------------------------------------------- outer swaps and TRSM
+
+template <typename F>
+__global__ void __launch_bounds__(256) lu_outer_swap_trsm(SwapTrsmArgs a) {
+  using T = typename Fmt<F>::T;
+  F* A = (F*)a.A;
+  const int lda = a.lda, n = a.n, k = a.k, W = a.W;
+  const int cnt = *a.map_cnt;
+  const int nleft = k, nright = n - k - W;
+  const int tiles_left = (nleft + 31) / 32;
+  const int tiles_right = (nright + 31) / 32;
+  const int tid = threadIdx.x;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* X = (T*)smem_raw;                       // W x 32
+  F* L = (F*)(X + (size_t)W * 32);           // W x W (only when right tiles exist)
+  F* E = L + (size_t)W * W;                  // (cnt - W) x 32 displaced rows
+  size_t off = sizeof(T) * (size_t)W * 32 + sizeof(F) * ((size_t)W * W + (size_t)W * 32);
+  off = (off + 15) & ~(size_t)15;
+  int* pos = (int*)(smem_raw + off);
+  int* val = pos + 2 * W;
+  __shared__ int s_nf;
+  if (tid == 0) s_nf = 0;
+  for (int s = tid; s < cnt; s += blockDim.x) { pos[s] = a.map_pos[s]; val[s] = a.map_val[s]; }
+  bool need_L = false;
+  for (int t = blockIdx.x; t < tiles_left + tiles_right; t += gridDim.x)
+    if (t >= tiles_left) need_L = true;
+  if (need_L) {
+    for (int idx = tid; idx < W * W; idx += blockDim.x) {
+      const int i = idx / W, c = idx % W;
+      L[idx] = A[(size_t)(k + i) * lda + k + c];
+    }
+  }
+  __syncthreads();
+
+  for (int t = blockIdx.x; t < tiles_left + tiles_right; t += gridDim.x) {
+    const bool right = t >= tiles_left;
+    const int c0 = right ? k + W + (t - tiles_left) * 32 : t * 32;
+    const int cend = right ? n : k;
+    // gather sources
+    for (int idx = tid; idx < cnt * 32; idx += blockDim.x) {
+      const int s = idx / 32, cc = idx % 32, c = c0 + cc;
+      if (c < cend) {
+        F v = A[(size_t)(k + val[s]) * lda + c];
+        if (s < W) X[s * 32 + cc] = (T)to_f(v);
+        else E[(s - W) * 32 + cc] = v;
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < (cnt - W) * 32; idx += blockDim.x) {
+      const int s = W + idx / 32, cc = idx % 32, c = c0 + cc;
+      if (c < cend) A[(size_t)(k + pos[s]) * lda + c] = E[(s - W) * 32 + cc];
+    }
+    if (right) {
+      for (int mm = 0; mm < W - 1; ++mm) {
+        const int rows = W - 1 - mm;
+        for (int idx = tid; idx < rows * 32; idx += blockDim.x) {
+          const int i = mm + 1 + idx / 32, cc = idx % 32;
+          X[i * 32 + cc] = sub_rn(X[i * 32 + cc], mul_rn((T)to_f(L[i * W + mm]), X[mm * 32 + cc]));
+        }
+        __syncthreads();
+      }
+    }
+    int nf = 0;
+    for (int idx = tid; idx < W * 32; idx += blockDim.x) {
+      const int s = idx / 32, cc = idx % 32, c = c0 + cc;
+      if (c < cend) {
+        F v = store_rn<F>(X[s * 32 + cc]);
+        A[(size_t)(k + s) * lda + c] = v;
+        if (right && !isfinite((double)to_f(v))) nf = 1;
+      }
+    }
+    if (right && a.Ut != nullptr) {
+      F* Ut = (F*)a.Ut;
+      for (int idx = tid; idx < W * 32; idx += blockDim.x) {
+        const int cc = idx / W, s = idx % W, c = c0 + cc;
+        if (c < cend) Ut[(size_t)(c - k - W) * a.ldut + s] = store_rn<F>(X[s * 32 + cc]);
+      }
+    }
+    if (nf) s_nf = 1;
+    __syncthreads();
+  }
+  if (s_nf) atomicExch(a.nonfinite, 1);
+}
+
+// ------------------------------------------------------- SIMT update
+
+template <typename F>
+__global__ void __launch_bounds__(256) lu_update_simt(UpdateArgs a) {
+  using T = typename Fmt<F>::T;
+  F* A = (F*)a.A;
+  const int lda = a.lda, k = a.k, W = a.W;
+  const int r0 = k + W, M = a.n - r0;
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 1];
+  __shared__ T Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int tm = blockIdx.y * BM, tn = blockIdx.x * BN;
+  const int ty = tid / 16, tx = tid % 16;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int kc = 0; kc < W; kc += BK) {
+    for (int idx = tid; idx < BM * BK; idx += 256) {
+      const int i = idx / BK, kq = idx % BK;
+      const int row = tm + i, kk = kc + kq;
+      As[kq][i] = (row < M && kk < W) ? (T)to_f(A[(size_t)(r0 + row) * lda + k + kk]) : (T)0;
+    }
+    for (int idx = tid; idx < BK * BN; idx += 256) {
+      const int kq = idx / BN, j = idx % BN;
+      const int col = tn + j, kk = kc + kq;
+      Bs[kq][j] = (col < M && kk < W) ? (T)to_f(A[(size_t)(k + kk) * lda + r0 + col]) : (T)0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kq = 0; kq < BK; ++kq) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kq][ty * 4 + i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kq][tx * 4 + j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma_rn(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = tm + ty * 4 + i;
+    if (row >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int col = tn + tx * 4 + j;
+      if (col >= M) continue;
+      F* p = A + (size_t)(r0 + row) * lda + r0 + col;
+      *p = store_rn<F>(sub_rn((T)to_f(*p), acc[i][j]));
+    }
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+size_t panel_smem_bytes(int fmt, int R_cap, int nb, int W) {
+  const size_t ts = fmt == MSIR_FP64 ? 8 : 4;
+  const int NBM = fmt == MSIR_FP64 ? 16 : 32;
+  size_t b = ts * ((size_t)R_cap * (nb + 1) + 2 * 16 * NBM + 2 * NBM + NBM * NBM + (size_t)NBM * W);
+  b = (b + 7) & ~(size_t)7;
+  b += 32 * sizeof(double) + 32 * sizeof(int) + NBM * sizeof(int) + 4 * NBM * sizeof(int) +
+       4 * (size_t)W * sizeof(int);
+  return b;
+}
+
+size_t swap_trsm_smem_bytes(int fmt, int W) {
+  const size_t ts = fmt == MSIR_FP64 ? 8 : 4;
+  const size_t fs = fmt == MSIR_FP64 ? 8 : fmt == MSIR_FP32 ? 4 : 2;
+  size_t off = ts * (size_t)W * 32 + fs * ((size_t)W * W + (size_t)W * 32);
+  off = (off + 15) & ~(size_t)15;
+  return off + 4 * (size_t)W * sizeof(int);
+}
+
+template <typename F>
+static cudaError_t launch_panel_t(const PanelArgs& a, int C, cudaStream_t st) {
+  size_t smem = panel_smem_bytes(Fmt<F>::code, a.R_cap, a.nb, a.W);
+  cudaError_t e = cudaFuncSetAttribute(lu_outer_panel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(lu_outer_panel<F>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(kPanelThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, lu_outer_panel<F>, a);
+}
+
+cudaError_t launch_panel(int fmt, const PanelArgs& a, int C, cudaStream_t st) {
+  switch (fmt) {
+    case MSIR_FP16: return launch_panel_t<__half>(a, C, st);
+    case MSIR_BF16: return launch_panel_t<__nv_bfloat16>(a, C, st);
+    case MSIR_FP32: return launch_panel_t<float>(a, C, st);
+    case MSIR_FP64: return launch_panel_t<double>(a, C, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename F>
+static cudaError_t launch_swap_trsm_t(const SwapTrsmArgs& a, int grid, cudaStream_t st) {
+  size_t smem = swap_trsm_smem_bytes(Fmt<F>::code, a.W);
+  cudaError_t e = cudaFuncSetAttribute(lu_outer_swap_trsm<F>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  lu_outer_swap_trsm<F><<<grid, 256, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_swap_trsm(int fmt, const SwapTrsmArgs& a, int grid, cudaStream_t st) {
+  switch (fmt) {
+    case MSIR_FP16: return launch_swap_trsm_t<__half>(a, grid, st);
+    case MSIR_BF16: return launch_swap_trsm_t<__nv_bfloat16>(a, grid, st);
+    case MSIR_FP32: return launch_swap_trsm_t<float>(a, grid, st);
+    case MSIR_FP64: return launch_swap_trsm_t<double>(a, grid, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_update_simt(int fmt, const UpdateArgs& a, cudaStream_t st) {
+  const int M = a.n - a.k - a.W;
+  if (M <= 0) return cudaSuccess;
+  dim3 grid((M + 63) / 64, (M + 63) / 64);
+  switch (fmt) {
+    case MSIR_FP16: lu_update_simt<__half><<<grid, 256, 0, st>>>(a); break;
+    case MSIR_BF16: lu_update_simt<__nv_bfloat16><<<grid, 256, 0, st>>>(a); break;
+    case MSIR_FP32: lu_update_simt<float><<<grid, 256, 0, st>>>(a); break;
+    case MSIR_FP64: lu_update_simt<double><<<grid, 256, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace msir

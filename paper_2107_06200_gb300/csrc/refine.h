@@ -1,0 +1,103 @@
+// Arguments and state of the persistent refinement kernel (refine.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/msir.h"
+
+namespace msir {
+
+constexpr int kRefThreads = 256;  // 8 warps
+constexpr int kBlk = 64;          // rows per block of the row distribution / TRSV
+constexpr int kMaxKcap = 2048;    // GMRES iteration cap supported
+
+enum RefMode { MODE_SOLVE = 0, MODE_APPLY = 1, MODE_RESIDUAL = 2 };
+enum RefPhase {
+  PH_START = 0,      // compute x0, then refine
+  PH_ESCALATED = 1,  // factors replaced by a finer u_f: recompute r, start SIR
+  PH_DONE = 2,
+  PH_NEED_ESC = 3,   // GMRES-IR stage ended without convergence: host refactors
+  PH_ERROR = 4
+};
+
+// Controller state of Algorithm 4 kept on the device between launches.
+struct RefState {
+  int phase;
+  int alg, it;
+  int uf, u, ur;
+  int cged, status;
+  int have_phi0;
+  unsigned epoch;     // TRSV flag epoch
+  int nstages;
+  int total_steps, total_gmres;
+  double rho_max, delta_prev, phi0, phi;
+  double s, nbe, best_nbe;
+  double pad[4];
+};
+
+struct RefineArgs {
+  int mode;
+  int n;
+  int a_fmt;               // storage of A_u: MSIR_FP32 or MSIR_FP64
+  const void* A;           // A_u, row-major
+  int lda;
+  const double* b;         // b_u (values in u0)
+  const void* LU;          // packed factors in u_f storage, row-major
+  int ldf;
+  const int* perm;         // (P A)[i] = A[perm[i]]
+  const double* Rsc;       // squeezing row scalings (nullptr: none)
+  const double* Ssc;       // column scalings
+  double mu;
+  double normA, normb;
+  double* x;               // current iterate (values in u)
+  double* xn;              // next iterate
+  double* x0;
+  double* xbest;
+  double* r_hi;            // residual, permuted order: r_p[i] = r[perm[i]]
+  double* r_lo;
+  double* c_hi;            // TRSV right-hand side / work (permuted order)
+  double* c_lo;
+  double* y_hi;            // forward-substitution result
+  double* y_lo;
+  double* z_hi;            // backward-substitution result (natural order)
+  double* z_lo;
+  double* d;               // correction
+  double* w;               // GMRES work vector
+  double* V;               // Krylov basis: vector j at V + j*ldv
+  int ldv;
+  double* H;               // rotated Hessenberg, column-major (kcap+1) x kcap
+  double* yv;              // GMRES least-squares solution (kcap)
+  double* red;             // reduction scratch: 2 * gridDim.x * kRedW
+  double* hred;            // CGS partial sums: gridDim.x * (kcap+1)
+  double* hvec;            // reduced CGS coefficients (kcap+1)
+  unsigned* flags;         // TRSV block flags (ceil(n/kBlk))
+  unsigned* bar;           // grid barrier counter (zeroed before launch)
+  int* err;
+  RefState* st;
+  msir_report* rep;        // device copy of the report
+  // parameters of Algorithm 4
+  int i_max;
+  double rho_thresh;
+  double kmax;
+  int kcap;
+  double tau;              // <= 0: by u
+  double gamma;
+  int conv;
+  int allow_escalation;
+  int u0;
+  // MODE_APPLY: arith / store formats and input/output (natural order)
+  int ap_arith, ap_store;
+  const double* ap_in;
+  double* ap_out;
+  // MODE_RESIDUAL: output s
+  double* res_s;
+};
+
+constexpr int kRedW = 4;
+
+cudaError_t launch_refine(int a_fmt, int f_fmt, const RefineArgs& a, int grid, cudaStream_t st);
+int refine_max_grid(int a_fmt, int f_fmt, int kcap);
+size_t refine_smem_bytes(int kcap);
+
+}  // namespace msir

@@ -1,0 +1,8 @@
+// One instantiation of the persistent refinement kernel (A_u stored as
+// float, factors stored as float); split per file so the instantiations
+// compile in parallel.
+#include "refine_impl.cuh"
+
+namespace msir {
+template <> void* refine_entry<float, float>() { return (void*)refine_kernel<float, float>; }
+}  // namespace msir

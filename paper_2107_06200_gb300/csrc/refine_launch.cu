@@ -1,0 +1,68 @@
+// Dispatch of the persistent refinement kernel instantiations.
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+
+#include "refine.h"
+
+namespace msir {
+
+template <typename A0, typename F> void* refine_entry();
+
+constexpr int kDtLdL = kBlk + 1;
+
+// ---------------------------------------------------------- launchers
+
+size_t refine_smem_bytes(int kcap) {
+  return sizeof(double) * ((size_t)kBlk * kDtLdL + 3 * ((size_t)kcap + 2) + 2 * ((size_t)kcap + 1));
+}
+
+template <typename A0, typename F>
+static void* refine_fn() {
+  return refine_entry<A0, F>();
+}
+
+static void* pick(int a_fmt, int f_fmt) {
+  if (a_fmt == MSIR_FP32) {
+    switch (f_fmt) {
+      case MSIR_FP16: return refine_fn<float, __half>();
+      case MSIR_BF16: return refine_fn<float, __nv_bfloat16>();
+      case MSIR_FP32: return refine_fn<float, float>();
+      case MSIR_FP64: return refine_fn<float, double>();
+    }
+  } else {
+    switch (f_fmt) {
+      case MSIR_FP16: return refine_fn<double, __half>();
+      case MSIR_BF16: return refine_fn<double, __nv_bfloat16>();
+      case MSIR_FP32: return refine_fn<double, float>();
+      case MSIR_FP64: return refine_fn<double, double>();
+    }
+  }
+  return nullptr;
+}
+
+int refine_max_grid(int a_fmt, int f_fmt, int kcap) {
+  void* fn = pick(a_fmt, f_fmt);
+  if (!fn) return 0;
+  const size_t smem = refine_smem_bytes(kcap);
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int per_sm = 0, dev = 0, sms = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRefThreads, smem) != cudaSuccess)
+    return 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return per_sm * sms;
+}
+
+cudaError_t launch_refine(int a_fmt, int f_fmt, const RefineArgs& a, int grid, cudaStream_t st) {
+  void* fn = pick(a_fmt, f_fmt);
+  if (!fn) return cudaErrorInvalidValue;
+  const size_t smem = refine_smem_bytes(a.kcap);
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  RefineArgs copy = a;
+  void* params[] = {&copy};
+  return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kRefThreads), params, smem, st);
+}
+
+}  // namespace msir
