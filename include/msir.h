@@ -126,6 +126,11 @@ typedef struct {
   double phi;            /* last convergence estimate phi_i                  */
   double t_factor_ms;    /* device time in LU factorisations                 */
   double t_refine_ms;    /* device time in refinement                        */
+  double t_phase_ms[8];  /* refinement time by phase: residual, forward and
+                            backward substitution, Gram-Schmidt, operator
+                            product, reductions, Givens; other               */
+  int n_launches;        /* kernels this library launched for the system     */
+  int n_refine_launches; /* of which persistent refinement launches          */
   msir_stage stage[MSIR_MAX_STAGES];
 } msir_report;
 
@@ -149,7 +154,10 @@ msir_status msir_destroy(msir_ctx* ctx);
  * first step).  The factor object is owned by the library.  On success
  * *info receives the first exactly-zero pivot (1-based) or 0, and
  * *nonfinite 1 if L or U contain Inf or NaN (neither is an error here).
- * u must be FP32 or FP64, uf one of BF16/FP16/FP32/FP64 not finer than u. */
+ * u must be FP32 or FP64, uf one of BF16/FP16/FP32/FP64 (a u_f finer than u
+ * is what Algorithm 4 uses after raising u_f while u0 stays, e.g. fp64
+ * factors of fl_fp32(A)).  nb / nbo of params select the blocking (0: the
+ * library defaults for uf). */
 msir_status msir_factor(msir_ctx* ctx, int n, const double* A_dev, int lda, int u, int uf,
                         const msir_params* params, msir_factors** out, int* info,
                         int* nonfinite);

@@ -47,23 +47,25 @@ def _argmax_abs(col):
 
 
 def default_blocking(fmt_f):
-    """Default (nb, nbo): inner panel width and outer block width.
+    """Default (nb, nbo): inner panel width and outer block width (the same
+    defaults as the GPU library, which reports the values it used).
 
     The panel is held in the arithmetic precision while it is factored, so it
     is narrower when that precision is fp64."""
-    if fmt_f in (BF16, FP16):
-        return 32, 256
-    if fmt_f == FP32:
-        return 32, 128
-    return 16, 64
+    if fmt_f == FP64:
+        return 16, 64
+    return 32, 64
 
 
-def _panel(F, kk, w, T, fmt_f, ipiv):
+def _panel(F, kk, w, T, fmt_f, ipiv, trace=None):
     """Factor the (n-kk) x w panel at column kk in T; store fl_f.  Returns the
-    first zero-pivot column (1-based) or 0."""
+    first zero-pivot column (1-based) or 0.  If ``trace`` is a list, the
+    candidate magnitudes of every column are appended (for tests)."""
     info = 0
     P = F[kk:, kk:kk + w].astype(T)
     for j in range(w):
+        if trace is not None:
+            trace.append(np.abs(P[j:, j]).astype(np.float64))
         p = j + _argmax_abs(P[j:, j])
         ipiv[kk + j] = kk + p
         if p != j:
@@ -115,7 +117,7 @@ def _update(F, r0, w, c0, c1, fmt_f):
         F[r0 + w:, c0:c1] = fl(upd.astype(np.float32), fmt_f).astype(np.float64)
 
 
-def lu_factor(A, fmt_f, nb=None, nbo=None):
+def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None):
     """Factor A (float32/float64 array of working-precision values).
 
     Two-level right-looking blocking: outer blocks of nbo columns, each
@@ -144,7 +146,7 @@ def lu_factor(A, fmt_f, nb=None, nbo=None):
             W = min(nbo, n - k)
             for kk in range(k, k + W, nb):
                 w = min(nb, k + W - kk)
-                i = _panel(F, kk, w, T, fmt_f, ipiv)
+                i = _panel(F, kk, w, T, fmt_f, ipiv, trace)
                 info = info or i
                 _swap_cols(F, ipiv, kk, w, k, kk)
                 _swap_cols(F, ipiv, kk, w, kk + w, k + W)

@@ -229,8 +229,12 @@ class Controller:
         return esc
 
 
-def msir(A_in, b_in, triple, params=None, x_ref=None):
-    """Run Algorithm 4 on (A_in, b_in) with initial precisions triple=(uf,u,ur)."""
+def msir(A_in, b_in, triple, params=None, x_ref=None, factor_hook=None):
+    """Run Algorithm 4 on (A_in, b_in) with initial precisions triple=(uf,u,ur).
+
+    ``factor_hook(fmt)`` (tests only) may return a Factorization to use
+    instead of factoring in format fmt, e.g. factors produced elsewhere, so
+    that the refinement can be compared on identical factors."""
     p = params or Params()
     uf, u, ur = triple
     if ur != square_of(u):
@@ -256,6 +260,10 @@ def msir(A_in, b_in, triple, params=None, x_ref=None):
         nonlocal nfact
         while fmt is not None:
             nfact += 1
+            hooked = factor_hook(fmt) if factor_hook is not None else None
+            if hooked is not None:
+                scaled_flags.append(False)
+                return hooked
             fac, sc = factorize(A_u.astype(arith_dtype(u0)), fmt, p.nb, p.nbo)
             scaled_flags.append(sc)
             if fac is not None:

@@ -17,8 +17,8 @@ from ._lib import (BF16, FP16, FP32, FP64, DD, CONV_COMBINED, CONV_EST, ALG_NAME
 
 _L = _lib.load()
 
-__all__ = ["Context", "triple", "params_default", "report_to_dict", "stage_string", "BF16",
-           "FP16", "FP32", "FP64", "DD", "lib_path"]
+__all__ = ["Context", "Server", "MsirError", "triple", "params_default", "report_to_dict",
+           "stage_string", "BF16", "FP16", "FP32", "FP64", "DD", "lib_path"]
 
 
 def lib_path():
@@ -93,7 +93,9 @@ def report_to_dict(r):
                 n_factorizations=r.n_factorizations, scaled=bool(r.scaled), lu_info=r.lu_info,
                 nb=r.nb, nbo=r.nbo, total_steps=r.total_steps,
                 total_gmres_iters=r.total_gmres_iters, nbe=r.nbe, phi=r.phi,
-                t_factor_ms=r.t_factor_ms, t_refine_ms=r.t_refine_ms, stages=stages,
+                t_factor_ms=r.t_factor_ms, t_refine_ms=r.t_refine_ms,
+                t_phase_ms=[r.t_phase_ms[i] for i in range(8)], n_launches=r.n_launches,
+                n_refine_launches=r.n_refine_launches, stages=stages,
                 steps=stage_string(stages))
 
 

@@ -52,7 +52,8 @@ class Report(ctypes.Structure):
                 ("total_steps", ctypes.c_int), ("total_gmres_iters", ctypes.c_int),
                 ("nbe", ctypes.c_double), ("phi", ctypes.c_double),
                 ("t_factor_ms", ctypes.c_double), ("t_refine_ms", ctypes.c_double),
-                ("stage", Stage * MAX_STAGES)]
+                ("t_phase_ms", ctypes.c_double * 8), ("n_launches", ctypes.c_int),
+                ("n_refine_launches", ctypes.c_int), ("stage", Stage * MAX_STAGES)]
 
 
 def load(path=LIB_PATH):

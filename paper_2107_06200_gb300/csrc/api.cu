@@ -19,6 +19,8 @@
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -88,10 +90,13 @@ static bool valid_triple(msir_triple t) {
   return true;
 }
 
+// Default LU blocking (numeric parameters, reported back): panels of nb
+// columns inside outer blocks of nbo columns.  The outer update runs on the
+// tensor cores (bf16/fp16) or as a SIMT GEMM; the inner updates run inside
+// the panel kernel, so nbo is kept small.
 static void default_blocking(int fmt, int* nb, int* nbo) {
-  if (fmt == MSIR_BF16 || fmt == MSIR_FP16) { *nb = 32; *nbo = 256; }
-  else if (fmt == MSIR_FP32) { *nb = 32; *nbo = 128; }
-  else { *nb = 16; *nbo = 64; }
+  if (fmt == MSIR_FP64) { *nb = 16; *nbo = 64; }
+  else { *nb = 32; *nbo = 64; }
 }
 
 // ------------------------------------------------------------ TMA maps
@@ -187,6 +192,7 @@ struct Workspace {
   RefState* st = nullptr;
   msir_report* rep = nullptr;
   int* ident = nullptr;
+  unsigned long long* tsv = nullptr;
 };
 
 static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_level, char* base) {
@@ -215,7 +221,7 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
   }
   w.Ut = take((size_t)n * 256 * 2);
   w.map = (int*)take((4 * 256 + 8) * 4);
-  w.iflags = (int*)take(16 * 4);
+  w.iflags = (int*)take(32 * 4);
   double** vecs[] = {&w.x, &w.xn, &w.x0, &w.xbest, &w.r_hi, &w.r_lo, &w.c_hi,
                      &w.c_lo, &w.y_hi, &w.y_lo, &w.z_hi, &w.z_lo, &w.d, &w.w};
   for (double** v : vecs) *v = (double*)take(n * 8);
@@ -226,11 +232,12 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
   w.red = (double*)take((size_t)2 * G * kRedW * 8);
   w.hred = (double*)take((size_t)G * (kcap + 1) * 8);
   w.hvec = (double*)take((size_t)(kcap + 1) * 8);
-  w.flags = (unsigned*)take(((size_t)(n + kBlk - 1) / kBlk + 1) * 4);
+  w.flags = (unsigned*)take(((size_t)(n + kBlk - 1) / kBlk + 1) * kFlagStride * 4);
   w.bar = (unsigned*)take(64);
   w.st = (RefState*)take(sizeof(RefState));
   w.rep = (msir_report*)take(sizeof(msir_report));
   w.ident = (int*)take(n * 4);
+  w.tsv = (unsigned long long*)take(((size_t)(n + kBlk - 1) / kBlk) * 6 * 8);
   return off + 256;
 }
 
@@ -239,10 +246,13 @@ static int kcap_of(int n, double kmax_frac) {
   return std::max(1, std::min(k, kMaxKcap));
 }
 
-// grid of the refinement kernel for size n
+// Grid of the refinement kernel for size n: one CTA per 64-row block for
+// the substitution wavefronts, and enough CTAs that the O(n^2) fp64 work
+// (residual, u^2 operator) is spread over the SMs; never more than the SMs.
 static int refine_grid(msir_ctx* ctx, int n, int share) {
   const int nblk = (n + kBlk - 1) / kBlk;
-  int g = std::min(nblk, ctx->num_sms);
+  const long long work = ((long long)n * n + 16383) / 16384;
+  int g = (int)std::min<long long>(ctx->num_sms, std::max<long long>(nblk, work));
   if (share > 1) g = std::max(1, std::min(g, ctx->num_sms / share));
   return g;
 }
@@ -277,10 +287,23 @@ static size_t ws_bytes_for(int n, int kcap, int G) {
 
 // ------------------------------------------------------------ LU driver
 
+static bool trsv_timers_enabled();
+
+// MSIR_LU_TIMERS=1: the panel kernel accumulates section timers that the
+// factor call prints to stderr (diagnostics only).
+static bool lu_timers_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("MSIR_LU_TIMERS");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
 // Enqueue the LU of fl_fmt(A_u) (optionally squeezed) into level slot l.
 // The host reads info / nonfinite after the stream reaches the end.
 static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l, int fmt, int nb,
-                              int nbo, bool squeeze, Level& L, cudaStream_t st) {
+                              int nbo, bool squeeze, Level& L, cudaStream_t st, int* launches) {
   const int ldf = w.ldu;
   L = Level();
   L.fmt = fmt;
@@ -294,6 +317,7 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
   const double* S = nullptr;
   if (squeeze) {
     CK(squeeze_scalings(w.Au, w.ldu, n, u0, w.rowmax, w.R[l], w.colmax, w.S[l], st));
+    *launches += 4;
     R = w.R[l];
     S = w.S[l];
     L.R = w.R[l];
@@ -302,7 +326,8 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
     L.scaled = 1;
   }
   CK(make_factor_matrix(w.Au, w.ldu, n, u0, fmt, L.F, ldf, R, S, L.mu, st));
-  CK(cudaMemsetAsync(w.iflags, 0, 16 * sizeof(int), st));
+  *launches += 1;
+  CK(cudaMemsetAsync(w.iflags, 0, 32 * sizeof(int), st));
   const bool tc = fmt == MSIR_FP16 || fmt == MSIR_BF16;
   CUtensorMap tmA, tmB;
   if (tc && n > nbo) {
@@ -335,7 +360,9 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
     pa.map_pos = w.map;
     pa.map_val = w.map + 2 * nbo;
     pa.map_cnt = w.map + 4 * nbo;
+    pa.tdbg = lu_timers_enabled() ? (unsigned long long*)(w.iflags + 8) : nullptr;
     CK(launch_panel(fmt, pa, C, st));
+    *launches += 1;
     const int nright = n - k - W;
     if (k > 0 || nright > 0) {
       SwapTrsmArgs sa;
@@ -352,6 +379,7 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
       sa.nonfinite = w.iflags + 1;
       const int tiles = (k + 31) / 32 + (nright + 31) / 32;
       CK(launch_swap_trsm(fmt, sa, std::max(1, std::min(tiles, ctx->num_sms)), st));
+      *launches += 1;
     }
     if (nright > 0) {
       if (tc) {
@@ -365,6 +393,7 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
         ta.K = W;
         ta.err = w.iflags + 2;
         CK(launch_update_tc(fmt, &tmA, &tmB, ta, ctx->num_sms, st));
+        *launches += 1;
       } else {
         UpdateArgs ua;
         ua.A = L.F;
@@ -373,10 +402,12 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
         ua.k = k;
         ua.W = W;
         CK(launch_update_simt(fmt, ua, st));
+        *launches += 1;
       }
     }
   }
   CK(ipiv_to_perm(L.ipiv, n, L.perm, st));
+  *launches += 1;
   return MSIR_OK;
 }
 
@@ -420,6 +451,7 @@ struct Slot {
   float t_factor = 0, t_refine = 0;
   bool factoring_initial = true;
   int nfact = 0;
+  int launches = 0, refine_launches = 0;
   RefState state{};
 };
 
@@ -497,6 +529,7 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   a.d = w.d; a.w = w.w; a.V = w.V; a.ldv = w.ldv;
   a.H = w.H; a.yv = w.yv; a.red = w.red; a.hred = w.hred; a.hvec = w.hvec;
   a.flags = w.flags; a.bar = w.bar; a.err = w.iflags + 2; a.st = w.st; a.rep = w.rep;
+  a.tsv = trsv_timers_enabled() ? w.tsv : nullptr;
   a.i_max = j.p.i_max;
   a.rho_thresh = j.p.rho_thresh;
   a.kmax = j.p.kmax_frac * j.n;
@@ -510,6 +543,56 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
 }
 
 // Enqueue one factorisation attempt of the slot's current job.
+// MSIR_TRSV_TIMERS=1: per-block timestamps of the last substitution pair of
+// each refinement launch, summarised on stderr (diagnostics only).
+static bool trsv_timers_enabled() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("MSIR_TRSV_TIMERS");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  return v == 1;
+}
+
+static void print_trsv_timers(Slot& s) {
+  if (!trsv_timers_enabled() || !s.job) return;
+  const int nblk = (s.job->n + kBlk - 1) / kBlk;
+  std::vector<unsigned long long> t((size_t)nblk * 6);
+  cudaStreamSynchronize(s.st);
+  cudaMemcpy(t.data(), s.w.tsv, t.size() * 8, cudaMemcpyDeviceToHost);
+  for (int dir = 0; dir < 2; ++dir) {
+    unsigned long long t0 = ~0ull, t1 = 0;
+    double off = 0, diag = 0, offmax = 0, diagmax = 0, gap = 0;
+    int ngap = 0;
+    for (int b = 0; b < nblk; ++b) {
+      const unsigned long long* q = &t[((size_t)dir * nblk + b) * 3];
+      t0 = std::min(t0, q[0]);
+      t1 = std::max(t1, q[2]);
+      off += (double)(q[1] - q[0]);
+      diag += (double)(q[2] - q[1]);
+      offmax = std::max(offmax, (double)(q[1] - q[0]));
+      diagmax = std::max(diagmax, (double)(q[2] - q[1]));
+      const int pb = dir ? b + 1 : b - 1;  // the block this one waits for last
+      if (pb >= 0 && pb < nblk) {
+        const unsigned long long* pq = &t[((size_t)dir * nblk + pb) * 3];
+        if (q[1] > pq[2]) { gap += (double)(q[1] - pq[2]); ++ngap; }
+      }
+    }
+    fprintf(stderr, "[msir trsv %s] blocks %d span %.1f us, per block: offdiag avg %.2f max %.2f us, diag avg %.2f max %.2f us, publish->next offdiag done %.2f us\n",
+            dir ? "upper" : "lower", nblk, (t1 - t0) * 1e-3, off / nblk * 1e-3, offmax * 1e-3,
+            diag / nblk * 1e-3, diagmax * 1e-3, ngap ? gap / ngap * 1e-3 : 0.0);
+  }
+}
+
+static void print_lu_timers(Slot& s) {
+  if (!lu_timers_enabled()) return;
+  unsigned long long t[8];
+  cudaStreamSynchronize(s.st);
+  cudaMemcpy(t, s.w.iflags + 8, sizeof(t), cudaMemcpyDeviceToHost);
+  fprintf(stderr, "[msir lu timers ms] colloop %.3f clsync %.3f pivot+push %.3f update %.3f store+maps %.3f inner_swap_trsm %.3f inner_update %.3f load %.3f\n",
+          t[0] * 1e-6, t[1] * 1e-6, t[2] * 1e-6, t[3] * 1e-6, t[4] * 1e-6, t[5] * 1e-6, t[6] * 1e-6, t[7] * 1e-6);
+}
+
 static msir_status slot_enqueue_factor(msir_ctx* ctx, Slot& s, int fmt, bool squeeze) {
   Job& j = *s.job;
   int nb = j.p.nb, nbo = j.p.nbo;
@@ -525,7 +608,8 @@ static msir_status slot_enqueue_factor(msir_ctx* ctx, Slot& s, int fmt, bool squ
   s.try_level = level_index(fmt);
   s.nfact += squeeze ? 0 : 1;
   CK(cudaEventRecord(s.e0, s.st));
-  msir_status r = enqueue_lu(ctx, s.w, j.n, s.u0, s.try_level, fmt, nb, nbo, squeeze, s.lv[s.try_level], s.st);
+  msir_status r = enqueue_lu(ctx, s.w, j.n, s.u0, s.try_level, fmt, nb, nbo, squeeze, s.lv[s.try_level], s.st,
+                             &s.launches);
   if (r != MSIR_OK) return r;
   CK(cudaMemcpyAsync(s.h_flags, s.w.iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, s.st));
   CK(cudaEventRecord(s.e1, s.st));
@@ -541,6 +625,8 @@ static msir_status slot_enqueue_refine(msir_ctx* ctx, Slot& s) {
   CK(cudaMemsetAsync(s.w.bar, 0, 64, s.st));
   CK(cudaEventRecord(s.e0, s.st));
   CK(launch_refine(s.u0, s.lv[s.cur].fmt, a, s.G, s.st));
+  s.launches += 1;
+  s.refine_launches += 1;
   CK(cudaEventRecord(s.e1, s.st));
   CK(cudaMemcpyAsync(s.h_state, s.w.st, sizeof(RefState), cudaMemcpyDeviceToHost, s.st));
   CK(cudaMemcpyAsync(s.h_rep, s.w.rep, sizeof(msir_report), cudaMemcpyDeviceToHost, s.st));
@@ -571,6 +657,8 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
   if (r != MSIR_OK) return r;
   s.t_factor = s.t_refine = 0;
   s.nfact = 0;
+  s.launches = 0;
+  s.refine_launches = 0;
   memset(&j.rep, 0, sizeof(j.rep));
   const bool same = j.matrix_id != 0 && j.matrix_id == s.loaded_id;
   if (!same) {
@@ -580,9 +668,11 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
     CK(max_abs(s.w.rowsum, j.n, 0, s.w.scal + 0, s.st));
     CK(iota(s.w.ident, j.n, s.st));
     s.loaded_id = j.matrix_id;
+    s.launches += 4;
   }
   CK(round_vec(j.b, j.n, s.u0, s.w.b_u, s.st));
   CK(max_abs(s.w.b_u, j.n, 1, s.w.scal + 1, s.st));
+  s.launches += 2;
   double hs[2];
   CK(cudaMemcpyAsync(hs, s.w.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s.st));
   CK(cudaStreamSynchronize(s.st));
@@ -595,7 +685,7 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
   s.state.ur = j.t.ur;
   s.state.delta_prev = INFINITY;
   CK(cudaMemsetAsync(s.w.rep, 0, sizeof(msir_report), s.st));
-  CK(cudaMemsetAsync(s.w.flags, 0, ((size_t)(j.n + kBlk - 1) / kBlk + 1) * 4, s.st));
+  CK(cudaMemsetAsync(s.w.flags, 0, ((size_t)(j.n + kBlk - 1) / kBlk + 1) * kFlagStride * 4, s.st));
   s.factoring_initial = true;
   const int li = level_index(j.t.uf);
   if (same && s.lv[li].valid && s.lv[li].fmt == j.t.uf) {
@@ -623,6 +713,12 @@ static void fill_report(Slot& s) {
   R.phi = s.h_state->phi;
   R.t_factor_ms = s.t_factor;
   R.t_refine_ms = s.t_refine;
+  R.n_launches = s.launches;
+  R.n_refine_launches = s.refine_launches;
+  for (int i = 0; i < 7; ++i) R.t_phase_ms[i] = 1e-6 * (double)s.h_state->t_ns[i];
+  double acc = 0;
+  for (int i = 0; i < 7; ++i) acc += R.t_phase_ms[i];
+  R.t_phase_ms[7] = std::max(0.0, R.t_refine_ms - acc);
 }
 
 // Advance a slot whose event has completed.  Returns true when its job is done.
@@ -632,6 +728,7 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
   if (s.step == S_FACTOR) {
     cudaEventElapsedTime(&ms, s.e0, s.e1);
     s.t_factor += ms;
+    print_lu_timers(s);
     Level& L = s.lv[s.try_level];
     L.info = s.h_flags[0];
     L.nonfinite = s.h_flags[1];
@@ -671,6 +768,7 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
   if (s.step == S_REFINE) {
     cudaEventElapsedTime(&ms, s.e0, s.e1);
     s.t_refine += ms;
+    print_trsv_timers(s);
     s.state = *s.h_state;
     const int err = s.h_flags[2];
     if (err || s.state.phase == PH_ERROR) { slot_finish(s, err ? err : MSIR_ERR_TIMEOUT); return false; }
@@ -844,8 +942,8 @@ struct msir_factors {
 msir_status msir_factor(msir_ctx* ctx, int n, const double* A_dev, int lda, int u, int uf,
                         const msir_params* params, msir_factors** out, int* info, int* nonfinite) {
   if (!ctx || !out || n <= 0 || lda < n || !A_dev) return MSIR_ERR_INVALID;
+  if ((u != MSIR_FP32 && u != MSIR_FP64) || uf < MSIR_BF16 || uf > MSIR_FP64) return MSIR_ERR_INVALID;
   msir_triple t{uf, u, u == MSIR_FP32 ? MSIR_FP64 : MSIR_DD};
-  if (!valid_triple(t)) return MSIR_ERR_INVALID;
   msir_params p = resolve_params(params);
   if (!valid_params(p)) return MSIR_ERR_INVALID;
   CK(cudaSetDevice(ctx->device));
@@ -866,6 +964,7 @@ msir_status msir_factor(msir_ctx* ctx, int n, const double* A_dev, int lda, int 
   if (r == MSIR_OK) r = cuda_status(ingest_matrix(A_dev, lda, n, u, s.w.Au, s.w.ldu, s.st));
   if (r == MSIR_OK) r = slot_enqueue_factor(ctx, s, uf, false);
   if (r == MSIR_OK) r = cuda_status(cudaStreamSynchronize(s.st));
+  if (r == MSIR_OK) print_lu_timers(s);
   if (r != MSIR_OK) { slot_destroy(s); delete f; return r; }
   Level& L = s.lv[s.try_level];
   L.info = s.h_flags[0];
@@ -952,7 +1051,7 @@ msir_status msir_factors_apply(msir_ctx* ctx, const msir_factors* fc, int nrhs, 
   if (arith != MSIR_DD && (store < MSIR_BF16 || store > MSIR_FP64)) return MSIR_ERR_INVALID;
   CK(cudaSetDevice(ctx->device));
   Slot& s = const_cast<Slot&>(fc->slot);
-  CK(cudaMemsetAsync(s.w.flags, 0, ((size_t)(n + kBlk - 1) / kBlk + 1) * 4, s.st));
+  CK(cudaMemsetAsync(s.w.flags, 0, ((size_t)(n + kBlk - 1) / kBlk + 1) * kFlagStride * 4, s.st));
   RefState st0;
   memset(&st0, 0, sizeof(st0));
   for (int c = 0; c < nrhs; ++c) {

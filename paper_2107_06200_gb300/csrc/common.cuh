@@ -170,6 +170,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned
     unsigned long long t0 = gtimer();
     unsigned spins = 0;
     while ((int)(ld_acquire_u32(count) - target) < 0) {
+      __nanosleep(20);
       if ((++spins & 63u) == 0u) {
         if (ld_volatile_i32(err) != 0) { ok = 0; break; }
         if (gtimer() - t0 > kWaitTimeoutNs) {
@@ -185,21 +186,34 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned
   return s_ok != 0;
 }
 
-// Spin (all lanes of the calling warp) until *flag >= epoch.  Bounded.
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Wait until *flag >= epoch.  Called by a whole warp: lane 0 polls with
+// acquire loads; the warp barrier then orders the other lanes' later loads
+// after the producer's release.  Bounded: returns false after recording
+// MSIR_ERR_TIMEOUT or another block's error.
 __device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned epoch, int* err) {
-  unsigned long long t0 = 0;
-  unsigned spins = 0;
-  while ((int)(ld_acquire_u32(flag) - epoch) < 0) {
-    if ((++spins & 255u) == 0u) {
-      if (t0 == 0) t0 = gtimer();
-      if (ld_volatile_i32(err) != 0) return false;
-      if (gtimer() - t0 > kWaitTimeoutNs) {
-        atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
-        return false;
+  int ok = 1;
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long t0 = 0;
+    unsigned spins = 0;
+    while ((int)(ld_acquire_u32(flag) - epoch) < 0) {
+      if ((++spins & 1023u) == 0u) {
+        if (t0 == 0) t0 = gtimer();
+        if (ld_volatile_i32(err) != 0) { ok = 0; break; }
+        if (gtimer() - t0 > kWaitTimeoutNs) {
+          atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
+          ok = 0;
+          break;
+        }
       }
     }
   }
-  return true;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 // ------------------------------------------------------------ reductions

@@ -106,18 +106,26 @@ __global__ void copy_strided_kernel(const double* src, int n, double* dst) {
   if (i < n) dst[i] = src[i];
 }
 
+// The interchanges are sequential by nature: one thread applies them to a
+// permutation held in shared memory (the block stages ipiv and perm).
 __global__ void ipiv_to_perm_kernel(const int* ipiv, int n, int* perm) {
-  // sequential by nature; one thread (n <= a few 10^4, once per factorisation)
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  for (int i = 0; i < n; ++i) perm[i] = i;
-  for (int j = 0; j < n; ++j) {
-    const int p = ipiv[j];
-    if (p != j) {
-      const int t = perm[j];
-      perm[j] = perm[p];
-      perm[p] = t;
+  extern __shared__ int sm[];
+  int* sp = sm;
+  int* si = sm + n;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) { sp[i] = i; si[i] = ipiv[i]; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < n; ++j) {
+      const int p = si[j];
+      if (p != j) {
+        const int t = sp[j];
+        sp[j] = sp[p];
+        sp[p] = t;
+      }
     }
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) perm[i] = sp[i];
 }
 
 __global__ void iota_kernel(int* p, int n) {
@@ -190,7 +198,11 @@ cudaError_t max_abs(const double* v, int n, int absval, double* out, cudaStream_
 }
 
 cudaError_t ipiv_to_perm(const int* ipiv, int n, int* perm, cudaStream_t st) {
-  ipiv_to_perm_kernel<<<1, 32, 0, st>>>(ipiv, n, perm);
+  const size_t smem = (size_t)2 * n * sizeof(int);
+  cudaError_t e = cudaFuncSetAttribute(ipiv_to_perm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  ipiv_to_perm_kernel<<<1, 1024, smem, st>>>(ipiv, n, perm);
   return cudaGetLastError();
 }
 

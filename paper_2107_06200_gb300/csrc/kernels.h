@@ -19,6 +19,7 @@ struct PanelArgs {
   int* map_pos;   // outer composite permutation (positions relative to k), 2W
   int* map_val;
   int* map_cnt;
+  unsigned long long* tdbg;  // optional section timers of rank 0 / thread 0 (ns), 8
 };
 
 // lu_outer_swap_trsm: interchanges of the outer block on the other columns,

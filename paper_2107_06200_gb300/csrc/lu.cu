@@ -58,12 +58,33 @@ template <typename T> struct PanelNB { static constexpr int v = 32; };
 template <> struct PanelNB<double> { static constexpr int v = 16; };
 
 // Pivot order: larger |a| first; NaN (mapped to -1) only if nothing else;
-// equal magnitudes -> smaller row index.
-__device__ __forceinline__ bool better(double av, int ai, double bv, int bi) {
+// equal magnitudes -> smaller row index.  Compared in the panel's own
+// arithmetic precision (fp64 instructions are scarce on this GPU).
+template <typename T>
+__device__ __forceinline__ bool better(T av, int ai, T bv, int bi) {
   return av > bv || (av == bv && ai < bi);
+}
+template <typename T>
+__device__ __forceinline__ void warp_argmax(T& v, int& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (better(ov, oi, v, i)) { v = ov; i = oi; }
+  }
 }
 
 // ------------------------------------------------------------------ panel
+
+// Optional section timers (rank 0, thread 0): 0 column loop, 1 cluster
+// barrier of the column loop, 2 pivot search + push, 3 rank-1 update,
+// 4 panel store + permutation maps, 5 inner interchanges + substitution,
+// 6 inner update, 7 panel load.
+#define PT_BEGIN(id) unsigned long long _t##id = (a.tdbg && rank == 0 && tid == 0) ? gtimer() : 0
+#define PT_END(id) \
+  if (a.tdbg && rank == 0 && tid == 0) a.tdbg[id] += gtimer() - _t##id
+
+constexpr int kInnerRows = 8;   // rows per warp step of the inner update
 
 template <typename F>
 __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) {
@@ -83,19 +104,19 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
   T* P = (T*)smem_raw;                                        // R_cap x ldp
   T* cand_row = P + (size_t)a.R_cap * ldp;                    // [2][16][NBM]
   T* jrow = cand_row + 2 * 16 * NBM;                          // [2][NBM]
-  T* L11 = jrow + 2 * NBM;                                    // NBM x NBM
-  T* U12 = L11 + NBM * NBM;                                   // NBM x W
+  T* L11t = jrow + 2 * NBM;                                   // NBM x NBM, transposed
+  T* U12 = L11t + NBM * NBM;                                  // NBM x W
+  T* cand_v = U12 + (size_t)NBM * W;                          // [2][16]
   size_t off = sizeof(T) * ((size_t)a.R_cap * ldp + 2 * 16 * NBM + 2 * NBM + NBM * NBM +
-                            (size_t)NBM * W);
+                            (size_t)NBM * W + 32);
   off = (off + 7) & ~(size_t)7;
-  double* cand_v = (double*)(smem_raw + off);                 // [2][16]
-  int* cand_i = (int*)(cand_v + 32);                          // [2][16]
+  int* cand_i = (int*)(smem_raw + off);                       // [2][16]
   int* s_piv = cand_i + 32;                                   // [NBM]
   int* mpos = s_piv + NBM;                                    // inner map positions [2*NBM]
   int* mval = mpos + 2 * NBM;                                 // inner map sources
   int* opos = mval + 2 * NBM;                                 // outer map (rank 0) [2*W]
   int* oval = opos + 2 * W;
-  __shared__ double s_wv[NW];
+  __shared__ T s_wv[NW];
   __shared__ int s_wi[NW];
   __shared__ int s_cnt, s_ocnt, s_nf;
 
@@ -110,68 +131,67 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
     const int my0 = rank * R;
     const int nloc = max(0, min(m, my0 + R) - my0);
 
+    PT_BEGIN(7);
     for (int li = tid; li < nloc; li += blockDim.x) {
       const F* src = A + (size_t)(kk + my0 + li) * lda + kk;
-      for (int c = 0; c < w; ++c) P[li * ldp + c] = (T)to_f(src[c]);
+      F v[NBM];
+#pragma unroll
+      for (int c = 0; c < NBM; ++c) v[c] = c < w ? src[c] : F(0);
+#pragma unroll
+      for (int c = 0; c < NBM; ++c)
+        if (c < w) P[li * ldp + c] = (T)to_f(v[c]);
     }
     __syncthreads();
+    PT_END(7);
 
+    PT_BEGIN(0);
     for (int j = 0; j < w; ++j) {
       const int buf = j & 1;
+      PT_BEGIN(2);
       // local pivot candidate among my rows with panel index >= j
-      double bv = -2.0;
+      T bv = (T)-2;
       int bi = INT_MAX;
       for (int li = tid; li < nloc; li += blockDim.x) {
         const int gi = my0 + li;
         if (gi >= j) {
-          double av = fabs((double)P[li * ldp + j]);
-          if (isnan(av)) av = -1.0;
+          T av = fabs(P[li * ldp + j]);
+          if (isnan(av)) av = (T)-1;
           if (better(av, gi, bv, bi)) { bv = av; bi = gi; }
         }
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, bv, o);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (better(ov, oi, bv, bi)) { bv = ov; bi = oi; }
-      }
+      warp_argmax(bv, bi);
       if (lane == 0) { s_wv[warp] = bv; s_wi[warp] = bi; }
       __syncthreads();
-      bv = s_wv[0];
-      bi = s_wi[0];
-      for (int q = 1; q < NW; ++q)
-        if (better(s_wv[q], s_wi[q], bv, bi)) { bv = s_wv[q]; bi = s_wi[q]; }
-      // push my candidate (value, index, row) and, if I own row j, row j
-      if (tid < C) {
-        double* rv = cl.map_shared_rank(cand_v, tid);
-        int* ri = cl.map_shared_rank(cand_i, tid);
-        rv[buf * 16 + rank] = bv;
-        ri[buf * 16 + rank] = bi;
-      }
-      const bool valid = bi != INT_MAX;
-      const int lb = bi - my0;
-      for (int idx = tid; idx < C * w; idx += blockDim.x) {
-        const int d = idx / w, c = idx % w;
-        T* rr = cl.map_shared_rank(cand_row, d);
-        rr[(buf * 16 + rank) * NBM + c] = valid ? P[lb * ldp + c] : (T)0;
-      }
       const int ownj = j / R;
-      if (ownj == rank) {
-        for (int idx = tid; idx < C * w; idx += blockDim.x) {
+      if (warp == 0) {
+        T v = lane < NW ? s_wv[lane] : (T)-2;
+        int i = lane < NW ? s_wi[lane] : INT_MAX;
+        warp_argmax(v, i);
+        // push (value, index) and the candidate row to every CTA
+        if (lane < C) {
+          cl.map_shared_rank(cand_v, lane)[buf * 16 + rank] = v;
+          cl.map_shared_rank(cand_i, lane)[buf * 16 + rank] = i;
+        }
+        const bool valid = i != INT_MAX;
+        const int lb = i - my0;
+        for (int idx = lane; idx < C * w; idx += 32) {
           const int d = idx / w, c = idx % w;
-          T* rj = cl.map_shared_rank(jrow, d);
-          rj[buf * NBM + c] = P[(j - my0) * ldp + c];
+          cl.map_shared_rank(cand_row, d)[(buf * 16 + rank) * NBM + c] = valid ? P[lb * ldp + c] : (T)0;
+        }
+      } else if (warp == 1 && ownj == rank) {
+        for (int idx = lane; idx < C * w; idx += 32) {
+          const int d = idx / w, c = idx % w;
+          cl.map_shared_rank(jrow, d)[buf * NBM + c] = P[(j - my0) * ldp + c];
         }
       }
+      PT_END(2);
+      PT_BEGIN(1);
       cl.sync();
-      // every thread reduces the C candidates from local shared memory
-      double pv = cand_v[buf * 16];
-      int p = cand_i[buf * 16];
-      for (int q = 1; q < C; ++q) {
-        double qv = cand_v[buf * 16 + q];
-        int qi = cand_i[buf * 16 + q];
-        if (better(qv, qi, pv, p)) { pv = qv; p = qi; }
-      }
+      PT_END(1);
+      // every warp reduces the C candidates (lane q reads rank q's)
+      T pv = lane < C ? cand_v[buf * 16 + lane] : (T)-2;
+      int p = lane < C ? cand_i[buf * 16 + lane] : INT_MAX;
+      warp_argmax(pv, p);
       const int ownp = p / R;
       const T* prow = cand_row + (buf * 16 + ownp) * NBM;
       const T* jr = jrow + buf * NBM;
@@ -181,6 +201,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
       }
       if (tid == 0) s_piv[j] = p;
       __syncthreads();
+      PT_BEGIN(3);
       const T piv = prow[j];
       if (piv != (T)0) {
         for (int li = tid; li < nloc; li += blockDim.x) {
@@ -189,23 +210,29 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
             T* row = P + li * ldp;
             const T l = div_rn(row[j], piv);
             row[j] = l;
-            for (int c = j + 1; c < w; ++c) row[c] = sub_rn(row[c], mul_rn(l, prow[c]));
+#pragma unroll
+            for (int c = 1; c < NBM; ++c)
+              if (c > j && c < w) row[c] = sub_rn(row[c], mul_rn(l, prow[c]));
           }
         }
       } else if (rank == 0 && tid == 0) {
         atomicCAS(a.info, 0, kk + j + 1);
       }
       __syncthreads();
+      PT_END(3);
     }
+    PT_END(0);
 
-    // store the panel (rounded to F) and its pivots
+    // round the panel to F in place, store it, and record its pivots
+    PT_BEGIN(4);
     int nf = 0;
     for (int li = tid; li < nloc; li += blockDim.x) {
       F* dst = A + (size_t)(kk + my0 + li) * lda + kk;
       for (int c = 0; c < w; ++c) {
-        F v = store_rn<F>(P[li * ldp + c]);
+        const F v = store_rn<F>(P[li * ldp + c]);
         dst[c] = v;
-        if (!isfinite((double)to_f(v))) nf = 1;
+        P[li * ldp + c] = (T)to_f(v);
+        if (!isfinite(to_f(v))) nf = 1;
       }
     }
     if (nf) s_nf = 1;
@@ -224,7 +251,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
         if (q < w) {
           sq = q;
         } else {
-          int cnt = s_cnt;
+          const int cnt = s_cnt;
           unsigned hit = __ballot_sync(0xffffffffu, lane + w < cnt && mpos[lane + w] == q);
           if (hit) {
             sq = w + __ffs(hit) - 1;
@@ -235,7 +262,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
           __syncwarp();
         }
         if (lane == 0 && sq != j) {
-          int t = mval[j];
+          const int t = mval[j];
           mval[j] = mval[sq];
           mval[sq] = t;
         }
@@ -249,7 +276,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
           if (pb < W) {
             sb = pb;
           } else {
-            int cnt = s_ocnt;
+            const int cnt = s_ocnt;
             int found = -1;
             for (int s0 = W; s0 < cnt; s0 += 32) {
               unsigned hit = __ballot_sync(0xffffffffu, s0 + lane < cnt && opos[s0 + lane] == pb);
@@ -263,7 +290,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
             __syncwarp();
           }
           if (lane == 0 && sb != pa) {
-            int t = oval[pa];
+            const int t = oval[pa];
             oval[pa] = oval[sb];
             oval[sb] = t;
           }
@@ -273,80 +300,85 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
     }
     __syncthreads();
     cl.sync();  // panel values visible to the whole cluster
+    PT_END(4);
+    PT_BEGIN(5);
 
     // inner interchanges on [k, kk) and [kk+w, k+W), then U12 = L11^{-1} A12
+    // for [kk+w, k+W): one warp per column
     const int nleft = kk - k, nright = k + W - kk - w;
     if (nright > 0) {
       for (int idx = tid; idx < w * w; idx += blockDim.x) {
-        const int i = idx / w, c = idx % w;
-        L11[i * NBM + c] = (T)to_f(A[(size_t)(kk + i) * lda + kk + c]);
+        const int i = idx / w, c = idx % w;  // L11t[c][i] = L[i][c]
+        L11t[c * NBM + i] = (T)to_f(A[(size_t)(kk + i) * lda + kk + c]);
       }
     }
     __syncthreads();
     const int cnt = s_cnt;
-    for (int g = rank * blockDim.x + tid; g < nleft + nright; g += C * blockDim.x) {
+    for (int g = rank * NW + warp; g < nleft + nright; g += C * NW) {
       const int c = g < nleft ? k + g : kk + w + (g - nleft);
-      T x[2 * NBM];
-#pragma unroll
-      for (int s = 0; s < 2 * NBM; ++s)
-        if (s < cnt) x[s] = (T)to_f(A[(size_t)(kk + mval[s]) * lda + c]);
-#pragma unroll
-      for (int s = 0; s < 2 * NBM; ++s)
-        if (s >= w && s < cnt) A[(size_t)(kk + mpos[s]) * lda + c] = store_rn<F>(x[s]);
+      // slots lane and lane + 32
+      T v0 = (T)0, v1 = (T)0;
+      if (lane < cnt) v0 = (T)to_f(A[(size_t)(kk + mval[lane]) * lda + c]);
+      if (lane + 32 < cnt) v1 = (T)to_f(A[(size_t)(kk + mval[lane + 32]) * lda + c]);
+      __syncwarp();
+      if (lane >= w && lane < cnt) A[(size_t)(kk + mpos[lane]) * lda + c] = store_rn<F>(v0);
+      if (lane + 32 >= w && lane + 32 < cnt) A[(size_t)(kk + mpos[lane + 32]) * lda + c] = store_rn<F>(v1);
       if (g < nleft) {
-#pragma unroll
-        for (int s = 0; s < NBM; ++s)
-          if (s < w) A[(size_t)(kk + s) * lda + c] = store_rn<F>(x[s]);
+        if (lane < w) A[(size_t)(kk + lane) * lda + c] = store_rn<F>(v0);
       } else {
-#pragma unroll
-        for (int mm = 0; mm < NBM - 1; ++mm) {
-          if (mm < w - 1) {
-#pragma unroll
-            for (int i = mm + 1; i < NBM; ++i)
-              if (i < w) x[i] = sub_rn(x[i], mul_rn(L11[i * NBM + mm], x[mm]));
-          }
+        T x = v0;  // row `lane` of the column
+        for (int mm = 0; mm < w - 1; ++mm) {
+          const T xm = __shfl_sync(0xffffffffu, x, mm);
+          if (lane > mm && lane < w) x = sub_rn(x, mul_rn(L11t[mm * NBM + lane], xm));
         }
-        int nf2 = 0;
-#pragma unroll
-        for (int s = 0; s < NBM; ++s)
-          if (s < w) {
-            F v = store_rn<F>(x[s]);
-            A[(size_t)(kk + s) * lda + c] = v;
-            if (!isfinite((double)to_f(v))) nf2 = 1;
-          }
-        if (nf2) s_nf = 1;
+        if (lane < w) {
+          const F v = store_rn<F>(x);
+          A[(size_t)(kk + lane) * lda + c] = v;
+          if (!isfinite(to_f(v))) s_nf = 1;
+        }
       }
     }
     cl.sync();
+    PT_END(5);
+    PT_BEGIN(6);
 
-    // inner update: rows [kk+w, n), columns [kk+w, k+W)
-    if (nright > 0 && kk + w < n) {
+    // inner update of my panel rows below the diagonal block:
+    // A[kk+gi][kk+w+c] <- fl(A - sum_mm L[gi][mm] U12[mm][c]), L from P
+    if (nright > 0) {
       for (int idx = tid; idx < w * nright; idx += blockDim.x) {
         const int i = idx / nright, c = idx % nright;
         U12[i * W + c] = (T)to_f(A[(size_t)(kk + i) * lda + kk + w + c]);
       }
       __syncthreads();
-      const int rows = n - kk - w;
-      const int Rr = (rows + C - 1) / C;
-      const int r0 = rank * Rr, r1 = min(rows, r0 + Rr);
-      for (int r = r0 + warp; r < r1; r += NW) {
-        const size_t row = (size_t)(kk + w + r);
-        T lv = lane < w ? (T)to_f(A[row * lda + kk + lane]) : (T)0;
-        for (int c0 = 0; c0 < nright; c0 += 32) {
-          const int c = c0 + lane;
-          T acc = 0;
+      const int lfirst = max(0, w - my0);  // first local row with gi >= w
+      for (int c0 = 0; c0 < nright; c0 += 32) {
+        const int c = c0 + lane;
+        for (int l0 = lfirst + warp * kInnerRows; l0 < nloc; l0 += NW * kInnerRows) {
+          T acc[kInnerRows];
+#pragma unroll
+          for (int r = 0; r < kInnerRows; ++r) acc[r] = (T)0;
           for (int mm = 0; mm < w; ++mm) {
-            T l = __shfl_sync(0xffffffffu, lv, mm);
-            if (c < nright) acc = fma_rn(l, U12[mm * W + c], acc);
+            const T u = c < nright ? U12[mm * W + c] : (T)0;
+#pragma unroll
+            for (int r = 0; r < kInnerRows; ++r) {
+              const T l = (l0 + r < nloc) ? P[(l0 + r) * ldp + mm] : (T)0;
+              acc[r] = fma_rn(l, u, acc[r]);
+            }
           }
           if (c < nright) {
-            F* dst = A + row * lda + kk + w + c;
-            *dst = store_rn<F>(sub_rn((T)to_f(*dst), acc));
+#pragma unroll
+            for (int r = 0; r < kInnerRows; ++r) {
+              if (l0 + r < nloc) {
+                F* dst = A + (size_t)(kk + my0 + l0 + r) * lda + kk + w + c;
+                *dst = store_rn<F>(sub_rn((T)to_f(*dst), acc[r]));
+              }
+            }
           }
         }
       }
     }
     cl.sync();
+    PT_END(6);
   }
 
   if (s_nf) atomicExch(a.nonfinite, 1);
@@ -374,10 +406,11 @@ __global__ void __launch_bounds__(256) lu_outer_swap_trsm(SwapTrsmArgs a) {
   const int tid = threadIdx.x;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ldL = W + (sizeof(F) == 2 ? 2 : 1);  // padded: rows of L fall in different banks
   T* X = (T*)smem_raw;                       // W x 32
-  F* L = (F*)(X + (size_t)W * 32);           // W x W (only when right tiles exist)
-  F* E = L + (size_t)W * W;                  // (cnt - W) x 32 displaced rows
-  size_t off = sizeof(T) * (size_t)W * 32 + sizeof(F) * ((size_t)W * W + (size_t)W * 32);
+  F* L = (F*)(X + (size_t)W * 32);           // W x ldL (only when right tiles exist)
+  F* E = L + (size_t)W * ldL;                // (cnt - W) x 32 displaced rows
+  size_t off = sizeof(T) * (size_t)W * 32 + sizeof(F) * ((size_t)W * ldL + (size_t)W * 32);
   off = (off + 15) & ~(size_t)15;
   int* pos = (int*)(smem_raw + off);
   int* val = pos + 2 * W;
@@ -390,7 +423,7 @@ __global__ void __launch_bounds__(256) lu_outer_swap_trsm(SwapTrsmArgs a) {
   if (need_L) {
     for (int idx = tid; idx < W * W; idx += blockDim.x) {
       const int i = idx / W, c = idx % W;
-      L[idx] = A[(size_t)(k + i) * lda + k + c];
+      L[i * ldL + c] = A[(size_t)(k + i) * lda + k + c];
     }
   }
   __syncthreads();
@@ -418,7 +451,7 @@ __global__ void __launch_bounds__(256) lu_outer_swap_trsm(SwapTrsmArgs a) {
         const int rows = W - 1 - mm;
         for (int idx = tid; idx < rows * 32; idx += blockDim.x) {
           const int i = mm + 1 + idx / 32, cc = idx % 32;
-          X[i * 32 + cc] = sub_rn(X[i * 32 + cc], mul_rn((T)to_f(L[i * W + mm]), X[mm * 32 + cc]));
+          X[i * 32 + cc] = sub_rn(X[i * 32 + cc], mul_rn((T)to_f(L[i * ldL + mm]), X[mm * 32 + cc]));
         }
         __syncthreads();
       }
@@ -429,7 +462,7 @@ __global__ void __launch_bounds__(256) lu_outer_swap_trsm(SwapTrsmArgs a) {
       if (c < cend) {
         F v = store_rn<F>(X[s * 32 + cc]);
         A[(size_t)(k + s) * lda + c] = v;
-        if (right && !isfinite((double)to_f(v))) nf = 1;
+        if (right && !isfinite(to_f(v))) nf = 1;
       }
     }
     if (right && a.Ut != nullptr) {
@@ -509,17 +542,17 @@ __global__ void __launch_bounds__(256) lu_update_simt(UpdateArgs a) {
 size_t panel_smem_bytes(int fmt, int R_cap, int nb, int W) {
   const size_t ts = fmt == MSIR_FP64 ? 8 : 4;
   const int NBM = fmt == MSIR_FP64 ? 16 : 32;
-  size_t b = ts * ((size_t)R_cap * (nb + 1) + 2 * 16 * NBM + 2 * NBM + NBM * NBM + (size_t)NBM * W);
+  size_t b = ts * ((size_t)R_cap * (nb + 1) + 2 * 16 * NBM + 2 * NBM + NBM * NBM + (size_t)NBM * W + 32);
   b = (b + 7) & ~(size_t)7;
-  b += 32 * sizeof(double) + 32 * sizeof(int) + NBM * sizeof(int) + 4 * NBM * sizeof(int) +
-       4 * (size_t)W * sizeof(int);
+  b += 32 * sizeof(int) + NBM * sizeof(int) + 4 * NBM * sizeof(int) + 4 * (size_t)W * sizeof(int);
   return b;
 }
 
 size_t swap_trsm_smem_bytes(int fmt, int W) {
   const size_t ts = fmt == MSIR_FP64 ? 8 : 4;
   const size_t fs = fmt == MSIR_FP64 ? 8 : fmt == MSIR_FP32 ? 4 : 2;
-  size_t off = ts * (size_t)W * 32 + fs * ((size_t)W * W + (size_t)W * 32);
+  const size_t ldL = W + (fs == 2 ? 2 : 1);
+  size_t off = ts * (size_t)W * 32 + fs * ((size_t)W * ldL + (size_t)W * 32);
   off = (off + 15) & ~(size_t)15;
   return off + 4 * (size_t)W * sizeof(int);
 }

@@ -11,6 +11,9 @@ namespace msir {
 constexpr int kRefThreads = 256;  // 8 warps
 constexpr int kBlk = 64;          // rows per block of the row distribution / TRSV
 constexpr int kMaxKcap = 2048;    // GMRES iteration cap supported
+// Stride (in unsigned words) between the TRSV flags of consecutive blocks,
+// so that each flag has its own 128-byte line.
+constexpr int kFlagStride = 32;
 
 enum RefMode { MODE_SOLVE = 0, MODE_APPLY = 1, MODE_RESIDUAL = 2 };
 enum RefPhase {
@@ -33,7 +36,10 @@ struct RefState {
   int total_steps, total_gmres;
   double rho_max, delta_prev, phi0, phi;
   double s, nbe, best_nbe;
-  double pad[4];
+  // device time (ns) spent by CTA 0 per phase: 0 residual, 1 forward
+  // substitution, 2 backward substitution, 3 Gram-Schmidt, 4 operator
+  // matrix-vector product, 5 update/norm reductions, 6 Givens/least squares
+  unsigned long long t_ns[8];
 };
 
 struct RefineArgs {
@@ -92,6 +98,9 @@ struct RefineArgs {
   double* ap_out;
   // MODE_RESIDUAL: output s
   double* res_s;
+  // optional wavefront timestamps of the last substitution pair (ns):
+  // [direction][block][start, off-diagonal done, published]
+  unsigned long long* tsv;
 };
 
 constexpr int kRedW = 4;

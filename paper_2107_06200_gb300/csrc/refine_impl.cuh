@@ -31,6 +31,20 @@ struct Cx {
   int G, cta, tid, lane, warp, n, nblk;
   unsigned epoch;
   int redbuf;
+  unsigned long long* t_ns;  // per-phase timers (CTA 0, thread 0), shared memory
+};
+
+// Phase timer: CTA 0 / thread 0 accumulates %globaltimer deltas.
+struct PhaseTimer {
+  Cx& cx;
+  int ph;
+  unsigned long long t0;
+  __device__ PhaseTimer(Cx& c, int p) : cx(c), ph(p), t0(0) {
+    if (cx.cta == 0 && cx.tid == 0) t0 = gtimer();
+  }
+  __device__ ~PhaseTimer() {
+    if (cx.cta == 0 && cx.tid == 0) cx.t_ns[ph] += gtimer() - t0;
+  }
 };
 
 static __device__ __forceinline__ double urnd(double v, int u) {
@@ -77,17 +91,6 @@ __device__ double row_dot_d(const A0* row, const double* x, int n, int lane) {
   for (int j = lane; j < n; j += 32) acc = __fma_rn(AV<A0>::ld(row + j), __ldcg(x + j), acc);
   return warp_sum_d(acc);
 }
-// fp32 accumulation (operator applied in u = fp32).
-static __device__ float row_dot_f(const float* row, const double* x, int n, int lane) {
-  float acc = 0.0f;
-  for (int j = lane; j < n; j += 32) acc = __fmaf_rn(__ldg(row + j), (float)__ldcg(x + j), acc);
-  return warp_sum_f(acc);
-}
-static __device__ float row_dot_f(const double* row, const double* x, int n, int lane) {
-  float acc = 0.0f;
-  for (int j = lane; j < n; j += 32) acc = __fmaf_rn((float)__ldg(row + j), (float)__ldcg(x + j), acc);
-  return warp_sum_f(acc);
-}
 // Compensated (twice-working-precision) dot product, result as dd.
 template <typename A0>
 __device__ dd_t row_dot_dd(const A0* row, const double* x, int n, int lane) {
@@ -106,6 +109,7 @@ __device__ dd_t row_dot_dd(const A0* row, const double* x, int n, int lane) {
 // thread 0) across the grid.  op[i]: 0 = sum, 1 = NaN-propagating max.
 template <int NV>
 __device__ bool grid_reduce(Cx& cx, const RefineArgs& a, double (&v)[NV], const int (&op)[NV]) {
+  PhaseTimer pt(cx, 5);
   __shared__ double s_res[kRedW];
   double* buf = a.red + (size_t)cx.redbuf * cx.G * kRedW;
   cx.redbuf ^= 1;
@@ -146,62 +150,89 @@ static __device__ double cta_reduce(double v, int op, int tid) {
 
 // ----------------------------------------------------- triangular solves
 
-template <typename F> struct FV {
-  static __device__ __forceinline__ double ld(const F* p) { return (double)to_f(p[0]); }
-};
-
-// Accumulator policies.
+// Accumulator policies of the substitutions.  V: accumulator, L: factor
+// element after widening, storage of the vectors: float for AccF (so that
+// fp32 solves never touch the scarce fp64 pipe), double for AccD, a pair of
+// double arrays (high, low words) for AccDD.
 struct AccF {
   using V = float;
+  using L = float;
   static __device__ __forceinline__ V zero() { return 0.0f; }
-  static __device__ __forceinline__ V from(double h, double) { return (float)h; }
-  static __device__ __forceinline__ V fma(double l, V y, V acc) { return __fmaf_rn((float)l, y, acc); }
+  static __device__ __forceinline__ V load(const double* hi, const double*, int i) {
+    return __ldcg((const float*)hi + i);
+  }
+  static __device__ __forceinline__ void save(double* hi, double*, int i, V v) { ((float*)hi)[i] = v; }
+  static __device__ __forceinline__ void put(double* hi, double*, int i, double h, double) {
+    ((float*)hi)[i] = (float)h;
+  }
+  static __device__ __forceinline__ double get(const double* hi, const double*, int i) {
+    return (double)((const float*)hi)[i];
+  }
+  static __device__ __forceinline__ V fma(L l, V y, V acc) { return __fmaf_rn(l, y, acc); }
+  static __device__ __forceinline__ V mul(L l, V y) { return __fmul_rn(l, y); }
   static __device__ __forceinline__ V sub(V a, V b) { return __fsub_rn(a, b); }
-  static __device__ __forceinline__ V div(V a, double d) { return __fdiv_rn(a, (float)d); }
+  static __device__ __forceinline__ V div(V a, L d) { return __fdiv_rn(a, d); }
   static __device__ __forceinline__ V store(V v, int fmt) { return round_f(v, fmt); }
   static __device__ __forceinline__ V wsum(V v) { return warp_sum_f(v); }
   static __device__ __forceinline__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-  static __device__ __forceinline__ double hi(V v) { return (double)v; }
-  static __device__ __forceinline__ double lo(V) { return 0.0; }
 };
 struct AccD {
   using V = double;
+  using L = double;
   static __device__ __forceinline__ V zero() { return 0.0; }
-  static __device__ __forceinline__ V from(double h, double) { return h; }
-  static __device__ __forceinline__ V fma(double l, V y, V acc) { return __fma_rn(l, y, acc); }
+  static __device__ __forceinline__ V load(const double* hi, const double*, int i) { return __ldcg(hi + i); }
+  static __device__ __forceinline__ void save(double* hi, double*, int i, V v) { hi[i] = v; }
+  static __device__ __forceinline__ void put(double* hi, double*, int i, double h, double) { hi[i] = h; }
+  static __device__ __forceinline__ double get(const double* hi, const double*, int i) { return hi[i]; }
+  static __device__ __forceinline__ V fma(L l, V y, V acc) { return __fma_rn(l, y, acc); }
+  static __device__ __forceinline__ V mul(L l, V y) { return __dmul_rn(l, y); }
   static __device__ __forceinline__ V sub(V a, V b) { return __dsub_rn(a, b); }
-  static __device__ __forceinline__ V div(V a, double d) { return __ddiv_rn(a, d); }
+  static __device__ __forceinline__ V div(V a, L d) { return __ddiv_rn(a, d); }
   static __device__ __forceinline__ V store(V v, int) { return v; }
   static __device__ __forceinline__ V wsum(V v) { return warp_sum_d(v); }
   static __device__ __forceinline__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-  static __device__ __forceinline__ double hi(V v) { return v; }
-  static __device__ __forceinline__ double lo(V) { return 0.0; }
 };
 struct AccDD {
   using V = dd_t;
+  using L = double;
   static __device__ __forceinline__ V zero() { return dd_t{0.0, 0.0}; }
-  static __device__ __forceinline__ V from(double h, double l) { return dd_t{h, l}; }
-  static __device__ __forceinline__ V fma(double l, V y, V acc) { return dd_add(acc, dd_mul_d(y, l)); }
+  static __device__ __forceinline__ V load(const double* hi, const double* lo, int i) {
+    return dd_t{__ldcg(hi + i), __ldcg(lo + i)};
+  }
+  static __device__ __forceinline__ void save(double* hi, double* lo, int i, V v) { hi[i] = v.hi; lo[i] = v.lo; }
+  static __device__ __forceinline__ void put(double* hi, double* lo, int i, double h, double l) {
+    hi[i] = h;
+    lo[i] = l;
+  }
+  static __device__ __forceinline__ double get(const double* hi, const double* lo, int i) {
+    return __dadd_rn(hi[i], lo[i]);
+  }
+  static __device__ __forceinline__ V fma(L l, V y, V acc) { return dd_add(acc, dd_mul_d(y, l)); }
+  static __device__ __forceinline__ V mul(L l, V y) { return dd_mul_d(y, l); }
   static __device__ __forceinline__ V sub(V a, V b) { return dd_sub(a, b); }
-  static __device__ __forceinline__ V div(V a, double d) { return dd_div_d(a, d); }
+  static __device__ __forceinline__ V div(V a, L d) { return dd_div_d(a, d); }
   static __device__ __forceinline__ V store(V v, int) { return v; }
   static __device__ __forceinline__ V wsum(V v) { return warp_sum_dd(v); }
   static __device__ __forceinline__ V shfl(V v, int src) {
     return dd_t{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
   }
-  static __device__ __forceinline__ double hi(V v) { return v.hi; }
-  static __device__ __forceinline__ double lo(V v) { return v.lo; }
 };
+
+template <typename Lt, typename F>
+__device__ __forceinline__ Lt ld_fac(const F* p) {
+  return (Lt)to_f(*p);
+}
 
 constexpr int kDtLd = kBlk + 1;
 
 // One triangular solve (LOWER: L y = c, unit diagonal; else U z = y) over
-// all blocks this CTA owns.  Input/output vectors hold values as (hi, lo)
-// doubles; for non-dd accumulators lo is ignored.
+// all blocks this CTA owns.
 template <typename F, typename ACC, bool LOWER>
-__device__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt, double* Dt) {
+__device__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt, void* Dt_raw) {
   using V = typename ACC::V;
+  using Lt = typename ACC::L;
   __shared__ V s_sum[kBlk];
+  Lt* Dt = (Lt*)Dt_raw;
   const F* LU = (const F*)a.LU;
   const int ldf = a.ldf, n = cx.n;
   const unsigned epoch = ++cx.epoch;
@@ -216,11 +247,14 @@ __device__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt, double* Dt) {
     const int b = LOWER ? cx.cta + q * cx.G : cx.cta + (nmine - 1 - q) * cx.G;
     const int r0 = b * kBlk;
     const int nr = min(kBlk, n - r0);
+    unsigned long long* ts = a.tsv ? a.tsv + ((LOWER ? 0 : 1) * (size_t)cx.nblk + b) * 3 : nullptr;
+    if (ts && cx.tid == 0) ts[0] = gtimer();
     // diagonal tile, transposed: Dt[m][i] = T[r0+i][r0+m]
     for (int idx = cx.tid; idx < kBlk * kBlk; idx += kRefThreads) {
       const int i = idx / kBlk, m = idx % kBlk;
-      double v = 0.0;
-      if (i < nr && m < nr && (LOWER ? m < i : m >= i)) v = FV<F>::ld(LU + (size_t)(r0 + i) * ldf + r0 + m);
+      Lt v = (Lt)0;
+      if (i < nr && m < nr && (LOWER ? m < i : m >= i)) v = ld_fac<Lt>(LU + (size_t)(r0 + i) * ldf + r0 + m);
+      if (!LOWER && i == m && i >= nr) v = (Lt)1;  // padding rows of a partial block: identity
       Dt[m * kDtLd + i] = v;
     }
     // off-diagonal products
@@ -230,60 +264,77 @@ __device__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt, double* Dt) {
     const int njb = LOWER ? b : cx.nblk - 1 - b;
     for (int t = 0; t < njb; ++t) {
       const int jb = LOWER ? t : cx.nblk - 1 - t;
-      if (!wait_flag(a.flags + jb, epoch, a.err)) return false;
       const int c0 = jb * kBlk;
       const int ca = c0 + cx.lane, cb = c0 + 32 + cx.lane;
-      V y0 = ACC::zero(), y1 = ACC::zero();
-      if (ca < n) y0 = ACC::from(__ldcg(src_hi + ca), __ldcg(src_lo + ca));
-      if (cb < n) y1 = ACC::from(__ldcg(src_hi + cb), __ldcg(src_lo + cb));
+      // the tile of L (U) does not depend on the flag: load it first
+      Lt la[8], lb[8];
 #pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
         const int row = r0 + cx.warp * 8 + rr;
-        if (row < n) {
-          const F* lr = LU + (size_t)row * ldf;
-          if (ca < n) acc[rr] = ACC::fma(FV<F>::ld(lr + ca), y0, acc[rr]);
-          if (cb < n) acc[rr] = ACC::fma(FV<F>::ld(lr + cb), y1, acc[rr]);
-        }
+        const F* lr = LU + (size_t)row * ldf;
+        la[rr] = (row < n && ca < n) ? ld_fac<Lt>(lr + ca) : (Lt)0;
+        lb[rr] = (row < n && cb < n) ? ld_fac<Lt>(lr + cb) : (Lt)0;
+      }
+      if (!wait_flag(a.flags + (size_t)jb * kFlagStride, epoch, a.err)) return false;
+      V y0 = ACC::zero(), y1 = ACC::zero();
+      if (ca < n) y0 = ACC::load(src_hi, src_lo, ca);
+      if (cb < n) y1 = ACC::load(src_hi, src_lo, cb);
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) {
+        acc[rr] = ACC::fma(la[rr], y0, acc[rr]);
+        acc[rr] = ACC::fma(lb[rr], y1, acc[rr]);
       }
     }
 #pragma unroll
     for (int rr = 0; rr < 8; ++rr) {
-      V s = ACC::wsum(acc[rr]);
-      if (cx.lane == 0) s_sum[cx.warp * 8 + rr] = s;
+      V sm = ACC::wsum(acc[rr]);
+      if (cx.lane == 0) s_sum[cx.warp * 8 + rr] = sm;
     }
     __syncthreads();
+    if (ts && cx.tid == 0) ts[1] = gtimer();
     if (cx.warp == 0) {
       const int l = cx.lane;
       V z0 = ACC::zero(), z1 = ACC::zero();
-      if (l < nr) z0 = ACC::sub(ACC::from(in_hi[r0 + l], in_lo[r0 + l]), s_sum[l]);
-      if (l + 32 < nr) z1 = ACC::sub(ACC::from(in_hi[r0 + 32 + l], in_lo[r0 + 32 + l]), s_sum[32 + l]);
+      if (l < nr) z0 = ACC::sub(ACC::load(in_hi, in_lo, r0 + l), s_sum[l]);
+      if (l + 32 < nr) z1 = ACC::sub(ACC::load(in_hi, in_lo, r0 + 32 + l), s_sum[32 + l]);
+      // Fully unrolled: each lane keeps its two rows; rows beyond nr stay 0
+      // and are never stored.  y_m is broadcast from lane m mod 32.
+      V y0 = ACC::zero(), y1 = ACC::zero();
       if (LOWER) {
-        for (int m = 0; m < nr; ++m) {
-          V v = ACC::shfl(m < 32 ? z0 : z1, m & 31);
-          V ym = ACC::store(v, store_fmt);
-          if (l == (m & 31)) {
-            out_hi[r0 + m] = ACC::hi(ym);
-            out_lo[r0 + m] = ACC::lo(ym);
-          }
-          if (l > m) z0 = ACC::sub(z0, ACC::fma(Dt[m * kDtLd + l], ym, ACC::zero()));
-          if (l + 32 > m) z1 = ACC::sub(z1, ACC::fma(Dt[m * kDtLd + l + 32], ym, ACC::zero()));
+#pragma unroll
+        for (int m = 0; m < 32; ++m) {
+          const V ym = ACC::store(ACC::shfl(z0, m), store_fmt);
+          if (l == m) y0 = ym;
+          if (l > m) z0 = ACC::sub(z0, ACC::mul(Dt[m * kDtLd + l], ym));
+          z1 = ACC::sub(z1, ACC::mul(Dt[m * kDtLd + l + 32], ym));
+        }
+#pragma unroll
+        for (int m = 32; m < 64; ++m) {
+          const V ym = ACC::store(ACC::shfl(z1, m - 32), store_fmt);
+          if (l == m - 32) y1 = ym;
+          if (l + 32 > m) z1 = ACC::sub(z1, ACC::mul(Dt[m * kDtLd + l + 32], ym));
         }
       } else {
-        for (int m = nr - 1; m >= 0; --m) {
-          V v = ACC::shfl(m < 32 ? z0 : z1, m & 31);
-          V xm = ACC::store(ACC::div(v, Dt[m * kDtLd + m]), store_fmt);
-          if (l == (m & 31)) {
-            out_hi[r0 + m] = ACC::hi(xm);
-            out_lo[r0 + m] = ACC::lo(xm);
-          }
-          if (l < m) z0 = ACC::sub(z0, ACC::fma(Dt[m * kDtLd + l], xm, ACC::zero()));
-          if (l + 32 < m) z1 = ACC::sub(z1, ACC::fma(Dt[m * kDtLd + l + 32], xm, ACC::zero()));
+#pragma unroll
+        for (int m = 63; m >= 32; --m) {
+          const V xm = ACC::store(ACC::div(ACC::shfl(z1, m - 32), Dt[m * kDtLd + m]), store_fmt);
+          if (l == m - 32) y1 = xm;
+          if (l + 32 < m) z1 = ACC::sub(z1, ACC::mul(Dt[m * kDtLd + l + 32], xm));
+          z0 = ACC::sub(z0, ACC::mul(Dt[m * kDtLd + l], xm));
+        }
+#pragma unroll
+        for (int m = 31; m >= 0; --m) {
+          const V xm = ACC::store(ACC::div(ACC::shfl(z0, m), Dt[m * kDtLd + m]), store_fmt);
+          if (l == m) y0 = xm;
+          if (l < m) z0 = ACC::sub(z0, ACC::mul(Dt[m * kDtLd + l], xm));
         }
       }
+      if (l < nr) ACC::save(out_hi, out_lo, r0 + l, y0);
+      if (l + 32 < nr) ACC::save(out_hi, out_lo, r0 + 32 + l, y1);
       __syncwarp();
       if (l == 0) {
-        __threadfence();
-        st_release_u32(a.flags + b, epoch);
+        st_release_u32(a.flags + (size_t)b * kFlagStride, epoch);
+        if (ts) ts[2] = gtimer();
       }
     }
     __syncthreads();
@@ -295,16 +346,33 @@ __device__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt, double* Dt) {
 // order, scaled by R, rounded to the storage format): forward then backward
 // substitution.  Result in z (natural order, before the S*mu scaling).
 template <typename F, typename ACC>
-__device__ bool msolve(Cx& cx, const RefineArgs& a, int store_fmt, double* Dt) {
-  if (!trsv<F, ACC, true>(cx, a, store_fmt, Dt)) return false;
+__device__ bool msolve(Cx& cx, const RefineArgs& a, int store_fmt, void* Dt) {
+  {
+    PhaseTimer pt(cx, 1);
+    if (!trsv<F, ACC, true>(cx, a, store_fmt, Dt)) return false;
+  }
+  PhaseTimer pt(cx, 2);
   return trsv<F, ACC, false>(cx, a, store_fmt, Dt);
 }
 
 template <typename F>
-__device__ bool msolve_arith(Cx& cx, const RefineArgs& a, int arith, int store_fmt, double* Dt) {
+__device__ bool msolve_arith(Cx& cx, const RefineArgs& a, int arith, int store_fmt, void* Dt) {
   if (arith == MSIR_FP32) return msolve<F, AccF>(cx, a, store_fmt, Dt);
   if (arith == MSIR_FP64) return msolve<F, AccD>(cx, a, store_fmt, Dt);
   return msolve<F, AccDD>(cx, a, store_fmt, Dt);
+}
+
+// right-hand side element of a substitution in precision `arith`
+__device__ __forceinline__ void put_c(const RefineArgs& a, int arith, int i, double h, double l) {
+  if (arith == MSIR_FP32) AccF::put(a.c_hi, a.c_lo, i, h, l);
+  else if (arith == MSIR_FP64) AccD::put(a.c_hi, a.c_lo, i, h, l);
+  else AccDD::put(a.c_hi, a.c_lo, i, h, l);
+}
+// solution element (z) of a substitution in precision `arith`, as a double
+__device__ __forceinline__ double get_z(const RefineArgs& a, int arith, int i) {
+  if (arith == MSIR_FP32) return AccF::get(a.z_hi, a.z_lo, i);
+  if (arith == MSIR_FP64) return AccD::get(a.z_hi, a.z_lo, i);
+  return AccDD::get(a.z_hi, a.z_lo, i);
 }
 
 // iterate over the rows of my blocks
@@ -321,33 +389,33 @@ static __device__ __forceinline__ double cscale(const RefineArgs& a, int col) {
 
 // ------------------------------------------------------------ residual
 
-// r_p[i] = b[perm[i]] - A[perm[i]] x in ur for my rows; returns (via grid
-// reduction) s = ||r||_inf and ||x||_inf.
+// r_p[i] = b[perm[i]] - A[perm[i]] x in ur; rows are spread over every warp
+// of the grid (the fp64 work needs all SMs).  Returns (via grid reduction)
+// s = ||r||_inf and ||x||_inf.  The caller has made x complete (barrier).
 template <typename A0>
 __device__ bool residual(Cx& cx, const RefineArgs& a, const double* x, int ur, double& s,
                          double& xnorm) {
+  PhaseTimer pt(cx, 0);
   const A0* A = (const A0*)a.A;
   double mr = 0.0, mx = 0.0;
-  for (int b = cx.cta; b < cx.nblk; b += cx.G) {
-    for (int rr = 0; rr < 8; ++rr) {
-      const int i = b * kBlk + cx.warp * 8 + rr;
-      if (i >= cx.n) break;
-      const int ar = a.perm[i];
-      const A0* row = A + (size_t)ar * a.lda;
-      if (ur == MSIR_DD) {
-        dd_t ax = row_dot_dd<A0>(row, x, cx.n, cx.lane);
-        dd_t r = dd_sub(dd_t{a.b[ar], 0.0}, ax);
-        if (cx.lane == 0) { a.r_hi[i] = r.hi; a.r_lo[i] = r.lo; }
-        mr = nanmax(mr, fabs(r.hi));
-      } else {
-        double ax = row_dot_d<A0>(row, x, cx.n, cx.lane);
-        double r = __dsub_rn(a.b[ar], ax);
-        if (cx.lane == 0) { a.r_hi[i] = r; a.r_lo[i] = 0.0; }
-        mr = nanmax(mr, fabs(r));
-      }
+  const int nw = cx.G * (kRefThreads / 32);
+  for (int i = cx.cta * (kRefThreads / 32) + cx.warp; i < cx.n; i += nw) {
+    const int ar = a.perm[i];
+    const A0* row = A + (size_t)ar * a.lda;
+    if (ur == MSIR_DD) {
+      const dd_t ax = row_dot_dd<A0>(row, x, cx.n, cx.lane);
+      const dd_t r = dd_sub(dd_t{a.b[ar], 0.0}, ax);
+      if (cx.lane == 0) { a.r_hi[i] = r.hi; a.r_lo[i] = r.lo; }
+      mr = nanmax(mr, fabs(r.hi));
+    } else {
+      const double ax = row_dot_d<A0>(row, x, cx.n, cx.lane);
+      const double r = __dsub_rn(a.b[ar], ax);
+      if (cx.lane == 0) { a.r_hi[i] = r; a.r_lo[i] = 0.0; }
+      mr = nanmax(mr, fabs(r));
     }
   }
-  FOR_MY_ROWS(cx, i) mx = nanmax(mx, fabs(__ldcg(x + i)));
+  for (int i = cx.cta * kRefThreads + cx.tid; i < cx.n; i += cx.G * kRefThreads)
+    mx = nanmax(mx, fabs(__ldcg(x + i)));
   mr = cta_reduce(mr, 1, cx.tid);
   mx = cta_reduce(mx, 1, cx.tid);
   double v[2] = {mr, mx};
@@ -361,10 +429,10 @@ __device__ bool residual(Cx& cx, const RefineArgs& a, const double* x, int ur, d
 // fl_u(r_p[i] / s), division in u_r
 static __device__ __forceinline__ double scaled_r(const RefineArgs& a, int i, double s, int ur, int u) {
   if (ur == MSIR_DD) {
-    dd_t q = dd_div_d(dd_t{a.r_hi[i], a.r_lo[i]}, s);
+    const dd_t q = dd_div_d(dd_t{__ldcg(a.r_hi + i), __ldcg(a.r_lo + i)}, s);
     return urnd(q.hi, u);
   }
-  return urnd(__ddiv_rn(a.r_hi[i], s), u);
+  return urnd(__ddiv_rn(__ldcg(a.r_hi + i), s), u);
 }
 
 // --------------------------------------------------------------- GMRES
@@ -374,201 +442,259 @@ struct GmresOut {
   bool nonfinite;
 };
 
-// Operator t = A v in the operator precision for my (permuted) rows, into
-// c (scaled by R).  op: MSIR_FP32 (u = fp32, SGMRES), FP64 or DD.
-template <typename A0>
-__device__ void apply_A(Cx& cx, const RefineArgs& a, const double* v, int op) {
+// Working-precision arithmetic for the GMRES vectors and the Givens /
+// least-squares scalars (U = float for u = fp32, double for u = fp64).
+template <typename U> struct UA;
+template <> struct UA<float> {
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float div(float a, float b) { return __fdiv_rn(a, b); }
+  static __device__ __forceinline__ float sqrt_(float a) { return __fsqrt_rn(a); }
+  static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+  static __device__ __forceinline__ float wsum(float v) { return warp_sum_f(v); }
+  static __device__ __forceinline__ float rnd(double v) { return __double2float_rn(v); }
+};
+template <> struct UA<double> {
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double div(double a, double b) { return __ddiv_rn(a, b); }
+  static __device__ __forceinline__ double sqrt_(double a) { return __dsqrt_rn(a); }
+  static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+  static __device__ __forceinline__ double wsum(double v) { return warp_sum_d(v); }
+  static __device__ __forceinline__ double rnd(double v) { return v; }
+};
+
+// Operator t = A v (rows perm[i]) in the operator precision, scaled by R,
+// placed in c.  op = FP32: fp32 accumulation, rows of my blocks (no barrier
+// needed before the substitution); FP64 / DD: rows over every warp of the
+// grid, followed by a grid barrier.
+template <typename A0, typename U>
+__device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
+  PhaseTimer pt(cx, 4);
   const A0* A = (const A0*)a.A;
-  for (int b = cx.cta; b < cx.nblk; b += cx.G) {
-    for (int rr = 0; rr < 8; ++rr) {
-      const int i = b * kBlk + cx.warp * 8 + rr;
-      if (i >= cx.n) break;
-      const int ar = a.perm[i];
-      const A0* row = A + (size_t)ar * a.lda;
-      const double R = rscale(a, ar);
-      if (op == MSIR_DD) {
-        dd_t t = row_dot_dd<A0>(row, v, cx.n, cx.lane);
-        if (cx.lane == 0) { a.c_hi[i] = t.hi * R; a.c_lo[i] = t.lo * R; }
-      } else if (op == MSIR_FP32) {
-        float t = row_dot_f(row, v, cx.n, cx.lane);
-        if (cx.lane == 0) { a.c_hi[i] = (double)t * R; a.c_lo[i] = 0.0; }
-      } else {
-        double t = row_dot_d<A0>(row, v, cx.n, cx.lane);
-        if (cx.lane == 0) { a.c_hi[i] = t * R; a.c_lo[i] = 0.0; }
+  if (op == MSIR_FP32) {
+    for (int b = cx.cta; b < cx.nblk; b += cx.G) {
+      for (int rr = 0; rr < 8; ++rr) {
+        const int i = b * kBlk + cx.warp * 8 + rr;
+        if (i >= cx.n) break;
+        const int ar = a.perm[i];
+        const A0* row = A + (size_t)ar * a.lda;
+        float acc = 0.0f;
+        for (int j = cx.lane; j < cx.n; j += 32) acc = __fmaf_rn((float)__ldg(row + j), (float)__ldcg(v + j), acc);
+        acc = warp_sum_f(acc);
+        if (cx.lane == 0) {
+          const float R = a.Rsc ? (float)a.Rsc[ar] : 1.0f;
+          ((float*)a.c_hi)[i] = __fmul_rn(acc, R);
+        }
       }
     }
+    __syncthreads();
+    return true;
   }
-  __syncthreads();
+  const int nw = cx.G * (kRefThreads / 32);
+  for (int i = cx.cta * (kRefThreads / 32) + cx.warp; i < cx.n; i += nw) {
+    const int ar = a.perm[i];
+    const A0* row = A + (size_t)ar * a.lda;
+    const double R = rscale(a, ar);
+    if (op == MSIR_DD) {
+      double sh = 0.0, sc = 0.0;
+      for (int j = cx.lane; j < cx.n; j += 32) {
+        const dd_t p = two_prod((double)__ldg(row + j), (double)__ldcg(v + j));
+        const dd_t t = two_sum(sh, p.hi);
+        sh = t.hi;
+        sc = __dadd_rn(sc, __dadd_rn(t.lo, p.lo));
+      }
+      const dd_t tt = warp_sum_dd(fast_two_sum(sh, sc));
+      if (cx.lane == 0) { a.c_hi[i] = tt.hi * R; a.c_lo[i] = tt.lo * R; }
+    } else {
+      double acc = 0.0;
+      for (int j = cx.lane; j < cx.n; j += 32) acc = __fma_rn((double)__ldg(row + j), (double)__ldcg(v + j), acc);
+      acc = warp_sum_d(acc);
+      if (cx.lane == 0) a.c_hi[i] = acc * R;
+    }
+  }
+  return grid_barrier(a.bar, a.err, cx.G);
 }
 
 // out_i = fl_u(z_i * S_i * mu) for my rows
-static __device__ void finish_solve(Cx& cx, const RefineArgs& a, double* out, int u, int arith) {
-  FOR_MY_ROWS(cx, i) {
-    double v = arith == MSIR_DD ? dd_add(dd_t{a.z_hi[i], a.z_lo[i]}, dd_t{0.0, 0.0}).hi : a.z_hi[i];
-    out[i] = urnd(v * cscale(a, i), u);
-  }
+template <typename U>
+__device__ void finish_solve(Cx& cx, const RefineArgs& a, U* out, int arith) {
+  FOR_MY_ROWS(cx, i) out[i] = UA<U>::rnd(get_z(a, arith, i) * cscale(a, i));
   __syncthreads();
 }
 
-// Two-stage grid reduction of the (k+1) Gram-Schmidt partial sums.
-static __device__ bool cgs_reduce(Cx& cx, const RefineArgs& a, int kp1, int u, double* s_h) {
+// Two-stage grid reduction of the (k+1) Gram-Schmidt partial sums; the
+// result (rounded to u) lands in s_h[0..k].
+template <typename U>
+__device__ bool cgs_reduce(Cx& cx, const RefineArgs& a, int kp1, U* s_h) {
+  PhaseTimer pt(cx, 3);
   if (!grid_barrier(a.bar, a.err, cx.G)) return false;
   for (int j = cx.cta * 8 + cx.warp; j < kp1; j += cx.G * 8) {
     double acc = 0.0;
     for (int c = cx.lane; c < cx.G; c += 32) acc = __dadd_rn(acc, __ldcg(a.hred + (size_t)c * (a.kcap + 1) + j));
     acc = warp_sum_d(acc);
-    if (cx.lane == 0) a.hvec[j] = urnd(acc, u);
+    if (cx.lane == 0) a.hvec[j] = (double)UA<U>::rnd(acc);
   }
   if (!grid_barrier(a.bar, a.err, cx.G)) return false;
-  for (int j = cx.tid; j < kp1; j += kRefThreads) s_h[j] = __ldcg(a.hvec + j);
+  for (int j = cx.tid; j < kp1; j += kRefThreads) s_h[j] = (U)__ldcg(a.hvec + j);
   __syncthreads();
   return true;
 }
 
-// partial sums p_j = sum over my rows of V_j[i] * w[i], j = 0..k
-static __device__ void cgs_partials(Cx& cx, const RefineArgs& a, int kp1) {
+// partial sums p_j = sum over my rows of V_j[i] * w[i], j = 0..k.  Sums are
+// accumulated in fp64 (a product of two fp32 values is exact in fp64), then
+// rounded to u, as the oracle's reading of "inner products in u" states.
+template <typename U>
+__device__ void cgs_partials(Cx& cx, const RefineArgs& a, const U* V, const U* w, int kp1) {
+  PhaseTimer pt(cx, 3);
   for (int j = cx.warp; j < kp1; j += kRefThreads / 32) {
-    const double* Vj = a.V + (size_t)j * a.ldv;
+    const U* Vj = V + (size_t)j * a.ldv;
     double acc = 0.0;
     for (int b = cx.cta; b < cx.nblk; b += cx.G)
       for (int i = b * kBlk + cx.lane; i < min((b + 1) * kBlk, cx.n); i += 32)
-        acc = __fma_rn(__ldcg(Vj + i), __ldcg(a.w + i), acc);
+        acc = __fma_rn((double)__ldcg(Vj + i), (double)__ldcg(w + i), acc);
     acc = warp_sum_d(acc);
     if (cx.lane == 0) a.hred[(size_t)cx.cta * (a.kcap + 1) + j] = acc;
   }
 }
 
-// w_i = fl_u(w_i - sum_j V_j[i] h_j)
-static __device__ void cgs_update(Cx& cx, const RefineArgs& a, int kp1, int u, const double* s_h) {
+// w_i = fl_u(w_i - sum_j V_j[i] h_j), the sum in fp64
+template <typename U>
+__device__ void cgs_update(Cx& cx, const RefineArgs& a, const U* V, U* w, int kp1, const U* s_h) {
+  PhaseTimer pt(cx, 3);
   FOR_MY_ROWS(cx, i) {
     double acc = 0.0;
-    for (int j = 0; j < kp1; ++j) acc = __fma_rn(__ldcg(a.V + (size_t)j * a.ldv + i), s_h[j], acc);
-    a.w[i] = urnd(__dsub_rn(a.w[i], acc), u);
+    for (int j = 0; j < kp1; ++j) acc = __fma_rn((double)__ldcg(V + (size_t)j * a.ldv + i), (double)s_h[j], acc);
+    w[i] = UA<U>::rnd(__dsub_rn((double)w[i], acc));
   }
   __syncthreads();
 }
 
-template <typename A0, typename F>
+template <typename U>
+__device__ bool grid_sum_sq(Cx& cx, const RefineArgs& a, const U* w, double& out) {
+  double ss = 0.0;
+  FOR_MY_ROWS(cx, i) {
+    const double wv = (double)w[i];
+    ss = __fma_rn(wv, wv, ss);
+  }
+  double v[1] = {cta_reduce(ss, 0, cx.tid)};
+  const int opr[1] = {0};
+  if (!grid_reduce<1>(cx, a, v, opr)) return false;
+  out = v[0];
+  return true;
+}
+
+template <typename A0, typename F, typename U>
 __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int op, double tau,
-                      double* Dt, double* sm_cs, double* sm_sn, double* sm_g, double* s_h,
-                      GmresOut& out) {
-  __shared__ double s_bc[4];
+                      void* Dt, unsigned char* gsm, GmresOut& out) {
+  using M = UA<U>;
+  __shared__ double s_bc[1];
   const int kcap = a.kcap;
+  U* sm_cs = (U*)gsm;
+  U* sm_sn = sm_cs + kcap + 1;
+  U* sm_g = sm_sn + kcap + 1;   // kcap + 2
+  U* s_h = sm_g + kcap + 2;     // 2 (kcap + 1)
+  U* V = (U*)a.V;
+  U* w = (U*)a.w;
   out.k = 0;
   out.nonfinite = false;
   // w0 = fl_u(M^{-1} r~) with the substitutions in op
   for (int b = cx.cta; b < cx.nblk; b += cx.G)
-    for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads) {
-      const double rt = scaled_r(a, i, s, ur, u);
-      a.c_hi[i] = rt * rscale(a, a.perm[i]);
-      a.c_lo[i] = 0.0;
-    }
+    for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads)
+      put_c(a, op, i, scaled_r(a, i, s, ur, u) * rscale(a, a.perm[i]), 0.0);
   __syncthreads();
   if (!msolve_arith<F>(cx, a, op, op, Dt)) return false;
-  finish_solve(cx, a, a.w, u, op);
-  double ss = 0.0;
-  FOR_MY_ROWS(cx, i) { double wv = a.w[i]; ss = __fma_rn(wv, wv, ss); }
-  ss = cta_reduce(ss, 0, cx.tid);
-  {
-    double v[1] = {ss};
-    const int opr[1] = {0};
-    if (!grid_reduce<1>(cx, a, v, opr)) return false;
-    ss = v[0];
-  }
-  const double beta = usqrt(urnd(ss, u), u);
-  if (!isfinite(beta)) { out.nonfinite = true; return true; }
-  if (beta == 0.0) {
+  finish_solve<U>(cx, a, w, op);
+  double ss;
+  if (!grid_sum_sq<U>(cx, a, w, ss)) return false;
+  const U beta = M::sqrt_(M::rnd(ss));
+  if (!isfinite((double)beta)) { out.nonfinite = true; return true; }
+  if (beta == (U)0) {
     FOR_MY_ROWS(cx, i) a.d[i] = 0.0;
     __syncthreads();
     return true;
   }
-  FOR_MY_ROWS(cx, i) a.V[i] = urnd(a.w[i] / beta, u);
+  FOR_MY_ROWS(cx, i) V[i] = M::div(w[i], beta);
   if (cx.tid == 0) sm_g[0] = beta;
   __syncthreads();
   int kdone = 0;
   for (int k = 0; k < kcap; ++k) {
     // full V_k needed by the matrix-vector product
     if (!grid_barrier(a.bar, a.err, cx.G)) return false;
-    apply_A<A0>(cx, a, a.V + (size_t)k * a.ldv, op);
+    if (!apply_A<A0, U>(cx, a, V + (size_t)k * a.ldv, op)) return false;
     if (!msolve_arith<F>(cx, a, op, op, Dt)) return false;
-    finish_solve(cx, a, a.w, u, op);
+    finish_solve<U>(cx, a, w, op);
     // classical Gram-Schmidt, twice
-    cgs_partials(cx, a, k + 1);
-    if (!cgs_reduce(cx, a, k + 1, u, s_h)) return false;
-    cgs_update(cx, a, k + 1, u, s_h);
-    double h1[1];
-    (void)h1;
-    // keep the first-pass coefficients in the upper half of s_h
+    cgs_partials<U>(cx, a, V, w, k + 1);
+    if (!cgs_reduce<U>(cx, a, k + 1, s_h)) return false;
+    cgs_update<U>(cx, a, V, w, k + 1, s_h);
     for (int j = cx.tid; j <= k; j += kRefThreads) s_h[kcap + 1 + j] = s_h[j];
     __syncthreads();
-    cgs_partials(cx, a, k + 1);
-    if (!cgs_reduce(cx, a, k + 1, u, s_h)) return false;
-    cgs_update(cx, a, k + 1, u, s_h);
-    for (int j = cx.tid; j <= k; j += kRefThreads) s_h[j] = uadd(s_h[kcap + 1 + j], s_h[j], u);
-    double ww = 0.0;
-    FOR_MY_ROWS(cx, i) { double wv = a.w[i]; ww = __fma_rn(wv, wv, ww); }
-    ww = cta_reduce(ww, 0, cx.tid);
-    {
-      double v[1] = {ww};
-      const int opr[1] = {0};
-      if (!grid_reduce<1>(cx, a, v, opr)) return false;
-      ww = v[0];
-    }
-    const double hk1 = usqrt(urnd(ww, u), u);
+    cgs_partials<U>(cx, a, V, w, k + 1);
+    if (!cgs_reduce<U>(cx, a, k + 1, s_h)) return false;
+    cgs_update<U>(cx, a, V, w, k + 1, s_h);
+    for (int j = cx.tid; j <= k; j += kRefThreads) s_h[j] = M::add(s_h[kcap + 1 + j], s_h[j]);
+    __syncthreads();
+    double ww;
+    if (!grid_sum_sq<U>(cx, a, w, ww)) return false;
+    const U hk1 = M::sqrt_(M::rnd(ww));
     // Givens rotations (every CTA computes the same numbers)
+    unsigned long long tg0 = (cx.cta == 0 && cx.tid == 0) ? gtimer() : 0;
     if (cx.tid == 0) {
       for (int i = 0; i < k; ++i) {
-        const double x0 = s_h[i], x1 = s_h[i + 1];
-        s_h[i] = uadd(umul(sm_cs[i], x0, u), umul(sm_sn[i], x1, u), u);
-        s_h[i + 1] = uadd(umul(-sm_sn[i], x0, u), umul(sm_cs[i], x1, u), u);
+        const U x0 = s_h[i], x1 = s_h[i + 1];
+        s_h[i] = M::add(M::mul(sm_cs[i], x0), M::mul(sm_sn[i], x1));
+        s_h[i + 1] = M::add(M::mul(-sm_sn[i], x0), M::mul(sm_cs[i], x1));
       }
-      const double f = s_h[k], g = hk1;
-      double c, sn, r;
-      if (g == 0.0) {
-        c = 1.0; sn = 0.0; r = f;
+      const U f = s_h[k], g = hk1;
+      U c, sn, r;
+      if (g == (U)0) {
+        c = (U)1; sn = (U)0; r = f;
       } else {
-        const double ff = umul(f, f, u), gg = umul(g, g, u);
-        r = usqrt(uadd(ff, gg, u), u);
-        c = udiv(f, r, u);
-        sn = udiv(g, r, u);
+        r = M::sqrt_(M::add(M::mul(f, f), M::mul(g, g)));
+        c = M::div(f, r);
+        sn = M::div(g, r);
       }
       sm_cs[k] = c;
       sm_sn[k] = sn;
       s_h[k] = r;
-      const double gk = sm_g[k];
-      sm_g[k] = umul(c, gk, u);
-      sm_g[k + 1] = umul(-sn, gk, u);
-      s_bc[0] = fabs(sm_g[k + 1]) / beta;
+      const U gk = sm_g[k];
+      sm_g[k] = M::mul(c, gk);
+      sm_g[k + 1] = M::mul(-sn, gk);
+      s_bc[0] = fabs((double)sm_g[k + 1]) / (double)beta;
       if (cx.cta == 0) {
         double* Hk = a.H + (size_t)k * (kcap + 1);
-        for (int i = 0; i <= k; ++i) Hk[i] = s_h[i];
+        for (int i = 0; i <= k; ++i) Hk[i] = (double)s_h[i];
       }
     }
     __syncthreads();
+    if (cx.cta == 0 && cx.tid == 0) cx.t_ns[6] += gtimer() - tg0;
     const double relres = s_bc[0];
     kdone = k + 1;
-    if (hk1 != 0.0 && isfinite(hk1)) {
-      FOR_MY_ROWS(cx, i) a.V[(size_t)(k + 1) * a.ldv + i] = urnd(a.w[i] / hk1, u);
+    if (hk1 != (U)0 && isfinite((double)hk1)) {
+      FOR_MY_ROWS(cx, i) V[(size_t)(k + 1) * a.ldv + i] = M::div(w[i], hk1);
     }
     __syncthreads();
-    if (!isfinite(relres) || relres <= tau || hk1 == 0.0) break;
+    if (!isfinite(relres) || relres <= tau || hk1 == (U)0) break;
   }
   // y from the rotated Hessenberg matrix (CTA 0), then d = fl_u(V y)
   if (cx.cta == 0 && cx.tid == 0) {
     for (int i = kdone - 1; i >= 0; --i) {
-      double acc = sm_g[i];
+      U acc = sm_g[i];
       for (int j = i + 1; j < kdone; ++j)
-        acc = usub(acc, umul(a.H[(size_t)j * (kcap + 1) + i], a.yv[j], u), u);
-      a.yv[i] = udiv(acc, a.H[(size_t)i * (kcap + 1) + i], u);
+        acc = M::sub(acc, M::mul((U)a.H[(size_t)j * (kcap + 1) + i], (U)a.yv[j]));
+      a.yv[i] = (double)M::div(acc, (U)a.H[(size_t)i * (kcap + 1) + i]);
     }
   }
   if (!grid_barrier(a.bar, a.err, cx.G)) return false;
-  for (int j = cx.tid; j < kdone; j += kRefThreads) s_h[j] = __ldcg(a.yv + j);
+  for (int j = cx.tid; j < kdone; j += kRefThreads) s_h[j] = (U)__ldcg(a.yv + j);
   __syncthreads();
   FOR_MY_ROWS(cx, i) {
     double acc = 0.0;
-    for (int j = 0; j < kdone; ++j) acc = __fma_rn(__ldcg(a.V + (size_t)j * a.ldv + i), s_h[j], acc);
-    a.d[i] = urnd(acc, u);
+    for (int j = 0; j < kdone; ++j) acc = __fma_rn((double)__ldcg(V + (size_t)j * a.ldv + i), (double)s_h[j], acc);
+    a.d[i] = (double)M::rnd(acc);
   }
   __syncthreads();
   out.k = kdone;
@@ -594,7 +720,7 @@ static __device__ void rep_new_stage(const RefineArgs& a, RefState& S) {
 // with the readings listed in the library documentation).  Thread 0 only.
 // Returns 0 continue, 1 converged, 2 switch (reset = phi > phi_0).
 static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, double dnorm, double xnorm,
-                        double nbe, int kg, int* reset) {
+                               double nbe, int kg, int* reset) {
   const double delta = s * dnorm;
   const double z = xnorm > 0.0 ? delta / xnorm : __longlong_as_double(0x7ff0000000000000ll);
   const double v = isfinite(S.delta_prev) ? delta / S.delta_prev : 0.0;
@@ -623,11 +749,8 @@ static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, doubl
 template <typename A0, typename F>
 __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* Dt = (double*)smem_raw;                      // kBlk x kDtLd
-  double* sm_cs = Dt + kBlk * kDtLd;                   // kcap + 1
-  double* sm_sn = sm_cs + a.kcap + 1;                  // kcap + 1
-  double* sm_g = sm_sn + a.kcap + 1;                   // kcap + 2
-  double* s_h = sm_g + a.kcap + 2;                     // 2 (kcap + 1)
+  void* Dt = smem_raw;                                               // kBlk x kDtLd (double)
+  unsigned char* gsm = smem_raw + sizeof(double) * kBlk * kDtLd;     // GMRES scalars
   __shared__ RefState S;
   __shared__ int s_act, s_reset;
 
@@ -643,6 +766,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   if (cx.tid == 0) S = *a.st;
   __syncthreads();
   cx.epoch = S.epoch;
+  cx.t_ns = S.t_ns;
   bool ok = true;
   const int ff = Fmt<F>::code;
   const int arith_f = ff == MSIR_FP64 ? MSIR_FP64 : MSIR_FP32;
@@ -656,17 +780,11 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
       for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads) {
         const int pr = a.perm[i];
         const double v = a.ap_in[pr] * rscale(a, pr);
-        a.c_hi[i] = a.ap_arith == MSIR_DD ? v : round_to(v, a.ap_store);
-        a.c_lo[i] = 0.0;
+        put_c(a, a.ap_arith, i, a.ap_arith == MSIR_DD ? v : round_to(v, a.ap_store), 0.0);
       }
     __syncthreads();
     ok = msolve_arith<F>(cx, a, a.ap_arith, a.ap_store, Dt);
-    if (ok) {
-      FOR_MY_ROWS(cx, i) {
-        double v = a.ap_arith == MSIR_DD ? __dadd_rn(a.z_hi[i], a.z_lo[i]) : a.z_hi[i];
-        a.ap_out[i] = v * cscale(a, i);
-      }
-    }
+    if (ok) FOR_MY_ROWS(cx, i) a.ap_out[i] = get_z(a, a.ap_arith, i) * cscale(a, i);
   } else {
     // ------------------------------------------------------------ MSIR
     double s = S.s, xnorm = 0.0, nbe = S.nbe;
@@ -682,8 +800,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
         for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads) {
           const int pr = a.perm[i];
           const double bt = urnd(__ddiv_rn(a.b[pr], a.normb), S.u);
-          a.c_hi[i] = round_to(bt * rscale(a, pr), S.uf);
-          a.c_lo[i] = 0.0;
+          put_c(a, arith_f, i, round_to(bt * rscale(a, pr), S.uf), 0.0);
         }
       __syncthreads();
       ok = msolve_arith<F>(cx, a, arith_f, S.uf, Dt);
@@ -692,7 +809,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
         const double nb_u = urnd(a.normb, S.u);
         double mx = 0.0;
         FOR_MY_ROWS(cx, i) {
-          const double d0 = urnd(a.z_hi[i] * cscale(a, i), S.u);
+          const double d0 = urnd(get_z(a, arith_f, i) * cscale(a, i), S.u);
           const double x0 = urnd(nb_u * d0, S.u);
           a.x0[i] = x0;
           mx = nanmax(mx, fabs(x0));
@@ -751,18 +868,21 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
         for (int b = cx.cta; b < cx.nblk; b += cx.G)
           for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads) {
             const double rt = scaled_r(a, i, s, ur, u);
-            a.c_hi[i] = round_to(rt * rscale(a, a.perm[i]), S.uf);
-            a.c_lo[i] = 0.0;
+            put_c(a, arith_f, i, round_to(rt * rscale(a, a.perm[i]), S.uf), 0.0);
           }
         __syncthreads();
         if (!(ok = msolve_arith<F>(cx, a, arith_f, S.uf, Dt))) break;
-        FOR_MY_ROWS(cx, i) a.d[i] = urnd(a.z_hi[i] * cscale(a, i), u);
+        FOR_MY_ROWS(cx, i) a.d[i] = urnd(get_z(a, arith_f, i) * cscale(a, i), u);
         __syncthreads();
       } else {
         const int op = S.alg == MSIR_ALG_SGMRES ? u : square_of(u);
         const double tau = a.tau > 0.0 ? a.tau : (u == MSIR_FP32 ? 1e-6 : 1e-10);
         GmresOut go;
-        if (!(ok = gmres<A0, F>(cx, a, s, ur, u, op, tau, Dt, sm_cs, sm_sn, sm_g, s_h, go))) break;
+        if (u == MSIR_FP32) {
+          if (!(ok = gmres<A0, F, float>(cx, a, s, ur, u, op, tau, Dt, gsm, go))) break;
+        } else {
+          if (!(ok = gmres<A0, F, double>(cx, a, s, ur, u, op, tau, Dt, gsm, go))) break;
+        }
         kg = go.k;
         nonfinite = go.nonfinite;
       }

@@ -47,7 +47,7 @@ def test_struct_layouts_match_header():
     # int, pad, 4 doubles, 4 ints
     assert ctypes.sizeof(Params) == 4 + 4 + 8 * 4 + 4 * 4
     assert ctypes.sizeof(Stage) == 6 * 4 + 48 * 4
-    assert ctypes.sizeof(Report) == 10 * 4 + 4 * 8 + 24 * ctypes.sizeof(Stage)
+    assert ctypes.sizeof(Report) == 10 * 4 + 12 * 8 + 2 * 4 + 24 * ctypes.sizeof(Stage)
 
 
 def test_params_default_and_status_strings(lib):
