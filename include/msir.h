@@ -190,6 +190,27 @@ msir_status msir_residual(msir_ctx* ctx, int n, const double* A_dev, int lda, in
                           const double* x_dev, const double* b_dev, int ur, double* r_dev,
                           double* s_host);
 
+/* The paper has no counterpart of this entry point: msir_residual for
+ * callers that may not allocate device memory.  Some callers cannot call
+ * cudaMalloc themselves -- code running inside a host framework whose
+ * memory manager owns every device allocation, or code that must not
+ * allocate while a stream is being captured.  This call computes the same
+ * residual r = b_u - A_u x (A_u = fl_u0(A), b_u = fl_u0(b), in ur = FP64 or
+ * DD) and s = ||r||_inf into caller-provided device buffers: A_dev
+ * (column-major, lda), x_dev, b_dev (n doubles), r_dev (n doubles, or 2n
+ * for DD: high words then low words), s_dev (one double, device).  Work is
+ * enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream)
+ * and the call does not wait for it.  Its only scratch is a file-scope
+ * device array (about 8 KB per GPU, held until the process exits); the
+ * first call on a device looks up that array's device address, so make the
+ * first call on each device before any stream capture.  Calls share the
+ * scratch: calls that overlap on the GPU (different streams, or different
+ * host threads on one device) race.  n must be at most 131072
+ * (MSIR_ERR_INVALID otherwise).  Never allocates or frees device memory. */
+msir_status msir_residual_noalloc(int n, const double* A_dev, int lda, int u0,
+                                  const double* x_dev, const double* b_dev, int ur,
+                                  double* r_dev, double* s_dev, void* cuda_stream);
+
 /* Solves A X = B for nrhs right-hand sides with MSIR (Algorithm 4) from the
  * initial precisions t.  A_dev: fp64 column-major n x n (lda >= n); B_dev,
  * X_dev: fp64 column-major n x nrhs (ldb, ldx >= n); 1 <= nrhs <= 16.
