@@ -137,11 +137,11 @@ def run_cpu_baseline(max_seconds=25.0):
     from synth import randsvd_system, workloads
     from oracle import msir as OM, formats as OF
     names = {"fp16": OF.FP16, "bf16": OF.BF16, "fp32": OF.FP32, "fp64": OF.FP64, "dd": OF.DD}
-    t0 = time.time()
+    el = 0.0
     fl = 0.0
     done = []
     for (n, kappa, spec, graded) in workloads(WORKLOAD):
-        if time.time() - t0 > max_seconds and done:
+        if el > max_seconds and done:
             break
         if spec.endswith("dd"):
             continue  # dd GMRES-IR in pure numpy takes many minutes per system
@@ -150,13 +150,12 @@ def run_cpu_baseline(max_seconds=25.0):
         t1 = time.time()
         OM.msir(A, B[:, 0], trip, OM.Params())
         dt = time.time() - t1
+        el += dt
         fl += flops_equiv(n)
         done.append(f"n={n} kappa={kappa:.0e} {spec}{' graded' if graded else ''} {dt:.1f}s")
-        if time.time() - t0 > max_seconds:
-            break
-    el = time.time() - t0
     return {"value": fl / el / 1e12, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "; ".join(done)}
+            "sample": "oracle MSIR on the (half, single, double) systems of the sweep in order, "
+                      "until ~%.0f s: " % max_seconds + "; ".join(done)}
 
 
 def main():
@@ -203,7 +202,7 @@ def main():
     dev = torch.device("cuda", local)
     import paper_2107_06200_gb300 as M
 
-    systems = build_systems(device=dev)
+    systems = build_systems(device=None)  # numpy QR on the host (seeded, deterministic)
     ctx = M.Context(local)
     As = [torch.from_numpy(s["A"]).to(dev) for s in systems]
     bs = [torch.from_numpy(s["b"]).to(dev) for s in systems]
@@ -284,13 +283,17 @@ def main():
         for A, b in zip(As, bs):
             LU, piv = torch.linalg.lu_factor(A)
             torch.linalg.lu_solve(LU, piv, b[:, None])
-    fp64_step()
-    torch.cuda.synchronize()
-    tf = time.perf_counter()
-    fp64_step()
-    torch.cuda.synchronize()
-    fp64_s = time.perf_counter() - tf
-    fp64_val = fl_step / fp64_s / 1e12
+    try:
+        fp64_step()
+        torch.cuda.synchronize()
+        tf = time.perf_counter()
+        fp64_step()
+        torch.cuda.synchronize()
+        fp64_s = time.perf_counter() - tf
+        fp64_val = fl_step / fp64_s / 1e12
+    except Exception as exc:  # e.g. torch's linalg library not loadable in this environment
+        fp64_s, fp64_val = float("nan"), None
+        print(f"fp64 LU comparator unavailable: {exc}", file=sys.stderr)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -308,7 +311,8 @@ def main():
                        "parallelism": f"weak x{world}"},
             "latency_ms": {"p50": p50, "p99": p99},
             "all_converged_nbe_le_2u0": nbe_ok,
-            "fp64_lu": {"value": fp64_val, "unit": UNIT, "ms_per_step": fp64_s * 1e3,
+            "fp64_lu": {"value": fp64_val, "unit": UNIT,
+                        "ms_per_step": None if fp64_val is None else fp64_s * 1e3,
                         "impl": "torch.linalg.lu_factor+lu_solve float64"},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

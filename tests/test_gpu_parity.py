@@ -96,8 +96,8 @@ def test_blocked_lu_pivots_and_backward_error(ctx, uf, u, n, nb, nbo, kappa):
         assert near_tie(trace[j], ipo[j] - j, fac.ipiv[j] - j, scale), j
     if j > 0 and kappa <= 1e4:
         # rows in their original order (later interchanges permute L's rows);
-        # forward differences of the factors grow with kappa, so this check
-        # is made for well-conditioned cases, at 8x the backward-error scale
+        # forward differences of the factors are bounded by the conditioning
+        # times the backward-error scale, so the tolerance is 8 kappa c u_f
         perm_o = OL.ipiv_to_perm(ipo)
         Lg = np.empty_like(fac.F)
         Lo = np.empty_like(Fo)
@@ -105,8 +105,8 @@ def test_blocked_lu_pivots_and_backward_error(ctx, uf, u, n, nb, nbo, kappa):
         Lo[perm_o] = np.tril(Fo, -1)
         Lg, Lo = Lg[:, :j], Lo[:, :j]
         Ug, Uo = np.triu(fac.F)[:j], np.triu(Fo)[:j]
-        assert np.max(np.abs(Lg - Lo)) <= 8 * c_bound * max(1.0, float(np.max(np.abs(Lo))))
-        assert np.max(np.abs(Ug - Uo)) <= 8 * c_bound * float(np.max(LUabs))
+        assert np.max(np.abs(Lg - Lo)) <= 8 * kappa * c_bound * max(1.0, float(np.max(np.abs(Lo))))
+        assert np.max(np.abs(Ug - Uo)) <= 8 * kappa * c_bound * float(np.max(LUabs))
     L, U = OL.unpack(fac.F)
     Af = OF.fl(Au, uf).astype(np.float64)
     E = np.abs(Af[fac.perm] - L @ U)
