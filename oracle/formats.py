@@ -224,6 +224,24 @@ def dd_to_fp64(a):
     return np.asarray(a[0] + a[1], dtype=np.float64)
 
 
+def dd_to_fp32(a):
+    """Round a normalised dd to fp32 correctly (one rounding of hi + lo).
+
+    fl32(hi) is already the answer unless hi lies exactly halfway between
+    two fp32 neighbours; then the sign of lo decides (a nonzero lo moves the
+    exact value off the tie, towards the neighbour on its side)."""
+    hi = np.asarray(a[0], dtype=np.float64)
+    lo = np.asarray(a[1], dtype=np.float64)
+    with np.errstate(all="ignore"):
+        r = hi.astype(np.float32)
+        r64 = r.astype(np.float64)
+        d = hi - r64  # exact: |d| <= half an fp32 ulp of hi
+        other = np.nextafter(r, (r64 + 2.0 * d).astype(np.float32))
+        tie = np.isfinite(r64) & (d != 0) & (other.astype(np.float64) - r64 == 2.0 * d)
+        away = tie & (lo != 0) & (np.sign(lo) == np.sign(d))
+        return np.where(away, other, r)
+
+
 def dd_abs_max(a):
     """max_i |a_i| of a dd vector, returned as fp64 (the high word of the max)."""
     hi = np.abs(a[0])

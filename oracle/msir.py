@@ -91,6 +91,9 @@ class Factorization:
     R: np.ndarray = None
     S: np.ndarray = None
     mu: float = 1.0
+    # inverses of the diagonal blocks of L and U (oracle.trsv), filled on
+    # first use and kept while these factors are in use
+    inv_cache: dict = field(default_factory=dict, repr=False, compare=False)
 
     @property
     def scaled(self):
@@ -242,6 +245,11 @@ def msir(A_in, b_in, triple, params=None, x_ref=None, factor_hook=None):
     if u_of(uf) < u_of(u):
         raise ValueError("u_f must not be more precise than u")
     n = A_in.shape[0]
+    b_in = np.asarray(b_in, np.float64)
+    if b_in.ndim == 2 and b_in.shape[1] == 1:
+        b_in = b_in[:, 0]
+    if b_in.shape != (n,):
+        raise ValueError("b must be a vector of length n")
     u0 = u
     A_u = fl(np.asarray(A_in, np.float64), u0).astype(np.float64)
     b_u = fl(np.asarray(b_in, np.float64), u0).astype(np.float64)

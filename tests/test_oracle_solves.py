@@ -214,3 +214,137 @@ def test_arnoldi_relation_holds_in_working_precision():
     assert rel <= 50 * F.u_of(F.FP32)
     # CGS2 keeps the basis orthonormal to working precision
     assert np.linalg.norm(V.T @ V - np.eye(k + 1)) <= 50 * F.u_of(F.FP32) * np.sqrt(k)
+
+
+# ------------------------------------------- block substitution with inverses
+
+def test_dd_to_fp32_rounds_once():
+    """fl32(hi + lo) from the definition (exact rationals), ties included."""
+    from exact import round_q
+    rng = np.random.default_rng(21)
+    r = rng.standard_normal(300).astype(np.float32)
+    nxt = np.nextafter(r, np.float32(np.inf))
+    mid = (r.astype(np.float64) + nxt.astype(np.float64)) / 2  # exact fp32 ties
+    lo = rng.choice([-1.0, 0.0, 1.0], 300) * np.abs(mid) * 2.0 ** -70
+    hi = np.concatenate([mid, rng.standard_normal(300) * 10.0 ** rng.integers(-30, 30, 300)])
+    lo = np.concatenate([lo, hi[300:] * rng.uniform(-1, 1, 300) * 2.0 ** -54])
+    got = F.dd_to_fp32((hi, lo))
+    for h, l, g in zip(hi, lo, got):
+        assert float(g) == round_q(Fraction(float(h)) + Fraction(float(l)), "fp32")
+
+
+@pytest.mark.parametrize("lower", [True, False])
+def test_block_inverse_against_exact_rationals(lower):
+    rng = np.random.default_rng(22)
+    m = 12
+    B = rng.uniform(-1, 1, (m, m))
+    B = np.tril(B, -1) + np.eye(m) if lower else np.triu(B) + np.diag(np.sign(rng.standard_normal(m)) * 1.5)
+    Xh, Xl = T.inv_block_dd(B, 0, m, lower)
+    Q = [[Fraction(float(v)) for v in row] for row in B]
+    for c in range(m):  # exact column c of B^{-1}
+        x = [Fraction(0)] * m
+        rows = range(m) if lower else range(m - 1, -1, -1)
+        for i in rows:
+            rhs = Fraction(int(i == c))
+            ks = range(i) if lower else range(i + 1, m)
+            rhs -= sum(Q[i][k] * x[k] for k in ks)
+            x[i] = rhs if lower else rhs / Q[i][i]
+        scale = max(abs(v) for v in x)
+        for i in range(m):
+            got = Fraction(float(Xh[i, c])) + Fraction(float(Xl[i, c]))
+            assert abs(got - x[i]) <= Fraction(2) ** -100 * scale
+    # the stored-side entries of the inverse keep the triangle
+    assert np.all((np.triu(Xh, 1) if lower else np.tril(Xh, -1)) == 0)
+
+
+def _sparse_block_factor(n, seed):
+    """Packed factors whose diagonal blocks have exact dyadic inverses
+    (identity for L, diag of powers of two for U) and sparse small
+    off-diagonal blocks, so block substitution is exact in fp32."""
+    rng = np.random.default_rng(seed)
+    Fm = np.zeros((n, n))
+    bl = T.blocks(n)
+    for b, (r0, r1) in enumerate(bl):
+        Fm[np.arange(r0, r1), np.arange(r0, r1)] = rng.choice([-2.0, 1.0, 2.0, 4.0], r1 - r0)
+        for jb, (c0, c1) in enumerate(bl):
+            if jb == b:
+                continue
+            for i in range(r0, r1):
+                j = rng.integers(c0, c1)
+                Fm[i, j] = rng.choice([-1.0, -0.5, 0.5, 1.0])
+    return Fm
+
+
+@pytest.mark.parametrize("arith", [F.FP32, F.FP64])
+def test_block_substitution_exact_across_blocks(arith):
+    n = 150  # two full blocks and a ragged one
+    Fm = _sparse_block_factor(n, 23)
+    Lm = np.tril(Fm, -1) + np.eye(n)
+    U = np.triu(Fm)
+    x_true = np.random.default_rng(24).integers(-3, 4, n).astype(float)
+    y_true = U @ x_true
+    c = Lm @ y_true
+    y = T.lower_unit(Fm, c, arith, arith)
+    assert np.array_equal(y, y_true)
+    x = T.upper(Fm, y_true, arith, arith)
+    assert np.array_equal(x, x_true)
+    yd = T.lower_unit_dd(Fm, F.dd(c))
+    assert np.array_equal(yd[0], y_true) and np.all(yd[1] == 0)
+    xd = T.upper_dd(Fm, F.dd(y_true))
+    assert np.array_equal(xd[0], x_true) and np.all(xd[1] == 0)
+
+
+def test_block_substitution_against_exact_rationals():
+    """GEPP factors of a random matrix, n = 150 (ragged last block): fp64
+    within a small multiple of n u cond, dd within 2^-96."""
+    rng = np.random.default_rng(25)
+    n = 150
+    import scipy.linalg as sla
+    lu, piv = sla.lu_factor(rng.standard_normal((n, n)))
+    c = rng.standard_normal(n)
+    Q = [[Fraction(float(v)) for v in row] for row in lu]
+    cq = [Fraction(float(v)) for v in c]
+    yq = []
+    for i in range(n):
+        yq.append(cq[i] - sum(Q[i][k] * yq[k] for k in range(i)))
+    xq = [Fraction(0)] * n
+    for i in range(n - 1, -1, -1):
+        xq[i] = (yq[i] - sum(Q[i][k] * xq[k] for k in range(i + 1, n))) / Q[i][i]
+    ye = np.array([float(v) for v in yq])
+    xe = np.array([float(v) for v in xq])
+    Lm, U = np.tril(lu, -1) + np.eye(n), np.triu(lu)
+    kL = np.linalg.cond(Lm, np.inf)
+    kU = np.linalg.cond(U, np.inf)
+    y = T.lower_unit(lu, c, F.FP64, F.FP64)
+    assert np.max(np.abs(y - ye)) <= 4 * n * 2.0 ** -53 * kL * np.max(np.abs(ye))
+    x = T.upper(lu, ye, F.FP64, F.FP64)
+    assert np.max(np.abs(x - xe)) <= 4 * n * 2.0 ** -53 * kU * np.max(np.abs(xe))
+    yd = T.lower_unit_dd(lu, F.dd(c))
+    xd = T.upper_dd(lu, yd)
+    for i in range(n):
+        got = Fraction(float(xd[0][i])) + Fraction(float(xd[1][i]))
+        assert abs(got - xq[i]) <= Fraction(2) ** -96 * kU * kL * max(abs(v) for v in xq)
+
+
+@pytest.mark.parametrize("lower", [True, False])
+def test_fp32_block_inverse_is_the_rounded_exact_inverse(lower):
+    """inv_T for T = fp32 is fl32 of the exact inverse, entry by entry."""
+    from exact import round_q
+    rng = np.random.default_rng(26)
+    m = 10
+    B = rng.uniform(-1, 1, (m, m)).astype(np.float32).astype(np.float64)
+    B = np.tril(B, -1) + np.eye(m) if lower else np.triu(B) + np.diag(np.sign(np.diag(B)) * 1.25)
+    X32 = T.block_inverses(B, lower, F.FP32)[0]
+    X64 = T.block_inverses(B, lower, F.FP64)[0]
+    Q = [[Fraction(float(v)) for v in row] for row in B]
+    for c in range(m):
+        x = [Fraction(0)] * m
+        rows = range(m) if lower else range(m - 1, -1, -1)
+        for i in rows:
+            rhs = Fraction(int(i == c))
+            ks = range(i) if lower else range(i + 1, m)
+            rhs -= sum(Q[i][k] * x[k] for k in ks)
+            x[i] = rhs if lower else rhs / Q[i][i]
+        for i in range(m):
+            assert X32[i, c] == round_q(x[i], "fp32")
+            assert X64[i, c] == round_q(x[i], "fp64")
