@@ -161,6 +161,9 @@ struct Level {  // one factorisation of the current matrix
   double* R = nullptr;
   double* S = nullptr;
   double mu = 1.0;
+  float* inv32 = nullptr;    // inverses of the diagonal blocks (inv.cu)
+  double* inv_hi = nullptr;
+  double* inv_lo = nullptr;
 };
 
 // Device workspace of one slot, sized for systems up to nmax.
@@ -180,6 +183,9 @@ struct Workspace {
   int* perm[3] = {};
   double* R[3] = {};
   double* S[3] = {};
+  float* inv32[3] = {};
+  double* inv_hi[3] = {};
+  double* inv_lo[3] = {};
   void* Ut = nullptr;
   int* map = nullptr;       // map_pos | map_val | map_cnt
   int* iflags = nullptr;    // info, nonfinite, err
@@ -187,13 +193,19 @@ struct Workspace {
   double* V = nullptr;
   int ldv = 0;
   double *H, *yv, *red, *hred, *hvec;
-  unsigned* flags = nullptr;
+  unsigned long long* ll = nullptr;  // substitution hand-off words
   unsigned* bar = nullptr;
   RefState* st = nullptr;
   msir_report* rep = nullptr;
   int* ident = nullptr;
   unsigned long long* tsv = nullptr;
 };
+
+// bytes of the substitution hand-off buffer for size n (zeroed whenever the
+// substitution epoch restarts)
+static size_t ll_bytes(int n) {
+  return (size_t)((n + kBlk - 1) / kBlk) * kBlk * kLLWords * sizeof(unsigned long long);
+}
 
 static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_level, char* base) {
   size_t off = 0;
@@ -218,6 +230,10 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
     w.perm[l] = (int*)take(n * 4);
     w.R[l] = (double*)take(n * 8);
     w.S[l] = (double*)take(n * 8);
+    const size_t ninv = lvl_bytes[l] ? (size_t)2 * ((n + kBlk - 1) / kBlk) * kBlk * kBlk : 0;
+    w.inv32[l] = ninv ? (float*)take(ninv * 4) : nullptr;
+    w.inv_hi[l] = ninv ? (double*)take(ninv * 8) : nullptr;
+    w.inv_lo[l] = ninv ? (double*)take(ninv * 8) : nullptr;
   }
   w.Ut = take((size_t)n * 256 * 2);
   w.map = (int*)take((4 * 256 + 8) * 4);
@@ -232,7 +248,7 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
   w.red = (double*)take((size_t)2 * G * kRedW * 8);
   w.hred = (double*)take((size_t)G * (kcap + 1) * 8);
   w.hvec = (double*)take((size_t)(kcap + 1) * 8);
-  w.flags = (unsigned*)take(((size_t)(n + kBlk - 1) / kBlk + 1) * kFlagStride * 4);
+  w.ll = (unsigned long long*)take(ll_bytes(n));
   w.bar = (unsigned*)take(64);
   w.st = (RefState*)take(sizeof(RefState));
   w.rep = (msir_report*)take(sizeof(msir_report));
@@ -408,6 +424,11 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
   }
   CK(ipiv_to_perm(L.ipiv, n, L.perm, st));
   *launches += 1;
+  L.inv32 = w.inv32[l];
+  L.inv_hi = w.inv_hi[l];
+  L.inv_lo = w.inv_lo[l];
+  CK(launch_inv_diag(fmt, L.F, ldf, n, L.inv32, L.inv_hi, L.inv_lo, st));
+  *launches += 1;
   return MSIR_OK;
 }
 
@@ -528,7 +549,8 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   a.y_hi = w.y_hi; a.y_lo = w.y_lo; a.z_hi = w.z_hi; a.z_lo = w.z_lo;
   a.d = w.d; a.w = w.w; a.V = w.V; a.ldv = w.ldv;
   a.H = w.H; a.yv = w.yv; a.red = w.red; a.hred = w.hred; a.hvec = w.hvec;
-  a.flags = w.flags; a.bar = w.bar; a.err = w.iflags + 2; a.st = w.st; a.rep = w.rep;
+  a.ll = w.ll; a.bar = w.bar;
+  a.inv32 = L.inv32; a.inv_hi = L.inv_hi; a.inv_lo = L.inv_lo; a.err = w.iflags + 2; a.st = w.st; a.rep = w.rep;
   a.tsv = trsv_timers_enabled() ? w.tsv : nullptr;
   a.i_max = j.p.i_max;
   a.rho_thresh = j.p.rho_thresh;
@@ -685,7 +707,7 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
   s.state.ur = j.t.ur;
   s.state.delta_prev = INFINITY;
   CK(cudaMemsetAsync(s.w.rep, 0, sizeof(msir_report), s.st));
-  CK(cudaMemsetAsync(s.w.flags, 0, ((size_t)(j.n + kBlk - 1) / kBlk + 1) * kFlagStride * 4, s.st));
+  CK(cudaMemsetAsync(s.w.ll, 0, ll_bytes(j.n), s.st));
   s.factoring_initial = true;
   const int li = level_index(j.t.uf);
   if (same && s.lv[li].valid && s.lv[li].fmt == j.t.uf) {
@@ -1051,7 +1073,7 @@ msir_status msir_factors_apply(msir_ctx* ctx, const msir_factors* fc, int nrhs, 
   if (arith != MSIR_DD && (store < MSIR_BF16 || store > MSIR_FP64)) return MSIR_ERR_INVALID;
   CK(cudaSetDevice(ctx->device));
   Slot& s = const_cast<Slot&>(fc->slot);
-  CK(cudaMemsetAsync(s.w.flags, 0, ((size_t)(n + kBlk - 1) / kBlk + 1) * kFlagStride * 4, s.st));
+  CK(cudaMemsetAsync(s.w.ll, 0, ll_bytes(n), s.st));
   RefState st0;
   memset(&st0, 0, sizeof(st0));
   for (int c = 0; c < nrhs; ++c) {

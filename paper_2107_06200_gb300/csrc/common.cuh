@@ -115,6 +115,11 @@ __device__ __forceinline__ dd_t dd_mul_d(dd_t a, double d) {
   double e = __dadd_rn(p.lo, __dmul_rn(a.lo, d));
   return fast_two_sum(p.hi, e);
 }
+__device__ __forceinline__ dd_t dd_mul(dd_t a, dd_t b) {
+  dd_t p = two_prod(a.hi, b.hi);
+  double e = __dadd_rn(p.lo, __dadd_rn(__dmul_rn(a.hi, b.lo), __dmul_rn(a.lo, b.hi)));
+  return fast_two_sum(p.hi, e);
+}
 __device__ __forceinline__ dd_t dd_div_d(dd_t a, double d) {
   double q1 = __ddiv_rn(a.hi, d);
   dd_t r = dd_sub(a, dd_mul_d(dd_t{d, 0.0}, q1));

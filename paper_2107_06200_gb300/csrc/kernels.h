@@ -60,4 +60,9 @@ struct TcUpdateArgs {
 cudaError_t launch_update_tc(int fmt, const void* tmA, const void* tmB, const TcUpdateArgs& a,
                              int num_sms, cudaStream_t st);
 
+// Inverses of the 64x64 diagonal blocks of L and U (inv.cu): outputs are
+// [2][ceil(n/64)][64][64] (triangle 0 = L, 1 = U).
+cudaError_t launch_inv_diag(int fmt, const void* LU, int ldf, int n, float* inv32, double* inv_hi,
+                            double* inv_lo, cudaStream_t st);
+
 }  // namespace msir

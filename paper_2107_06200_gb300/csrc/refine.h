@@ -11,9 +11,12 @@ namespace msir {
 constexpr int kRefThreads = 256;  // 8 warps
 constexpr int kBlk = 64;          // rows per block of the row distribution / TRSV
 constexpr int kMaxKcap = 2048;    // GMRES iteration cap supported
-// Stride (in unsigned words) between the TRSV flags of consecutive blocks,
-// so that each flag has its own 128-byte line.
-constexpr int kFlagStride = 32;
+// 64-bit payload words per value and block of the substitution hand-off
+// buffer (4: enough for a double-double value).
+constexpr int kLLWords = 4;
+// Shared scratch of the substitutions: 8 warps x 64 staged values plus the
+// 64 values of z, for the widest value type (double-double, 16 bytes).
+constexpr int kTrsvSmem = (kRefThreads / 32 + 1) * kBlk * 16;
 
 enum RefMode { MODE_SOLVE = 0, MODE_APPLY = 1, MODE_RESIDUAL = 2 };
 enum RefPhase {
@@ -31,7 +34,7 @@ struct RefState {
   int uf, u, ur;
   int cged, status;
   int have_phi0;
-  unsigned epoch;     // TRSV flag epoch
+  unsigned epoch;     // substitution epoch (one per triangular solve)
   int nstages;
   int total_steps, total_gmres;
   double rho_max, delta_prev, phi0, phi;
@@ -77,7 +80,10 @@ struct RefineArgs {
   double* red;             // reduction scratch: 2 * gridDim.x * kRedW
   double* hred;            // CGS partial sums: gridDim.x * (kcap+1)
   double* hvec;            // reduced CGS coefficients (kcap+1)
-  unsigned* flags;         // TRSV block flags (ceil(n/kBlk))
+  unsigned long long* ll;  // substitution hand-off words: ceil(n/kBlk) * kBlk * kLLWords
+  const float* inv32;      // inverses of the diagonal blocks of L and U:
+  const double* inv_hi;    // [2][ceil(n/kBlk)][kBlk][kBlk], fp32 and dd
+  const double* inv_lo;
   unsigned* bar;           // grid barrier counter (zeroed before launch)
   int* err;
   RefState* st;

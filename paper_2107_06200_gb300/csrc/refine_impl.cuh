@@ -11,8 +11,8 @@
 // pivoted order i -> perm[i], so the forward substitution of a block needs
 // only rows its own CTA computed.  Triangular solves are wavefronts: a CTA
 // accumulates the off-diagonal products of its block as soon as the blocks
-// it depends on publish their flag (epoch counter, release/acquire), then
-// one warp solves the 64x64 diagonal block by substitution and publishes.
+// it depends on publish their values (epoch-tagged 64-bit words), then
+// applies the inverse of its diagonal block and publishes.
 // Grid barriers are used only where a full vector is needed (matrix-vector
 // products) or a global reduction (norms, Gram-Schmidt coefficients).  The
 // stage controller is replicated in every CTA: all CTAs compute the same
@@ -32,6 +32,7 @@ struct Cx {
   unsigned epoch;
   int redbuf;
   unsigned long long* t_ns;  // per-phase timers (CTA 0, thread 0), shared memory
+  unsigned char* tsm;        // shared scratch of the substitutions (kTrsvSmem bytes)
 };
 
 // Phase timer: CTA 0 / thread 0 accumulates %globaltimer deltas.
@@ -149,14 +150,38 @@ static __device__ double cta_reduce(double v, int op, int tid) {
 }
 
 // ----------------------------------------------------- triangular solves
+//
+// Block substitution with inverted diagonal blocks.  Block b of the forward
+// solve computes z_b = c_b - sum_{j<b} L_bj y_j, then y_b = inv(L_bb) z_b
+// rounded to the storage format; the backward solve runs the same way from
+// the last block up with U.  The inverses come from inv.cu, in the
+// arithmetic format of the solve.
+//
+// Thread (r, seg) of the CTA owning block b handles row r and the 16
+// columns seg*16 .. seg*16+15 of every 64x64 tile of that row block.  As
+// the blocks it depends on become available, the CTA accumulates their
+// tiles (tile loads and payload loads issued one dependency ahead), so when
+// the last one arrives only that tile, a 4-lane reduction, the 64x64
+// product with the inverse and another 4-lane reduction remain on the
+// critical path.
+//
+// Hand-off between CTAs: each solved value is published as 64-bit words
+// carrying 32 payload bits and the 32-bit epoch of the solve.  A 64-bit
+// aligned store or load is single-copy atomic, so a consumer that sees the
+// current epoch in a word also sees that word's payload: no flag, fence or
+// second round trip is needed.  Epochs grow by one per triangular solve and
+// the payload buffer is zeroed whenever the epoch counter restarts.
 
-// Accumulator policies of the substitutions.  V: accumulator, L: factor
-// element after widening, storage of the vectors: float for AccF (so that
-// fp32 solves never touch the scarce fp64 pipe), double for AccD, a pair of
-// double arrays (high, low words) for AccDD.
+// Accumulator policies.  V: value type of the solve; L: factor element
+// after widening; I: inverse element; kW: 32-bit payload words per value.
+// Vectors live in double arrays (fp32 solves store floats in them, so that
+// they never touch the scarce fp64 pipe; dd solves use a high and a low
+// array).
 struct AccF {
   using V = float;
   using L = float;
+  using I = float;
+  static constexpr int kW = 1;
   static __device__ __forceinline__ V zero() { return 0.0f; }
   static __device__ __forceinline__ V load(const double* hi, const double*, int i) {
     return __ldcg((const float*)hi + i);
@@ -169,32 +194,45 @@ struct AccF {
     return (double)((const float*)hi)[i];
   }
   static __device__ __forceinline__ V fma(L l, V y, V acc) { return __fmaf_rn(l, y, acc); }
-  static __device__ __forceinline__ V mul(L l, V y) { return __fmul_rn(l, y); }
+  static __device__ __forceinline__ V ifma(I x, V z, V acc) { return __fmaf_rn(x, z, acc); }
+  static __device__ __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return __fsub_rn(a, b); }
-  static __device__ __forceinline__ V div(V a, L d) { return __fdiv_rn(a, d); }
   static __device__ __forceinline__ V store(V v, int fmt) { return round_f(v, fmt); }
-  static __device__ __forceinline__ V wsum(V v) { return warp_sum_f(v); }
-  static __device__ __forceinline__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  static __device__ __forceinline__ V sx(V v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  static __device__ __forceinline__ I inv(const RefineArgs& a, size_t o) { return __ldg(a.inv32 + o); }
+  static __device__ __forceinline__ unsigned word(V v, int) { return __float_as_uint(v); }
+  static __device__ __forceinline__ V unword(const unsigned* w) { return __uint_as_float(w[0]); }
 };
 struct AccD {
   using V = double;
   using L = double;
+  using I = double;
+  static constexpr int kW = 2;
   static __device__ __forceinline__ V zero() { return 0.0; }
   static __device__ __forceinline__ V load(const double* hi, const double*, int i) { return __ldcg(hi + i); }
   static __device__ __forceinline__ void save(double* hi, double*, int i, V v) { hi[i] = v; }
   static __device__ __forceinline__ void put(double* hi, double*, int i, double h, double) { hi[i] = h; }
   static __device__ __forceinline__ double get(const double* hi, const double*, int i) { return hi[i]; }
   static __device__ __forceinline__ V fma(L l, V y, V acc) { return __fma_rn(l, y, acc); }
-  static __device__ __forceinline__ V mul(L l, V y) { return __dmul_rn(l, y); }
+  static __device__ __forceinline__ V ifma(I x, V z, V acc) { return __fma_rn(x, z, acc); }
+  static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return __dsub_rn(a, b); }
-  static __device__ __forceinline__ V div(V a, L d) { return __ddiv_rn(a, d); }
   static __device__ __forceinline__ V store(V v, int) { return v; }
-  static __device__ __forceinline__ V wsum(V v) { return warp_sum_d(v); }
-  static __device__ __forceinline__ V shfl(V v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+  static __device__ __forceinline__ V sx(V v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+  static __device__ __forceinline__ I inv(const RefineArgs& a, size_t o) { return __ldg(a.inv_hi + o); }
+  static __device__ __forceinline__ unsigned word(V v, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return k == 0 ? (unsigned)b : (unsigned)(b >> 32);
+  }
+  static __device__ __forceinline__ V unword(const unsigned* w) {
+    return __longlong_as_double((long long)(((unsigned long long)w[1] << 32) | w[0]));
+  }
 };
 struct AccDD {
   using V = dd_t;
   using L = double;
+  using I = dd_t;
+  static constexpr int kW = 4;
   static __device__ __forceinline__ V zero() { return dd_t{0.0, 0.0}; }
   static __device__ __forceinline__ V load(const double* hi, const double* lo, int i) {
     return dd_t{__ldcg(hi + i), __ldcg(lo + i)};
@@ -208,38 +246,178 @@ struct AccDD {
     return __dadd_rn(hi[i], lo[i]);
   }
   static __device__ __forceinline__ V fma(L l, V y, V acc) { return dd_add(acc, dd_mul_d(y, l)); }
-  static __device__ __forceinline__ V mul(L l, V y) { return dd_mul_d(y, l); }
+  static __device__ __forceinline__ V ifma(I x, V z, V acc) { return dd_add(acc, dd_mul(x, z)); }
+  static __device__ __forceinline__ V add(V a, V b) { return dd_add(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return dd_sub(a, b); }
-  static __device__ __forceinline__ V div(V a, L d) { return dd_div_d(a, d); }
   static __device__ __forceinline__ V store(V v, int) { return v; }
-  static __device__ __forceinline__ V wsum(V v) { return warp_sum_dd(v); }
-  static __device__ __forceinline__ V shfl(V v, int src) {
-    return dd_t{__shfl_sync(0xffffffffu, v.hi, src), __shfl_sync(0xffffffffu, v.lo, src)};
+  static __device__ __forceinline__ V sx(V v, int m) { return dd_shfl_xor(v, m); }
+  static __device__ __forceinline__ I inv(const RefineArgs& a, size_t o) {
+    return dd_t{__ldg(a.inv_hi + o), __ldg(a.inv_lo + o)};
+  }
+  static __device__ __forceinline__ unsigned word(V v, int k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(k < 2 ? v.hi : v.lo);
+    return (k & 1) ? (unsigned)(b >> 32) : (unsigned)b;
+  }
+  static __device__ __forceinline__ V unword(const unsigned* w) {
+    return dd_t{__longlong_as_double((long long)(((unsigned long long)w[1] << 32) | w[0])),
+                __longlong_as_double((long long)(((unsigned long long)w[3] << 32) | w[2]))};
   }
 };
 
-template <typename Lt, typename F>
-__device__ __forceinline__ Lt ld_fac(const F* p) {
-  return (Lt)to_f(*p);
+constexpr int kSegs = 4;               // threads per row of a block
+constexpr int kSegW = kBlk / kSegs;    // columns per thread in a 64x64 tile
+static_assert(kRefThreads == kBlk * kSegs, "one thread per (row, segment)");
+
+// 16 consecutive factor values (32-byte aligned), widened.
+template <typename F> struct Seg16;
+template <> struct Seg16<float> {
+  template <typename Lt>
+  static __device__ __forceinline__ void ld(const float* p, Lt (&v)[kSegW]) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float4 f = __ldg((const float4*)p + m);
+      v[4 * m] = (Lt)f.x; v[4 * m + 1] = (Lt)f.y; v[4 * m + 2] = (Lt)f.z; v[4 * m + 3] = (Lt)f.w;
+    }
+  }
+};
+template <> struct Seg16<double> {
+  template <typename Lt>
+  static __device__ __forceinline__ void ld(const double* p, Lt (&v)[kSegW]) {
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+      const double2 f = __ldg((const double2*)p + m);
+      v[2 * m] = (Lt)f.x; v[2 * m + 1] = (Lt)f.y;
+    }
+  }
+};
+// 16-bit formats: each 32-bit word holds two values, the lower address in
+// the low half
+__device__ __forceinline__ float h16_to_f(unsigned short b, __half*) { return __half2float(__ushort_as_half(b)); }
+__device__ __forceinline__ float h16_to_f(unsigned short b, __nv_bfloat16*) { return __uint_as_float((unsigned)b << 16); }
+template <typename H> struct Seg16H {
+  template <typename Lt>
+  static __device__ __forceinline__ void ld(const H* p, Lt (&v)[kSegW]) {
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const uint4 u = __ldg((const uint4*)p + m);
+      const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        v[8 * m + 2 * k] = (Lt)h16_to_f((unsigned short)(w[k] & 0xffffu), (H*)nullptr);
+        v[8 * m + 2 * k + 1] = (Lt)h16_to_f((unsigned short)(w[k] >> 16), (H*)nullptr);
+      }
+    }
+  }
+};
+template <> struct Seg16<__half> : Seg16H<__half> {};
+template <> struct Seg16<__nv_bfloat16> : Seg16H<__nv_bfloat16> {};
+
+// 16 consecutive factor values of one row, widened; zero outside the matrix.
+template <typename F, typename Lt>
+__device__ __forceinline__ void load_seg(const F* LU, int ldf, int n, int row, int col, Lt (&v)[kSegW]) {
+  if (row < n && col + kSegW <= n) {
+    // ldf is a multiple of 64 and col of 16: the 16 values start on a
+    // 32-byte boundary for every storage format
+    Seg16<F>::ld(LU + (size_t)row * ldf + col, v);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kSegW; ++k)
+      v[k] = (row < n && col + k < n) ? (Lt)to_f(LU[(size_t)row * ldf + col + k]) : (Lt)0;
+  }
 }
 
-constexpr int kDtLd = kBlk + 1;
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Payload words of one block held by one lane: values lane and lane + 32.
+template <int W>
+struct LLRaw {
+  unsigned long long w[2][W];
+};
+
+template <int W>
+__device__ __forceinline__ void ll_issue(const unsigned long long* blk, int lane, LLRaw<W>& r) {
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int k = 0; k < W; ++k) r.w[m][k] = ld_relaxed_u64(blk + (size_t)(lane + 32 * m) * W + k);
+}
+
+template <int W>
+__device__ __forceinline__ bool ll_ready(const LLRaw<W>& r, unsigned epoch) {
+  bool ok = true;
+#pragma unroll
+  for (int m = 0; m < 2; ++m)
+#pragma unroll
+    for (int k = 0; k < W; ++k) ok &= (unsigned)(r.w[m][k] >> 32) == epoch;
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Complete the payload of block `blk` whose loads were issued into r: poll
+// until every word carries `epoch`, then stage the 64 values for the warp.
+// Bounded like every device wait (MSIR_ERR_TIMEOUT, or another block's
+// error).
+template <typename ACC>
+__device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsigned epoch, int lane,
+                                            LLRaw<ACC::kW>& r, typename ACC::V* stage, int* err) {
+  constexpr int W = ACC::kW;
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  while (!ll_ready<W>(r, epoch)) {
+    if ((++spins & 255u) == 0u) {
+      int bad = 0;
+      if (lane == 0) {
+        if (t0 == 0) t0 = gtimer();
+        if (ld_volatile_i32(err) != 0) {
+          bad = 1;
+        } else if (gtimer() - t0 > kWaitTimeoutNs) {
+          atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
+          bad = 1;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+    }
+    ll_issue<W>(blk, lane, r);
+  }
+  __syncwarp();  // the previous block's staged values have been consumed
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    unsigned p[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) p[k] = (unsigned)r.w[m][k];
+    stage[lane + 32 * m] = ACC::unword(p);
+  }
+  __syncwarp();
+  return true;
+}
 
 // One triangular solve (LOWER: L y = c, unit diagonal; else U z = y) over
 // all blocks this CTA owns.
+// Not inlined: its register-heavy loop then does not raise the pressure of
+// the rest of the kernel (the call costs a few register saves per solve).
 template <typename F, typename ACC, bool LOWER>
-__device__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt, void* Dt_raw) {
+__device__ __noinline__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt) {
   using V = typename ACC::V;
   using Lt = typename ACC::L;
-  __shared__ V s_sum[kBlk];
-  Lt* Dt = (Lt*)Dt_raw;
+  using I = typename ACC::I;
+  constexpr int W = ACC::kW;
+  constexpr bool kPrefetchInv = W <= 2;  // the dd inverse row would cost 64 registers
+  V* s_stage = (V*)cx.tsm;                       // per warp: 64 staged values
+  V* s_z = s_stage + (kRefThreads / 32) * kBlk;  // z of the block
   const F* LU = (const F*)a.LU;
   const int ldf = a.ldf, n = cx.n;
+  const int r = cx.tid >> 2, seg = cx.tid & 3;
+  V* stage = s_stage + cx.warp * kBlk;
   const unsigned epoch = ++cx.epoch;
+  const int tri = LOWER ? 0 : 1;
   const double* in_hi = LOWER ? a.c_hi : a.y_hi;
   const double* in_lo = LOWER ? a.c_lo : a.y_lo;
-  const double* src_hi = LOWER ? a.y_hi : a.z_hi;  // solved components read from other blocks
-  const double* src_lo = LOWER ? a.y_lo : a.z_lo;
   double* out_hi = LOWER ? a.y_hi : a.z_hi;
   double* out_lo = LOWER ? a.y_lo : a.z_lo;
   const int nmine = cx.cta < cx.nblk ? (cx.nblk - 1 - cx.cta) / cx.G + 1 : 0;
@@ -247,97 +425,73 @@ __device__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt, void* Dt_raw) {
     const int b = LOWER ? cx.cta + q * cx.G : cx.cta + (nmine - 1 - q) * cx.G;
     const int r0 = b * kBlk;
     const int nr = min(kBlk, n - r0);
+    const int row = r0 + r;
     unsigned long long* ts = a.tsv ? a.tsv + ((LOWER ? 0 : 1) * (size_t)cx.nblk + b) * 3 : nullptr;
     if (ts && cx.tid == 0) ts[0] = gtimer();
-    // diagonal tile, transposed: Dt[m][i] = T[r0+i][r0+m]
-    for (int idx = cx.tid; idx < kBlk * kBlk; idx += kRefThreads) {
-      const int i = idx / kBlk, m = idx % kBlk;
-      Lt v = (Lt)0;
-      if (i < nr && m < nr && (LOWER ? m < i : m >= i)) v = ld_fac<Lt>(LU + (size_t)(r0 + i) * ldf + r0 + m);
-      if (!LOWER && i == m && i >= nr) v = (Lt)1;  // padding rows of a partial block: identity
-      Dt[m * kDtLd + i] = v;
+    const V cr = (seg == 0 && r < nr) ? ACC::load(in_hi, in_lo, row) : ACC::zero();
+    const size_t inv_row = (((size_t)tri * cx.nblk + b) * kBlk + r) * kBlk + seg * kSegW;
+    I xinv[kPrefetchInv ? kSegW : 1];
+    if (kPrefetchInv) {
+#pragma unroll
+      for (int k = 0; k < (kPrefetchInv ? kSegW : 1); ++k) xinv[k] = ACC::inv(a, inv_row + k);
     }
-    // off-diagonal products
-    V acc[8];
+    // dependencies in the order they become available
+    const int ndep = LOWER ? b : cx.nblk - 1 - b;
+    V acc = ACC::zero();
+    bool ok = true;  // a failed wait ends the warp's loop; the CTA leaves together below
+    if (ndep > 0) {
+      Lt tc[kSegW], tn[kSegW];
+      LLRaw<W> pc, pn;
+      int jb = LOWER ? 0 : cx.nblk - 1;
+      load_seg<F, Lt>(LU, ldf, n, row, jb * kBlk + seg * kSegW, tc);
+      ll_issue<W>(a.ll + (size_t)jb * kBlk * W, cx.lane, pc);
+      for (int t = 0; t < ndep; ++t) {
+        const int jn = LOWER ? jb + 1 : jb - 1;
+        const bool more = t + 1 < ndep;
+        if (more) {
+          load_seg<F, Lt>(LU, ldf, n, row, jn * kBlk + seg * kSegW, tn);
+          ll_issue<W>(a.ll + (size_t)jn * kBlk * W, cx.lane, pn);
+        }
+        if (!ll_complete<ACC>(a.ll + (size_t)jb * kBlk * W, epoch, cx.lane, pc, stage, a.err)) {
+          ok = false;
+          break;
+        }
+        const V* ys = stage + seg * kSegW;
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) acc[rr] = ACC::zero();
-    const int njb = LOWER ? b : cx.nblk - 1 - b;
-    for (int t = 0; t < njb; ++t) {
-      const int jb = LOWER ? t : cx.nblk - 1 - t;
-      const int c0 = jb * kBlk;
-      const int ca = c0 + cx.lane, cb = c0 + 32 + cx.lane;
-      // the tile of L (U) does not depend on the flag: load it first
-      Lt la[8], lb[8];
+        for (int k = 0; k < kSegW; ++k) acc = ACC::fma(tc[k], ys[k], acc);
+        if (!more) break;
 #pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
-        const int row = r0 + cx.warp * 8 + rr;
-        const F* lr = LU + (size_t)row * ldf;
-        la[rr] = (row < n && ca < n) ? ld_fac<Lt>(lr + ca) : (Lt)0;
-        lb[rr] = (row < n && cb < n) ? ld_fac<Lt>(lr + cb) : (Lt)0;
+        for (int k = 0; k < kSegW; ++k) tc[k] = tn[k];
+        pc = pn;
+        jb = jn;
       }
-      if (!wait_flag(a.flags + (size_t)jb * kFlagStride, epoch, a.err)) return false;
-      V y0 = ACC::zero(), y1 = ACC::zero();
-      if (ca < n) y0 = ACC::load(src_hi, src_lo, ca);
-      if (cb < n) y1 = ACC::load(src_hi, src_lo, cb);
-#pragma unroll
-      for (int rr = 0; rr < 8; ++rr) {
-        acc[rr] = ACC::fma(la[rr], y0, acc[rr]);
-        acc[rr] = ACC::fma(lb[rr], y1, acc[rr]);
-      }
     }
-#pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
-      V sm = ACC::wsum(acc[rr]);
-      if (cx.lane == 0) s_sum[cx.warp * 8 + rr] = sm;
-    }
-    __syncthreads();
+    // the four segments of the row: s_r, then z_r = c_r - s_r
+    acc = ACC::add(acc, ACC::sx(acc, 1));
+    acc = ACC::add(acc, ACC::sx(acc, 2));
     if (ts && cx.tid == 0) ts[1] = gtimer();
-    if (cx.warp == 0) {
-      const int l = cx.lane;
-      V z0 = ACC::zero(), z1 = ACC::zero();
-      if (l < nr) z0 = ACC::sub(ACC::load(in_hi, in_lo, r0 + l), s_sum[l]);
-      if (l + 32 < nr) z1 = ACC::sub(ACC::load(in_hi, in_lo, r0 + 32 + l), s_sum[32 + l]);
-      // Fully unrolled: each lane keeps its two rows; rows beyond nr stay 0
-      // and are never stored.  y_m is broadcast from lane m mod 32.
-      V y0 = ACC::zero(), y1 = ACC::zero();
-      if (LOWER) {
+    if (seg == 0) s_z[r] = r < nr ? ACC::sub(cr, acc) : ACC::zero();
+    if (__syncthreads_or(!ok)) return false;
+    // y_r = (inverse row r) z, rounded to the storage format
+    V y = ACC::zero();
+    const V* zs = s_z + seg * kSegW;
 #pragma unroll
-        for (int m = 0; m < 32; ++m) {
-          const V ym = ACC::store(ACC::shfl(z0, m), store_fmt);
-          if (l == m) y0 = ym;
-          if (l > m) z0 = ACC::sub(z0, ACC::mul(Dt[m * kDtLd + l], ym));
-          z1 = ACC::sub(z1, ACC::mul(Dt[m * kDtLd + l + 32], ym));
-        }
-#pragma unroll
-        for (int m = 32; m < 64; ++m) {
-          const V ym = ACC::store(ACC::shfl(z1, m - 32), store_fmt);
-          if (l == m - 32) y1 = ym;
-          if (l + 32 > m) z1 = ACC::sub(z1, ACC::mul(Dt[m * kDtLd + l + 32], ym));
-        }
-      } else {
-#pragma unroll
-        for (int m = 63; m >= 32; --m) {
-          const V xm = ACC::store(ACC::div(ACC::shfl(z1, m - 32), Dt[m * kDtLd + m]), store_fmt);
-          if (l == m - 32) y1 = xm;
-          if (l + 32 < m) z1 = ACC::sub(z1, ACC::mul(Dt[m * kDtLd + l + 32], xm));
-          z0 = ACC::sub(z0, ACC::mul(Dt[m * kDtLd + l], xm));
-        }
-#pragma unroll
-        for (int m = 31; m >= 0; --m) {
-          const V xm = ACC::store(ACC::div(ACC::shfl(z0, m), Dt[m * kDtLd + m]), store_fmt);
-          if (l == m) y0 = xm;
-          if (l < m) z0 = ACC::sub(z0, ACC::mul(Dt[m * kDtLd + l], xm));
-        }
-      }
-      if (l < nr) ACC::save(out_hi, out_lo, r0 + l, y0);
-      if (l + 32 < nr) ACC::save(out_hi, out_lo, r0 + 32 + l, y1);
-      __syncwarp();
-      if (l == 0) {
-        st_release_u32(a.flags + (size_t)b * kFlagStride, epoch);
-        if (ts) ts[2] = gtimer();
-      }
+    for (int k = 0; k < kSegW; ++k) {
+      const I x = kPrefetchInv ? xinv[kPrefetchInv ? k : 0] : ACC::inv(a, inv_row + k);
+      y = ACC::ifma(x, zs[k], y);
     }
-    __syncthreads();
+    y = ACC::add(y, ACC::sx(y, 1));
+    y = ACC::add(y, ACC::sx(y, 2));
+    y = ACC::store(y, store_fmt);
+    if (r >= nr) y = ACC::zero();
+    // publish: segment k writes payload word k of the row (rows past n as 0)
+    if (seg < W) {
+      const unsigned long long wv = ((unsigned long long)epoch << 32) | ACC::word(y, seg);
+      st_relaxed_u64(a.ll + ((size_t)b * kBlk + r) * W + seg, wv);
+    }
+    if (seg == 0 && r < nr) ACC::save(out_hi, out_lo, row, y);
+    if (ts && cx.tid == 0) ts[2] = gtimer();
+    __syncthreads();  // s_z is reused by the next block
   }
   return true;
 }
@@ -346,20 +500,20 @@ __device__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt, void* Dt_raw) {
 // order, scaled by R, rounded to the storage format): forward then backward
 // substitution.  Result in z (natural order, before the S*mu scaling).
 template <typename F, typename ACC>
-__device__ bool msolve(Cx& cx, const RefineArgs& a, int store_fmt, void* Dt) {
+__device__ bool msolve(Cx& cx, const RefineArgs& a, int store_fmt) {
   {
     PhaseTimer pt(cx, 1);
-    if (!trsv<F, ACC, true>(cx, a, store_fmt, Dt)) return false;
+    if (!trsv<F, ACC, true>(cx, a, store_fmt)) return false;
   }
   PhaseTimer pt(cx, 2);
-  return trsv<F, ACC, false>(cx, a, store_fmt, Dt);
+  return trsv<F, ACC, false>(cx, a, store_fmt);
 }
 
 template <typename F>
-__device__ bool msolve_arith(Cx& cx, const RefineArgs& a, int arith, int store_fmt, void* Dt) {
-  if (arith == MSIR_FP32) return msolve<F, AccF>(cx, a, store_fmt, Dt);
-  if (arith == MSIR_FP64) return msolve<F, AccD>(cx, a, store_fmt, Dt);
-  return msolve<F, AccDD>(cx, a, store_fmt, Dt);
+__device__ bool msolve_arith(Cx& cx, const RefineArgs& a, int arith, int store_fmt) {
+  if (arith == MSIR_FP32) return msolve<F, AccF>(cx, a, store_fmt);
+  if (arith == MSIR_FP64) return msolve<F, AccD>(cx, a, store_fmt);
+  return msolve<F, AccDD>(cx, a, store_fmt);
 }
 
 // right-hand side element of a substitution in precision `arith`
@@ -588,7 +742,7 @@ __device__ bool grid_sum_sq(Cx& cx, const RefineArgs& a, const U* w, double& out
 
 template <typename A0, typename F, typename U>
 __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int op, double tau,
-                      void* Dt, unsigned char* gsm, GmresOut& out) {
+                      unsigned char* gsm, GmresOut& out) {
   using M = UA<U>;
   __shared__ double s_bc[1];
   const int kcap = a.kcap;
@@ -605,7 +759,7 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads)
       put_c(a, op, i, scaled_r(a, i, s, ur, u) * rscale(a, a.perm[i]), 0.0);
   __syncthreads();
-  if (!msolve_arith<F>(cx, a, op, op, Dt)) return false;
+  if (!msolve_arith<F>(cx, a, op, op)) return false;
   finish_solve<U>(cx, a, w, op);
   double ss;
   if (!grid_sum_sq<U>(cx, a, w, ss)) return false;
@@ -624,7 +778,7 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     // full V_k needed by the matrix-vector product
     if (!grid_barrier(a.bar, a.err, cx.G)) return false;
     if (!apply_A<A0, U>(cx, a, V + (size_t)k * a.ldv, op)) return false;
-    if (!msolve_arith<F>(cx, a, op, op, Dt)) return false;
+    if (!msolve_arith<F>(cx, a, op, op)) return false;
     finish_solve<U>(cx, a, w, op);
     // classical Gram-Schmidt, twice
     cgs_partials<U>(cx, a, V, w, k + 1);
@@ -749,12 +903,12 @@ static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, doubl
 template <typename A0, typename F>
 __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  void* Dt = smem_raw;                                               // kBlk x kDtLd (double)
-  unsigned char* gsm = smem_raw + sizeof(double) * kBlk * kDtLd;     // GMRES scalars
+  unsigned char* gsm = smem_raw + kTrsvSmem;  // GMRES scalars
   __shared__ RefState S;
   __shared__ int s_act, s_reset;
 
   Cx cx;
+  cx.tsm = smem_raw;
   cx.G = gridDim.x;
   cx.cta = blockIdx.x;
   cx.tid = threadIdx.x;
@@ -783,7 +937,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
         put_c(a, a.ap_arith, i, a.ap_arith == MSIR_DD ? v : round_to(v, a.ap_store), 0.0);
       }
     __syncthreads();
-    ok = msolve_arith<F>(cx, a, a.ap_arith, a.ap_store, Dt);
+    ok = msolve_arith<F>(cx, a, a.ap_arith, a.ap_store);
     if (ok) FOR_MY_ROWS(cx, i) a.ap_out[i] = get_z(a, a.ap_arith, i) * cscale(a, i);
   } else {
     // ------------------------------------------------------------ MSIR
@@ -803,7 +957,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
           put_c(a, arith_f, i, round_to(bt * rscale(a, pr), S.uf), 0.0);
         }
       __syncthreads();
-      ok = msolve_arith<F>(cx, a, arith_f, S.uf, Dt);
+      ok = msolve_arith<F>(cx, a, arith_f, S.uf);
       if (!ok) goto finish;
       {
         const double nb_u = urnd(a.normb, S.u);
@@ -871,7 +1025,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
             put_c(a, arith_f, i, round_to(rt * rscale(a, a.perm[i]), S.uf), 0.0);
           }
         __syncthreads();
-        if (!(ok = msolve_arith<F>(cx, a, arith_f, S.uf, Dt))) break;
+        if (!(ok = msolve_arith<F>(cx, a, arith_f, S.uf))) break;
         FOR_MY_ROWS(cx, i) a.d[i] = urnd(get_z(a, arith_f, i) * cscale(a, i), u);
         __syncthreads();
       } else {
@@ -879,9 +1033,9 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
         const double tau = a.tau > 0.0 ? a.tau : (u == MSIR_FP32 ? 1e-6 : 1e-10);
         GmresOut go;
         if (u == MSIR_FP32) {
-          if (!(ok = gmres<A0, F, float>(cx, a, s, ur, u, op, tau, Dt, gsm, go))) break;
+          if (!(ok = gmres<A0, F, float>(cx, a, s, ur, u, op, tau, gsm, go))) break;
         } else {
-          if (!(ok = gmres<A0, F, double>(cx, a, s, ur, u, op, tau, Dt, gsm, go))) break;
+          if (!(ok = gmres<A0, F, double>(cx, a, s, ur, u, op, tau, gsm, go))) break;
         }
         kg = go.k;
         nonfinite = go.nonfinite;

@@ -8,12 +8,10 @@ namespace msir {
 
 template <typename A0, typename F> void* refine_entry();
 
-constexpr int kDtLdL = kBlk + 1;
-
 // ---------------------------------------------------------- launchers
 
 size_t refine_smem_bytes(int kcap) {
-  return sizeof(double) * ((size_t)kBlk * kDtLdL + 3 * ((size_t)kcap + 2) + 2 * ((size_t)kcap + 1));
+  return kTrsvSmem + sizeof(double) * (3 * ((size_t)kcap + 2) + 2 * ((size_t)kcap + 1));
 }
 
 template <typename A0, typename F>
