@@ -204,7 +204,7 @@ struct Workspace {
 // bytes of the substitution hand-off buffer for size n (zeroed whenever the
 // substitution epoch restarts)
 static size_t ll_bytes(int n) {
-  return (size_t)((n + kBlk - 1) / kBlk) * kBlk * kLLWords * sizeof(unsigned long long);
+  return (size_t)4 * ((n + kBlk - 1) / kBlk) * kBlk * kLLWords * sizeof(unsigned long long);
 }
 
 static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_level, char* base) {
@@ -262,13 +262,14 @@ static int kcap_of(int n, double kmax_frac) {
   return std::max(1, std::min(k, kMaxKcap));
 }
 
-// Grid of the refinement kernel for size n: one CTA per 64-row block for
-// the substitution wavefronts, and enough CTAs that the O(n^2) fp64 work
-// (residual, u^2 operator) is spread over the SMs; never more than the SMs.
+// Grid of the refinement kernel for size n: up to four CTAs per 64-row
+// block (fp64 and double-double substitutions split each block over a team
+// of CTAs), and enough CTAs that the O(n^2) fp64 work (residual, u^2
+// operator) is spread over the SMs; never more than the SMs.
 static int refine_grid(msir_ctx* ctx, int n, int share) {
   const int nblk = (n + kBlk - 1) / kBlk;
   const long long work = ((long long)n * n + 16383) / 16384;
-  int g = (int)std::min<long long>(ctx->num_sms, std::max<long long>(nblk, work));
+  int g = (int)std::min<long long>(ctx->num_sms, std::max<long long>(4LL * nblk, work));
   if (share > 1) g = std::max(1, std::min(g, ctx->num_sms / share));
   return g;
 }
@@ -576,6 +577,22 @@ static bool trsv_timers_enabled() {
   return v == 1;
 }
 
+// MSIR_DEBUG_WAITS=1: after a device wait ran out, print where (the site
+// record the kernels leave next to the error flag; diagnostics only).
+static void print_wait_site(Slot& s) {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = getenv("MSIR_DEBUG_WAITS");
+    v = (e && e[0] == '1') ? 1 : 0;
+  }
+  if (v != 1) return;
+  int d[5] = {0, 0, 0, 0, 0};
+  cudaMemcpy(d, s.w.iflags + 24, sizeof(d), cudaMemcpyDeviceToHost);  // err (iflags + 2) + 22
+  static const char* names[] = {"?", "grid barrier", "substitution hand-off", "?", "tensor-core mbarrier"};
+  fprintf(stderr, "[msir wait] n=%d G=%d site=%s block=%d values=%d %d %d (0x%x; 0x%x)\n", s.job ? s.job->n : 0, s.G,
+          names[(d[0] >= 0 && d[0] <= 4) ? d[0] : 0], d[1], d[2], d[3], d[4], (unsigned)d[2], (unsigned)d[4]);
+}
+
 static void print_trsv_timers(Slot& s) {
   if (!trsv_timers_enabled() || !s.job) return;
   const int nblk = (s.job->n + kBlk - 1) / kBlk;
@@ -755,7 +772,7 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
     L.info = s.h_flags[0];
     L.nonfinite = s.h_flags[1];
     const int err = s.h_flags[2];
-    if (err) { slot_finish(s, err); return false; }
+    if (err) { print_wait_site(s); slot_finish(s, err); return false; }
     const bool good = L.info == 0 && L.nonfinite == 0;
     if (good) {
       L.valid = true;
@@ -793,7 +810,11 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
     print_trsv_timers(s);
     s.state = *s.h_state;
     const int err = s.h_flags[2];
-    if (err || s.state.phase == PH_ERROR) { slot_finish(s, err ? err : MSIR_ERR_TIMEOUT); return false; }
+    if (err || s.state.phase == PH_ERROR) {
+      print_wait_site(s);
+      slot_finish(s, err ? err : MSIR_ERR_TIMEOUT);
+      return false;
+    }
     if (s.state.phase == PH_NEED_ESC) {
       const int nx = next_uf(s.state.uf);
       if (!nx || !j.p.allow_escalation) {

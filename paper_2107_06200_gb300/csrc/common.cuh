@@ -161,6 +161,20 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) {
 // milliseconds; after this the waiter records MSIR_ERR_TIMEOUT and returns.
 constexpr unsigned long long kWaitTimeoutNs = 4000000000ull;
 
+// Record a wait that ran out: the first one sets *err to MSIR_ERR_TIMEOUT
+// and leaves, in err[22..26], where it happened (site, block, three
+// site-specific values) for the host's diagnostics.  err points into an
+// int array of at least 27 entries.
+__device__ __forceinline__ void record_timeout(int* err, int site, int v0, int v1, int v2) {
+  if (atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT) == 0) {
+    err[22] = site;
+    err[23] = (int)blockIdx.x;
+    err[24] = v0;
+    err[25] = v1;
+    err[26] = v2;
+  }
+}
+
 // Grid-wide barrier for a cooperative launch of G blocks.  `count` grows by
 // G per episode and is zeroed by the host before the launch.  Returns false
 // (after recording the error) on timeout or if another block failed.
@@ -179,7 +193,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned
       if ((++spins & 63u) == 0u) {
         if (ld_volatile_i32(err) != 0) { ok = 0; break; }
         if (gtimer() - t0 > kWaitTimeoutNs) {
-          atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
+          record_timeout(err, 1, (int)ld_acquire_u32(count), (int)target, (int)G);
           ok = 0;
           break;
         }
@@ -195,30 +209,6 @@ __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
   unsigned v;
   asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
-}
-
-// Wait until *flag >= epoch.  Called by a whole warp: lane 0 polls with
-// acquire loads; the warp barrier then orders the other lanes' later loads
-// after the producer's release.  Bounded: returns false after recording
-// MSIR_ERR_TIMEOUT or another block's error.
-__device__ __forceinline__ bool wait_flag(const unsigned* flag, unsigned epoch, int* err) {
-  int ok = 1;
-  if ((threadIdx.x & 31) == 0) {
-    unsigned long long t0 = 0;
-    unsigned spins = 0;
-    while ((int)(ld_acquire_u32(flag) - epoch) < 0) {
-      if ((++spins & 1023u) == 0u) {
-        if (t0 == 0) t0 = gtimer();
-        if (ld_volatile_i32(err) != 0) { ok = 0; break; }
-        if (gtimer() - t0 > kWaitTimeoutNs) {
-          atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-  }
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 // ------------------------------------------------------------ reductions

@@ -64,7 +64,7 @@ __device__ __noinline__ bool mbar_wait(uint32_t addr, uint32_t parity, volatile 
         t0 = t;
       } else if (t - t0 > kWaitTimeoutNs) {
         *abort_flag = 1;
-        atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
+        record_timeout(err, 4, (int)addr, (int)parity, (int)threadIdx.x);
         return false;
       }
     }

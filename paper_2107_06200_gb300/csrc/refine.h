@@ -11,8 +11,10 @@ namespace msir {
 constexpr int kRefThreads = 256;  // 8 warps
 constexpr int kBlk = 64;          // rows per block of the row distribution / TRSV
 constexpr int kMaxKcap = 2048;    // GMRES iteration cap supported
-// 64-bit payload words per value and block of the substitution hand-off
-// buffer (4: enough for a double-double value).
+// 64-bit payload words per value of the substitution hand-off buffer (4:
+// enough for a double-double value).  The buffer holds, per direction
+// (forward, backward), the solved values and the team-exchanged z of every
+// block: 2 * 2 * ceil(n/kBlk) * kBlk * kLLWords words.
 constexpr int kLLWords = 4;
 // Shared scratch of the substitutions: 8 warps x 64 staged values plus the
 // 64 values of z, for the widest value type (double-double, 16 bytes).
@@ -80,7 +82,7 @@ struct RefineArgs {
   double* red;             // reduction scratch: 2 * gridDim.x * kRedW
   double* hred;            // CGS partial sums: gridDim.x * (kcap+1)
   double* hvec;            // reduced CGS coefficients (kcap+1)
-  unsigned long long* ll;  // substitution hand-off words: ceil(n/kBlk) * kBlk * kLLWords
+  unsigned long long* ll;  // substitution hand-off words (see kLLWords)
   const float* inv32;      // inverses of the diagonal blocks of L and U:
   const double* inv_hi;    // [2][ceil(n/kBlk)][kBlk][kBlk], fp32 and dd
   const double* inv_lo;

@@ -172,13 +172,15 @@ static __device__ double cta_reduce(double v, int op, int tid) {
 // second round trip is needed.  Epochs grow by one per triangular solve and
 // the payload buffer is zeroed whenever the epoch counter restarts.
 
-// Accumulator policies.  V: value type of the solve; L: factor element
-// after widening; I: inverse element; kW: 32-bit payload words per value.
+// Accumulator policies.  V: value type of the solve; A: running sum of
+// products (fin() turns it into a V); L: factor element after widening;
+// I: inverse element; kW: 32-bit payload words per value.
 // Vectors live in double arrays (fp32 solves store floats in them, so that
 // they never touch the scarce fp64 pipe; dd solves use a high and a low
 // array).
 struct AccF {
   using V = float;
+  using A = float;
   using L = float;
   using I = float;
   static constexpr int kW = 1;
@@ -193,8 +195,10 @@ struct AccF {
   static __device__ __forceinline__ double get(const double* hi, const double*, int i) {
     return (double)((const float*)hi)[i];
   }
-  static __device__ __forceinline__ V fma(L l, V y, V acc) { return __fmaf_rn(l, y, acc); }
-  static __device__ __forceinline__ V ifma(I x, V z, V acc) { return __fmaf_rn(x, z, acc); }
+  static __device__ __forceinline__ A azero() { return 0.0f; }
+  static __device__ __forceinline__ A fma(L l, V y, A acc) { return __fmaf_rn(l, y, acc); }
+  static __device__ __forceinline__ A ifma(I x, V z, A acc) { return __fmaf_rn(x, z, acc); }
+  static __device__ __forceinline__ V fin(A acc) { return acc; }
   static __device__ __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ V store(V v, int fmt) { return round_f(v, fmt); }
@@ -205,6 +209,7 @@ struct AccF {
 };
 struct AccD {
   using V = double;
+  using A = double;
   using L = double;
   using I = double;
   static constexpr int kW = 2;
@@ -213,8 +218,10 @@ struct AccD {
   static __device__ __forceinline__ void save(double* hi, double*, int i, V v) { hi[i] = v; }
   static __device__ __forceinline__ void put(double* hi, double*, int i, double h, double) { hi[i] = h; }
   static __device__ __forceinline__ double get(const double* hi, const double*, int i) { return hi[i]; }
-  static __device__ __forceinline__ V fma(L l, V y, V acc) { return __fma_rn(l, y, acc); }
-  static __device__ __forceinline__ V ifma(I x, V z, V acc) { return __fma_rn(x, z, acc); }
+  static __device__ __forceinline__ A azero() { return 0.0; }
+  static __device__ __forceinline__ A fma(L l, V y, A acc) { return __fma_rn(l, y, acc); }
+  static __device__ __forceinline__ A ifma(I x, V z, A acc) { return __fma_rn(x, z, acc); }
+  static __device__ __forceinline__ V fin(A acc) { return acc; }
   static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ V store(V v, int) { return v; }
@@ -228,8 +235,19 @@ struct AccD {
     return __longlong_as_double((long long)(((unsigned long long)w[1] << 32) | w[0]));
   }
 };
+// Double-double sums of products are accumulated with compensation: each
+// product is split exactly (TwoProduct) and its low-order parts kept apart,
+// the running high word is updated by TwoSum and the rounding errors are
+// summed in a second word (the scheme of Ogita, Rump and Oishi's Dot2,
+// extended by the low words of the dd operands).  About 11 fp64 operations
+// per term instead of 26 for a dd multiply and an accurate dd add, with an
+// error of order n u^2 times the sum of |terms|, as for sums in dd.
+struct DDAcc {
+  double s, c;
+};
 struct AccDD {
   using V = dd_t;
+  using A = DDAcc;
   using L = double;
   using I = dd_t;
   static constexpr int kW = 4;
@@ -245,8 +263,20 @@ struct AccDD {
   static __device__ __forceinline__ double get(const double* hi, const double* lo, int i) {
     return __dadd_rn(hi[i], lo[i]);
   }
-  static __device__ __forceinline__ V fma(L l, V y, V acc) { return dd_add(acc, dd_mul_d(y, l)); }
-  static __device__ __forceinline__ V ifma(I x, V z, V acc) { return dd_add(acc, dd_mul(x, z)); }
+  static __device__ __forceinline__ A azero() { return DDAcc{0.0, 0.0}; }
+  static __device__ __forceinline__ A fma(L l, V y, A acc) {
+    const dd_t p = two_prod(l, y.hi);
+    const double pl = __fma_rn(l, y.lo, p.lo);
+    const dd_t t = two_sum(acc.s, p.hi);
+    return DDAcc{t.hi, __dadd_rn(acc.c, __dadd_rn(t.lo, pl))};
+  }
+  static __device__ __forceinline__ A ifma(I x, V z, A acc) {
+    const dd_t p = two_prod(x.hi, z.hi);
+    const double pl = __fma_rn(x.hi, z.lo, __fma_rn(x.lo, z.hi, p.lo));
+    const dd_t t = two_sum(acc.s, p.hi);
+    return DDAcc{t.hi, __dadd_rn(acc.c, __dadd_rn(t.lo, pl))};
+  }
+  static __device__ __forceinline__ V fin(A acc) { return two_sum(acc.s, acc.c); }
   static __device__ __forceinline__ V add(V a, V b) { return dd_add(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return dd_sub(a, b); }
   static __device__ __forceinline__ V store(V v, int) { return v; }
@@ -264,27 +294,30 @@ struct AccDD {
   }
 };
 
-constexpr int kSegs = 4;               // threads per row of a block
-constexpr int kSegW = kBlk / kSegs;    // columns per thread in a 64x64 tile
-static_assert(kRefThreads == kBlk * kSegs, "one thread per (row, segment)");
+static_assert(kRefThreads == 4 * kBlk, "substitution thread layout");
 
-// 16 consecutive factor values (32-byte aligned), widened.
-template <typename F> struct Seg16;
-template <> struct Seg16<float> {
+// N consecutive factor values of one row (N in {4, 8, 16}), widened.  The
+// first value's column is a multiple of N and rows start on 64-element
+// boundaries, so the N values are aligned to N * sizeof(F) bytes.
+__device__ __forceinline__ float h16_to_f(unsigned short b, __half*) { return __half2float(__ushort_as_half(b)); }
+__device__ __forceinline__ float h16_to_f(unsigned short b, __nv_bfloat16*) { return __uint_as_float((unsigned)b << 16); }
+
+template <typename F, int N> struct SegLd;
+template <int N> struct SegLd<float, N> {
   template <typename Lt>
-  static __device__ __forceinline__ void ld(const float* p, Lt (&v)[kSegW]) {
+  static __device__ __forceinline__ void ld(const float* p, Lt (&v)[N]) {
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
+    for (int m = 0; m < N / 4; ++m) {
       const float4 f = __ldg((const float4*)p + m);
       v[4 * m] = (Lt)f.x; v[4 * m + 1] = (Lt)f.y; v[4 * m + 2] = (Lt)f.z; v[4 * m + 3] = (Lt)f.w;
     }
   }
 };
-template <> struct Seg16<double> {
+template <int N> struct SegLd<double, N> {
   template <typename Lt>
-  static __device__ __forceinline__ void ld(const double* p, Lt (&v)[kSegW]) {
+  static __device__ __forceinline__ void ld(const double* p, Lt (&v)[N]) {
 #pragma unroll
-    for (int m = 0; m < 8; ++m) {
+    for (int m = 0; m < N / 2; ++m) {
       const double2 f = __ldg((const double2*)p + m);
       v[2 * m] = (Lt)f.x; v[2 * m + 1] = (Lt)f.y;
     }
@@ -292,36 +325,38 @@ template <> struct Seg16<double> {
 };
 // 16-bit formats: each 32-bit word holds two values, the lower address in
 // the low half
-__device__ __forceinline__ float h16_to_f(unsigned short b, __half*) { return __half2float(__ushort_as_half(b)); }
-__device__ __forceinline__ float h16_to_f(unsigned short b, __nv_bfloat16*) { return __uint_as_float((unsigned)b << 16); }
-template <typename H> struct Seg16H {
+template <typename H, int N> struct SegLdH {
   template <typename Lt>
-  static __device__ __forceinline__ void ld(const H* p, Lt (&v)[kSegW]) {
+  static __device__ __forceinline__ void ld(const H* p, Lt (&v)[N]) {
+    unsigned w[N / 2];
+    if (N >= 8) {
 #pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const uint4 u = __ldg((const uint4*)p + m);
-      const unsigned w[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        v[8 * m + 2 * k] = (Lt)h16_to_f((unsigned short)(w[k] & 0xffffu), (H*)nullptr);
-        v[8 * m + 2 * k + 1] = (Lt)h16_to_f((unsigned short)(w[k] >> 16), (H*)nullptr);
+      for (int m = 0; m < N / 8; ++m) {
+        const uint4 u = __ldg((const uint4*)p + m);
+        w[4 * m] = u.x; w[4 * m + 1] = u.y; w[4 * m + 2] = u.z; w[4 * m + 3] = u.w;
       }
+    } else {
+      const uint2 u = __ldg((const uint2*)p);
+      w[0] = u.x; w[1] = u.y;
+    }
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      v[2 * k] = (Lt)h16_to_f((unsigned short)(w[k] & 0xffffu), (H*)nullptr);
+      v[2 * k + 1] = (Lt)h16_to_f((unsigned short)(w[k] >> 16), (H*)nullptr);
     }
   }
 };
-template <> struct Seg16<__half> : Seg16H<__half> {};
-template <> struct Seg16<__nv_bfloat16> : Seg16H<__nv_bfloat16> {};
+template <int N> struct SegLd<__half, N> : SegLdH<__half, N> {};
+template <int N> struct SegLd<__nv_bfloat16, N> : SegLdH<__nv_bfloat16, N> {};
 
-// 16 consecutive factor values of one row, widened; zero outside the matrix.
-template <typename F, typename Lt>
-__device__ __forceinline__ void load_seg(const F* LU, int ldf, int n, int row, int col, Lt (&v)[kSegW]) {
-  if (row < n && col + kSegW <= n) {
-    // ldf is a multiple of 64 and col of 16: the 16 values start on a
-    // 32-byte boundary for every storage format
-    Seg16<F>::ld(LU + (size_t)row * ldf + col, v);
+// N consecutive factor values of one row, widened; zero outside the matrix.
+template <typename F, typename Lt, int N>
+__device__ __forceinline__ void load_seg(const F* LU, int ldf, int n, int row, int col, Lt (&v)[N]) {
+  if (row < n && col + N <= n) {
+    SegLd<F, N>::ld(LU + (size_t)row * ldf + col, v);
   } else {
 #pragma unroll
-    for (int k = 0; k < kSegW; ++k)
+    for (int k = 0; k < N; ++k)
       v[k] = (row < n && col + k < n) ? (Lt)to_f(LU[(size_t)row * ldf + col + k]) : (Lt)0;
   }
 }
@@ -365,7 +400,8 @@ __device__ __forceinline__ bool ll_ready(const LLRaw<W>& r, unsigned epoch) {
 // error).
 template <typename ACC>
 __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsigned epoch, int lane,
-                                            LLRaw<ACC::kW>& r, typename ACC::V* stage, int* err) {
+                                            LLRaw<ACC::kW>& r, typename ACC::V* stage, int* err,
+                                            int where) {
   constexpr int W = ACC::kW;
   unsigned long long t0 = 0;
   unsigned spins = 0;
@@ -374,14 +410,29 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
       int bad = 0;
       if (lane == 0) {
         if (t0 == 0) t0 = gtimer();
-        if (ld_volatile_i32(err) != 0) {
-          bad = 1;
-        } else if (gtimer() - t0 > kWaitTimeoutNs) {
-          atomicCAS(err, 0, (int)MSIR_ERR_TIMEOUT);
-          bad = 1;
-        }
+        if (ld_volatile_i32(err) != 0) bad = 1;
+        else if (gtimer() - t0 > kWaitTimeoutNs) bad = 2;
       }
-      if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+      bad = __shfl_sync(0xffffffffu, bad, 0);
+      if (bad == 2) {
+        // diagnostics: the first word still missing and the epoch it holds
+        int idx = -1;
+        unsigned tag = 0;
+#pragma unroll
+        for (int m = 0; m < 2; ++m)
+#pragma unroll
+          for (int k = 0; k < W; ++k)
+            if (idx < 0 && (unsigned)(r.w[m][k] >> 32) != epoch) {
+              idx = (lane + 32 * m) * W + k;
+              tag = (unsigned)(r.w[m][k] >> 32);
+            }
+        const unsigned mk = __ballot_sync(0xffffffffu, idx >= 0);
+        const int src = mk ? __ffs(mk) - 1 : 0;
+        idx = __shfl_sync(0xffffffffu, idx, src);
+        tag = __shfl_sync(0xffffffffu, tag, src);
+        if (lane == 0) record_timeout(err, 2, where, (int)epoch, (idx << 20) | (int)(tag & 0xfffffu));
+      }
+      if (bad) return false;
     }
     ll_issue<W>(blk, lane, r);
   }
@@ -398,102 +449,163 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
 }
 
 // One triangular solve (LOWER: L y = c, unit diagonal; else U z = y) over
-// all blocks this CTA owns.
+// all blocks of this CTA's team.
+//
+// Teams: K CTAs (K in {1, 2, 4}) share each 64-row block, member m taking
+// rows m*64/K .. (m+1)*64/K - 1; teams own blocks t, t + T, t + 2T, ...
+// (T = floor(G / K) teams; CTAs beyond K*T idle).  Each row is handled by
+// TPR = 256 K / 64 adjacent threads, each with 64 / TPR columns of every
+// tile.  With K > 1 the members publish their rows of z_b (tagged words,
+// as for the solved values) and every warp gathers all 64 before applying
+// the inverse: one more hand-off per block, but each member does 1/K of
+// the two 64x64 products, which is what limits the fp64 and dd solves
+// (GB300 has about 2 fp64 operations per clock per SM).
+//
 // Not inlined: its register-heavy loop then does not raise the pressure of
 // the rest of the kernel (the call costs a few register saves per solve).
-template <typename F, typename ACC, bool LOWER>
-__device__ __noinline__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt) {
+template <typename F, typename ACC, bool LOWER, int K>
+__device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fmt, unsigned epoch) {
   using V = typename ACC::V;
   using Lt = typename ACC::L;
   using I = typename ACC::I;
   constexpr int W = ACC::kW;
-  constexpr bool kPrefetchInv = W <= 2;  // the dd inverse row would cost 64 registers
+  constexpr int R = kBlk / K;               // rows per member
+  constexpr int TPR = kRefThreads / R;      // threads per row
+  constexpr int NC = kBlk / TPR;            // columns per thread and tile
+  constexpr bool kPrefetchInv = W * NC <= 32;
+  static_assert(TPR <= 32 && NC >= 4, "team shape");
   V* s_stage = (V*)cx.tsm;                       // per warp: 64 staged values
-  V* s_z = s_stage + (kRefThreads / 32) * kBlk;  // z of the block
+  V* s_z = s_stage + (kRefThreads / 32) * kBlk;  // z of the block (K = 1)
   const F* LU = (const F*)a.LU;
   const int ldf = a.ldf, n = cx.n;
-  const int r = cx.tid >> 2, seg = cx.tid & 3;
+  const int r = cx.tid / TPR, seg = cx.tid % TPR;
   V* stage = s_stage + cx.warp * kBlk;
-  const unsigned epoch = ++cx.epoch;
   const int tri = LOWER ? 0 : 1;
   const double* in_hi = LOWER ? a.c_hi : a.y_hi;
   const double* in_lo = LOWER ? a.c_lo : a.y_lo;
   double* out_hi = LOWER ? a.y_hi : a.z_hi;
   double* out_lo = LOWER ? a.y_lo : a.z_lo;
-  const int nmine = cx.cta < cx.nblk ? (cx.nblk - 1 - cx.cta) / cx.G + 1 : 0;
+  // hand-off words: [direction][y | z][block][64][W]
+  const size_t llblk = (size_t)kBlk * kLLWords;
+  unsigned long long* ll_y = a.ll + (size_t)(2 * tri) * cx.nblk * llblk;
+  unsigned long long* ll_z = a.ll + (size_t)(2 * tri + 1) * cx.nblk * llblk;
+  const int T = cx.G / K;
+  const int team = cx.cta / K, member = cx.cta % K;
+  const int nmine = team < T && team < cx.nblk ? (cx.nblk - 1 - team) / T + 1 : 0;
   for (int q = 0; q < nmine; ++q) {
-    const int b = LOWER ? cx.cta + q * cx.G : cx.cta + (nmine - 1 - q) * cx.G;
+    const int b = LOWER ? team + q * T : team + (nmine - 1 - q) * T;
     const int r0 = b * kBlk;
     const int nr = min(kBlk, n - r0);
-    const int row = r0 + r;
+    const int rr = member * R + r;  // row within the block
+    const int row = r0 + rr;
     unsigned long long* ts = a.tsv ? a.tsv + ((LOWER ? 0 : 1) * (size_t)cx.nblk + b) * 3 : nullptr;
-    if (ts && cx.tid == 0) ts[0] = gtimer();
-    const V cr = (seg == 0 && r < nr) ? ACC::load(in_hi, in_lo, row) : ACC::zero();
-    const size_t inv_row = (((size_t)tri * cx.nblk + b) * kBlk + r) * kBlk + seg * kSegW;
-    I xinv[kPrefetchInv ? kSegW : 1];
+    if (ts && cx.tid == 0 && member == 0) ts[0] = gtimer();
+    // every lane of the row holds c_r: with K > 1 several lanes publish
+    // words of z_r
+    const V cr = rr < nr ? ACC::load(in_hi, in_lo, row) : ACC::zero();
+    const size_t inv_row = (((size_t)tri * cx.nblk + b) * kBlk + rr) * kBlk + seg * NC;
+    I xinv[kPrefetchInv ? NC : 1];
     if (kPrefetchInv) {
 #pragma unroll
-      for (int k = 0; k < (kPrefetchInv ? kSegW : 1); ++k) xinv[k] = ACC::inv(a, inv_row + k);
+      for (int k = 0; k < (kPrefetchInv ? NC : 1); ++k) xinv[k] = ACC::inv(a, inv_row + k);
     }
     // dependencies in the order they become available
     const int ndep = LOWER ? b : cx.nblk - 1 - b;
-    V acc = ACC::zero();
+    typename ACC::A acc = ACC::azero();
     bool ok = true;  // a failed wait ends the warp's loop; the CTA leaves together below
     if (ndep > 0) {
-      Lt tc[kSegW], tn[kSegW];
+      Lt tc[NC], tn[NC];
       LLRaw<W> pc, pn;
       int jb = LOWER ? 0 : cx.nblk - 1;
-      load_seg<F, Lt>(LU, ldf, n, row, jb * kBlk + seg * kSegW, tc);
-      ll_issue<W>(a.ll + (size_t)jb * kBlk * W, cx.lane, pc);
+      load_seg<F, Lt, NC>(LU, ldf, n, row, jb * kBlk + seg * NC, tc);
+      ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
       for (int t = 0; t < ndep; ++t) {
         const int jn = LOWER ? jb + 1 : jb - 1;
         const bool more = t + 1 < ndep;
         if (more) {
-          load_seg<F, Lt>(LU, ldf, n, row, jn * kBlk + seg * kSegW, tn);
-          ll_issue<W>(a.ll + (size_t)jn * kBlk * W, cx.lane, pn);
+          load_seg<F, Lt, NC>(LU, ldf, n, row, jn * kBlk + seg * NC, tn);
+          ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
         }
-        if (!ll_complete<ACC>(a.ll + (size_t)jb * kBlk * W, epoch, cx.lane, pc, stage, a.err)) {
+        if (!ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err,
+                              (tri << 24) | (b << 12) | jb)) {
           ok = false;
           break;
         }
-        const V* ys = stage + seg * kSegW;
+        const V* ys = stage + seg * NC;
 #pragma unroll
-        for (int k = 0; k < kSegW; ++k) acc = ACC::fma(tc[k], ys[k], acc);
+        for (int k = 0; k < NC; ++k) acc = ACC::fma(tc[k], ys[k], acc);
         if (!more) break;
 #pragma unroll
-        for (int k = 0; k < kSegW; ++k) tc[k] = tn[k];
+        for (int k = 0; k < NC; ++k) tc[k] = tn[k];
         pc = pn;
         jb = jn;
       }
     }
-    // the four segments of the row: s_r, then z_r = c_r - s_r
-    acc = ACC::add(acc, ACC::sx(acc, 1));
-    acc = ACC::add(acc, ACC::sx(acc, 2));
-    if (ts && cx.tid == 0) ts[1] = gtimer();
-    if (seg == 0) s_z[r] = r < nr ? ACC::sub(cr, acc) : ACC::zero();
-    if (__syncthreads_or(!ok)) return false;
-    // y_r = (inverse row r) z, rounded to the storage format
-    V y = ACC::zero();
-    const V* zs = s_z + seg * kSegW;
+    // the TPR segments of the row: s_r, then z_r = c_r - s_r
+    V sr = ACC::fin(acc);
 #pragma unroll
-    for (int k = 0; k < kSegW; ++k) {
+    for (int m = 1; m < TPR; m <<= 1) sr = ACC::add(sr, ACC::sx(sr, m));
+    if (ts && cx.tid == 0 && member == 0) ts[1] = gtimer();
+    const V zr = rr < nr ? ACC::sub(cr, sr) : ACC::zero();
+    const V* zs;
+    if (K == 1) {
+      if (seg == 0) s_z[r] = zr;
+      if (__syncthreads_or(!ok)) return false;
+      zs = s_z + seg * NC;
+    } else {
+      if (__syncthreads_or(!ok)) return false;
+      if (seg < W)
+        st_relaxed_u64(ll_z + (size_t)b * llblk + (size_t)rr * W + seg,
+                       ((unsigned long long)epoch << 32) | ACC::word(zr, seg));
+      LLRaw<W> pz;
+      ll_issue<W>(ll_z + (size_t)b * llblk, cx.lane, pz);
+      const bool zok = ll_complete<ACC>(ll_z + (size_t)b * llblk, epoch, cx.lane, pz, stage, a.err,
+                                        (tri << 24) | (1 << 23) | (b << 12) | b);
+      if (__syncthreads_or(!zok)) return false;
+      zs = stage + seg * NC;
+    }
+    // y_r = (inverse row r) z, rounded to the storage format
+    typename ACC::A ya = ACC::azero();
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
       const I x = kPrefetchInv ? xinv[kPrefetchInv ? k : 0] : ACC::inv(a, inv_row + k);
-      y = ACC::ifma(x, zs[k], y);
+      ya = ACC::ifma(x, zs[k], ya);
     }
-    y = ACC::add(y, ACC::sx(y, 1));
-    y = ACC::add(y, ACC::sx(y, 2));
+    V y = ACC::fin(ya);
+#pragma unroll
+    for (int m = 1; m < TPR; m <<= 1) y = ACC::add(y, ACC::sx(y, m));
     y = ACC::store(y, store_fmt);
-    if (r >= nr) y = ACC::zero();
+    if (rr >= nr) y = ACC::zero();
     // publish: segment k writes payload word k of the row (rows past n as 0)
-    if (seg < W) {
-      const unsigned long long wv = ((unsigned long long)epoch << 32) | ACC::word(y, seg);
-      st_relaxed_u64(a.ll + ((size_t)b * kBlk + r) * W + seg, wv);
-    }
-    if (seg == 0 && r < nr) ACC::save(out_hi, out_lo, row, y);
-    if (ts && cx.tid == 0) ts[2] = gtimer();
-    __syncthreads();  // s_z is reused by the next block
+    if (seg < W)
+      st_relaxed_u64(ll_y + (size_t)b * llblk + (size_t)rr * W + seg,
+                     ((unsigned long long)epoch << 32) | ACC::word(y, seg));
+    if (seg == 0 && rr < nr) ACC::save(out_hi, out_lo, row, y);
+    if (ts && cx.tid == 0 && member == 0) ts[2] = gtimer();
+    __syncthreads();  // staged values and s_z are reused by the next block
   }
   return true;
+}
+
+// Team size of a solve in arithmetic ACC: fp32 solves keep one CTA per
+// block (their products are cheap, the extra hand-off would dominate);
+// fp64 and dd solves use the largest K in {4, 2} whose teams cover every
+// block at once, else 1.
+template <typename ACC>
+__device__ __forceinline__ int team_size(const Cx& cx) {
+  if (ACC::kW == 1) return 1;
+  if (cx.G >= 4 * cx.nblk) return 4;
+  if (cx.G >= 2 * cx.nblk) return 2;
+  return 1;
+}
+
+template <typename F, typename ACC, bool LOWER>
+__device__ __forceinline__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt) {
+  const unsigned epoch = ++cx.epoch;
+  const int K = team_size<ACC>(cx);
+  if (ACC::kW > 1 && K == 4) return trsv_team<F, ACC, LOWER, 4>(cx, a, store_fmt, epoch);
+  if (ACC::kW > 1 && K == 2) return trsv_team<F, ACC, LOWER, 2>(cx, a, store_fmt, epoch);
+  return trsv_team<F, ACC, LOWER, 1>(cx, a, store_fmt, epoch);
 }
 
 // M^{-1} applied to the right-hand side already placed in c (permuted
@@ -501,12 +613,18 @@ __device__ __noinline__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt) {
 // substitution.  Result in z (natural order, before the S*mu scaling).
 template <typename F, typename ACC>
 __device__ bool msolve(Cx& cx, const RefineArgs& a, int store_fmt) {
+  // Rows of block b are prepared (c) and consumed (z) by CTA b mod G.  A
+  // team of K > 1 CTAs spreads them over other CTAs, so c must be visible
+  // grid-wide before the forward solve and z after the backward solve.
+  const bool team = team_size<ACC>(cx) > 1;
+  if (team && !grid_barrier(a.bar, a.err, cx.G)) return false;
   {
     PhaseTimer pt(cx, 1);
     if (!trsv<F, ACC, true>(cx, a, store_fmt)) return false;
   }
   PhaseTimer pt(cx, 2);
-  return trsv<F, ACC, false>(cx, a, store_fmt);
+  if (!trsv<F, ACC, false>(cx, a, store_fmt)) return false;
+  return !team || grid_barrier(a.bar, a.err, cx.G);
 }
 
 template <typename F>
@@ -905,7 +1023,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* gsm = smem_raw + kTrsvSmem;  // GMRES scalars
   __shared__ RefState S;
-  __shared__ int s_act, s_reset;
+  __shared__ int s_act, s_reset, s_alg;
 
   Cx cx;
   cx.tsm = smem_raw;
@@ -1084,6 +1202,8 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
       if (!(ok = residual<A0>(cx, a, a.x, ur, s, xnorm))) break;
       nbe = s / (a.normA * xnorm + a.normb);
       const bool better = nbe < S.best_nbe;
+      // every thread has read S before thread 0 updates it (shared memory)
+      __syncthreads();
       if (better) FOR_MY_ROWS(cx, i) a.xbest[i] = a.x[i];
       if (cx.tid == 0) {
         if (better) S.best_nbe = nbe;
@@ -1098,9 +1218,12 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
         int rs = 0;
         s_act = ctl_step(S, a, s_old, md, xnorm_old, nbe, kg, &rs);
         s_reset = rs;
+        s_alg = S.alg;
         S.nbe = nbe;
       }
       __syncthreads();
+      // decisions below use s_act/s_reset/s_alg: thread 0 changes S.alg
+      // inside this branch while other warps may not have reached it yet
       if (s_act == 1) {
         if (cx.tid == 0) { S.cged = 1; S.status = MSIR_OK; }
         break;
@@ -1108,7 +1231,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
       if (s_act == 2) {
         const bool reset = s_reset != 0;
         if (reset) FOR_MY_ROWS(cx, i) a.x[i] = a.x0[i];
-        if (S.alg == MSIR_ALG_GMRES) {
+        if (s_alg == MSIR_ALG_GMRES) {
           if (cx.tid == 0) S.phase = PH_NEED_ESC;
           __syncthreads();
           break;

@@ -260,6 +260,33 @@ def test_batched_equals_single_solves(ctx, M):
             assert r["nbe"] <= 2 * 2.0 ** -24
 
 
+def test_batched_multiblock_ctas_through_stage_switches(ctx, M):
+    """Ten systems share the GPU, so each refinement grid has fewer CTAs
+    than 64-row blocks (several blocks per CTA in the substitutions), and
+    the runs go through SIR -> SGMRES-IR -> GMRES-IR -> escalation, where the
+    substitution precision changes (fp32 -> fp64 -> dd).  Each batched
+    result must match the same system solved alone."""
+    n = 1500
+    cases = [(1e6, HSD, False), (1e8, HSD, False), (1e6, HSD, True), (1e10, SDQ, False),
+             (1e12, SDQ, False), (1e4, HSD, False), (1e8, SDQ, True), (1e6, HSD, False),
+             (1e8, HSD, True), (1e10, SDQ, True)]
+    As, bs, specs = [], [], []
+    for i, (kappa, spec, graded) in enumerate(cases):
+        A, B, _ = randsvd_system(n, kappa, 10 + i, graded=graded)
+        As.append(to_dev(A))
+        bs.append(to_dev(B[:, 0].copy()))
+        specs.append(spec)
+    xs, reps, st = ctx.solve_batched(As, bs, specs)
+    assert st in (M.OK, M.NOT_CONVERGED)
+    for A, b, x, r, spec in zip(As, bs, xs, reps, specs):
+        x1, r1, s1 = ctx.solve(A, b, spec)
+        assert [g[:4] for g in stages_of(r)] == [g[:4] for g in stages_of(r1[0])]
+        assert bool(r["cged"]) == bool(r1[0]["cged"])
+        if r["cged"]:
+            uu = 2.0 ** -24 if spec == HSD else 2.0 ** -53
+            assert r["nbe"] <= 2 * uu
+
+
 def test_server_results_match_solve(ctx, M):
     import time
     srv = M.Server(ctx, max_slots=4)
