@@ -196,6 +196,8 @@ struct AccF {
     return (double)((const float*)hi)[i];
   }
   static __device__ __forceinline__ A azero() { return 0.0f; }
+  static __device__ __forceinline__ A merge(A a, A b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ A ax(A a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
   static __device__ __forceinline__ A fma(L l, V y, A acc) { return __fmaf_rn(l, y, acc); }
   static __device__ __forceinline__ A ifma(I x, V z, A acc) { return __fmaf_rn(x, z, acc); }
   static __device__ __forceinline__ V fin(A acc) { return acc; }
@@ -219,6 +221,8 @@ struct AccD {
   static __device__ __forceinline__ void put(double* hi, double*, int i, double h, double) { hi[i] = h; }
   static __device__ __forceinline__ double get(const double* hi, const double*, int i) { return hi[i]; }
   static __device__ __forceinline__ A azero() { return 0.0; }
+  static __device__ __forceinline__ A merge(A a, A b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ A ax(A a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
   static __device__ __forceinline__ A fma(L l, V y, A acc) { return __fma_rn(l, y, acc); }
   static __device__ __forceinline__ A ifma(I x, V z, A acc) { return __fma_rn(x, z, acc); }
   static __device__ __forceinline__ V fin(A acc) { return acc; }
@@ -264,6 +268,15 @@ struct AccDD {
     return __dadd_rn(hi[i], lo[i]);
   }
   static __device__ __forceinline__ A azero() { return DDAcc{0.0, 0.0}; }
+  // two partial sums: TwoSum of the running words, errors added (exact
+  // error-free step, so every lane of a butterfly gets the same result)
+  static __device__ __forceinline__ A merge(A a, A b) {
+    const dd_t t = two_sum(a.s, b.s);
+    return DDAcc{t.hi, __dadd_rn(__dadd_rn(a.c, b.c), t.lo)};
+  }
+  static __device__ __forceinline__ A ax(A a, int m) {
+    return DDAcc{__shfl_xor_sync(0xffffffffu, a.s, m), __shfl_xor_sync(0xffffffffu, a.c, m)};
+  }
   static __device__ __forceinline__ A fma(L l, V y, A acc) {
     const dd_t p = two_prod(l, y.hi);
     const double pl = __fma_rn(l, y.lo, p.lo);
@@ -454,12 +467,14 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
 // Teams: K CTAs (K in {1, 2, 4}) share each 64-row block, member m taking
 // rows m*64/K .. (m+1)*64/K - 1; teams own blocks t, t + T, t + 2T, ...
 // (T = floor(G / K) teams; CTAs beyond K*T idle).  Each row is handled by
-// TPR = 256 K / 64 adjacent threads, each with 64 / TPR columns of every
-// tile.  With K > 1 the members publish their rows of z_b (tagged words,
-// as for the solved values) and every warp gathers all 64 before applying
-// the inverse: one more hand-off per block, but each member does 1/K of
-// the two 64x64 products, which is what limits the fp64 and dd solves
-// (GB300 has about 2 fp64 operations per clock per SM).
+// 4 adjacent threads with 16 columns of every tile each; a member's 64/K
+// rows use the first 256/K threads (whole warps), the other warps only
+// take part in the barriers.  With K > 1 the members publish their rows of
+// z_b (tagged words, as for the solved values) and every working warp
+// gathers all 64 before applying the inverse: one more hand-off per block,
+// but each member does 1/K of the two 64x64 products, which is what limits
+// the fp64 and dd solves (GB300 issues about 2 fp64 lane operations per
+// clock per SM, so few threads per row keep the reductions cheap).
 //
 // Not inlined: its register-heavy loop then does not raise the pressure of
 // the rest of the kernel (the call costs a few register saves per solve).
@@ -470,15 +485,17 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
   using I = typename ACC::I;
   constexpr int W = ACC::kW;
   constexpr int R = kBlk / K;               // rows per member
-  constexpr int TPR = kRefThreads / R;      // threads per row
+  constexpr int TPR = 4;                    // threads per row
   constexpr int NC = kBlk / TPR;            // columns per thread and tile
-  constexpr bool kPrefetchInv = W * NC <= 32;
-  static_assert(TPR <= 32 && NC >= 4, "team shape");
+  constexpr int NACT = R * TPR;             // working threads (whole warps)
+  constexpr bool kPrefetchInv = W * NC <= 64;
+  static_assert(NACT % 32 == 0 && NACT <= kRefThreads, "team shape");
   V* s_stage = (V*)cx.tsm;                       // per warp: 64 staged values
   V* s_z = s_stage + (kRefThreads / 32) * kBlk;  // z of the block (K = 1)
   const F* LU = (const F*)a.LU;
   const int ldf = a.ldf, n = cx.n;
-  const int r = cx.tid / TPR, seg = cx.tid % TPR;
+  const bool act = cx.tid < NACT;
+  const int r = act ? cx.tid / TPR : 0, seg = cx.tid % TPR;
   V* stage = s_stage + cx.warp * kBlk;
   const int tri = LOWER ? 0 : 1;
   const double* in_hi = LOWER ? a.c_hi : a.y_hi;
@@ -502,10 +519,10 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
     if (ts && cx.tid == 0 && member == 0) ts[0] = gtimer();
     // every lane of the row holds c_r: with K > 1 several lanes publish
     // words of z_r
-    const V cr = rr < nr ? ACC::load(in_hi, in_lo, row) : ACC::zero();
+    const V cr = (act && rr < nr) ? ACC::load(in_hi, in_lo, row) : ACC::zero();
     const size_t inv_row = (((size_t)tri * cx.nblk + b) * kBlk + rr) * kBlk + seg * NC;
     I xinv[kPrefetchInv ? NC : 1];
-    if (kPrefetchInv) {
+    if (kPrefetchInv && act) {
 #pragma unroll
       for (int k = 0; k < (kPrefetchInv ? NC : 1); ++k) xinv[k] = ACC::inv(a, inv_row + k);
     }
@@ -513,8 +530,13 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
     const int ndep = LOWER ? b : cx.nblk - 1 - b;
     typename ACC::A acc = ACC::azero();
     bool ok = true;  // a failed wait ends the warp's loop; the CTA leaves together below
-    if (ndep > 0) {
-      Lt tc[NC], tn[NC];
+    if (ndep > 0 && act) {
+      // fp32/fp64: tile and payload loads one dependency ahead (double
+      // buffer); dd: the next tile is loaded after the current one is used
+      // (its products, not the loads, bound the dd solve, and a second
+      // buffer of 16 doubles per thread would spill)
+      constexpr bool kDouble = W <= 2;
+      Lt tc[NC], tn[kDouble ? NC : 1];
       LLRaw<W> pc, pn;
       int jb = LOWER ? 0 : cx.nblk - 1;
       load_seg<F, Lt, NC>(LU, ldf, n, row, jb * kBlk + seg * NC, tc);
@@ -522,8 +544,8 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
       for (int t = 0; t < ndep; ++t) {
         const int jn = LOWER ? jb + 1 : jb - 1;
         const bool more = t + 1 < ndep;
-        if (more) {
-          load_seg<F, Lt, NC>(LU, ldf, n, row, jn * kBlk + seg * NC, tn);
+        if (kDouble && more) {
+          load_seg<F, Lt, NC>(LU, ldf, n, row, jn * kBlk + seg * NC, *(Lt(*)[NC])tn);
           ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
         }
         if (!ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err,
@@ -535,16 +557,21 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
 #pragma unroll
         for (int k = 0; k < NC; ++k) acc = ACC::fma(tc[k], ys[k], acc);
         if (!more) break;
+        if (kDouble) {
 #pragma unroll
-        for (int k = 0; k < NC; ++k) tc[k] = tn[k];
-        pc = pn;
+          for (int k = 0; k < NC; ++k) tc[k] = tn[kDouble ? k : 0];
+          pc = pn;
+        } else {
+          load_seg<F, Lt, NC>(LU, ldf, n, row, jn * kBlk + seg * NC, tc);
+          ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pc);
+        }
         jb = jn;
       }
     }
     // the TPR segments of the row: s_r, then z_r = c_r - s_r
-    V sr = ACC::fin(acc);
 #pragma unroll
-    for (int m = 1; m < TPR; m <<= 1) sr = ACC::add(sr, ACC::sx(sr, m));
+    for (int m = 1; m < TPR; m <<= 1) acc = ACC::merge(acc, ACC::ax(acc, m));
+    const V sr = ACC::fin(acc);
     if (ts && cx.tid == 0 && member == 0) ts[1] = gtimer();
     const V zr = rr < nr ? ACC::sub(cr, sr) : ACC::zero();
     const V* zs;
@@ -554,33 +581,37 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
       zs = s_z + seg * NC;
     } else {
       if (__syncthreads_or(!ok)) return false;
-      if (seg < W)
-        st_relaxed_u64(ll_z + (size_t)b * llblk + (size_t)rr * W + seg,
-                       ((unsigned long long)epoch << 32) | ACC::word(zr, seg));
-      LLRaw<W> pz;
-      ll_issue<W>(ll_z + (size_t)b * llblk, cx.lane, pz);
-      const bool zok = ll_complete<ACC>(ll_z + (size_t)b * llblk, epoch, cx.lane, pz, stage, a.err,
-                                        (tri << 24) | (1 << 23) | (b << 12) | b);
+      bool zok = true;
+      if (act) {
+        if (seg < W)
+          st_relaxed_u64(ll_z + (size_t)b * llblk + (size_t)rr * W + seg,
+                         ((unsigned long long)epoch << 32) | ACC::word(zr, seg));
+        LLRaw<W> pz;
+        ll_issue<W>(ll_z + (size_t)b * llblk, cx.lane, pz);
+        zok = ll_complete<ACC>(ll_z + (size_t)b * llblk, epoch, cx.lane, pz, stage, a.err,
+                               (tri << 24) | (1 << 23) | (b << 12) | b);
+      }
       if (__syncthreads_or(!zok)) return false;
       zs = stage + seg * NC;
     }
     // y_r = (inverse row r) z, rounded to the storage format
-    typename ACC::A ya = ACC::azero();
+    if (act) {
+      typename ACC::A ya = ACC::azero();
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-      const I x = kPrefetchInv ? xinv[kPrefetchInv ? k : 0] : ACC::inv(a, inv_row + k);
-      ya = ACC::ifma(x, zs[k], ya);
+      for (int k = 0; k < NC; ++k) {
+        const I x = kPrefetchInv ? xinv[kPrefetchInv ? k : 0] : ACC::inv(a, inv_row + k);
+        ya = ACC::ifma(x, zs[k], ya);
+      }
+#pragma unroll
+      for (int m = 1; m < TPR; m <<= 1) ya = ACC::merge(ya, ACC::ax(ya, m));
+      V y = ACC::store(ACC::fin(ya), store_fmt);
+      if (rr >= nr) y = ACC::zero();
+      // publish: segment k writes payload word k of the row (rows past n as 0)
+      if (seg < W)
+        st_relaxed_u64(ll_y + (size_t)b * llblk + (size_t)rr * W + seg,
+                       ((unsigned long long)epoch << 32) | ACC::word(y, seg));
+      if (seg == 0 && rr < nr) ACC::save(out_hi, out_lo, row, y);
     }
-    V y = ACC::fin(ya);
-#pragma unroll
-    for (int m = 1; m < TPR; m <<= 1) y = ACC::add(y, ACC::sx(y, m));
-    y = ACC::store(y, store_fmt);
-    if (rr >= nr) y = ACC::zero();
-    // publish: segment k writes payload word k of the row (rows past n as 0)
-    if (seg < W)
-      st_relaxed_u64(ll_y + (size_t)b * llblk + (size_t)rr * W + seg,
-                     ((unsigned long long)epoch << 32) | ACC::word(y, seg));
-    if (seg == 0 && rr < nr) ACC::save(out_hi, out_lo, row, y);
     if (ts && cx.tid == 0 && member == 0) ts[2] = gtimer();
     __syncthreads();  // staged values and s_z are reused by the next block
   }
