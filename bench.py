@@ -158,6 +158,34 @@ def run_cpu_baseline(max_seconds=25.0):
                       "until ~%.0f s: " % max_seconds + "; ".join(done)}
 
 
+# Small single solves for profiler captures: (n, kappa, triple, graded, repeats)
+PROFILE_CASES = {
+    "refine_n2000_k1e6_hsd": (2000, 1e6, "fp16,fp32,fp64", False, 2),
+    "refine_n2000_k1e10_sdq": (2000, 1e10, "fp32,fp64,dd", False, 2),
+    "lu_n8192_fp16": (8192, 1e3, "fp16,fp32,fp64", False, 2),
+}
+
+
+def run_profile_case(name):
+    """One solve (after one warm-up solve) of a named case, untimed: the
+    command that profiler captures of the kernels run."""
+    import torch
+    import paper_2107_06200_gb300 as M
+    from synth import randsvd_system
+    n, kappa, spec, graded, reps = PROFILE_CASES[name]
+    A, B, _ = randsvd_system(n, kappa, 0, graded=graded)
+    dev = torch.device("cuda", 0)
+    ctx = M.Context(0)
+    At = torch.from_numpy(A).to(dev)
+    bt = torch.from_numpy(B[:, 0].copy()).to(dev)
+    for _ in range(reps):
+        x, r, st = ctx.solve(At, bt, spec)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": name, "status": st, "cged": r[0]["cged"],
+                      "stages": M.stage_string(r[0]["stages"]), "t_factor_ms": r[0]["t_factor_ms"],
+                      "t_refine_ms": r[0]["t_refine_ms"]}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -165,7 +193,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+                    help="run one untimed solve of a named small case (for ncu captures) and exit")
+    ap.add_argument("--sequential", action="store_true",
+                    help="solve the systems one after another with msir_solve instead of msir_solve_batched")
     args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args.profile_case)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -214,6 +249,13 @@ def main():
             torch.distributed.barrier()
 
     def step():
+        if args.sequential:
+            xs, reps = [], []
+            for A, b, sp in zip(As, bs, specs):
+                x, r, st = ctx.solve(A, b, sp)
+                xs.append(x)
+                reps.append(r[0])
+            return xs, reps, st
         xs, reps, st = ctx.solve_batched(As, bs, specs)
         return xs, reps, st
 
@@ -308,7 +350,7 @@ def main():
             "config": {"workload": WORKLOAD, "systems": len(systems), "n": 2000, "nrhs": 1,
                        "triples": ["fp16,fp32,fp64", "fp32,fp64,dd"], "graded": "both",
                        "l2": "inputs larger than L2 (14 fp64 2000x2000 matrices per step)",
-                       "parallelism": f"weak x{world}"},
+                       "parallelism": f"weak x{world}", "mode": "sequential msir_solve" if args.sequential else "msir_solve_batched"},
             "latency_ms": {"p50": p50, "p99": p99},
             "all_converged_nbe_le_2u0": nbe_ok,
             "fp64_lu": {"value": fp64_val, "unit": UNIT,
