@@ -10,25 +10,28 @@ Algorithm 4 applies the factors in three precisions:
 
 The paper fixes only the precision of these solves, not how they are
 carried out.  Reading taken here: block substitution with blocks of
-BLK = 64 rows, each diagonal block applied through its inverse.  For the
-forward solve L y = c, block by block from the first,
-    z_b = T(c_b - sum_{j<b} L_bj y_j),
-    y_b = S(T(inv_T(L_bb) z_b)),
-and for the backward solve U x = y, from the last block up,
-    z_b = T(y_b - sum_{j>b} U_bj x_j),
-    x_b = S(T(inv_T(U_bb) z_b)).
+BLK = 64 rows in which each block row is scaled by the inverse of its
+diagonal block beforehand.  With D_b the diagonal block of L (unit lower)
+and M_bj = D_b^{-1} L_bj, the forward solve L y = c is, block by block,
+    w_b = T(inv_T(D_b) c_b),
+    y_b = S(T(w_b - sum_{j<b} M_bj y_j)),
+and the backward solve U x = y, from the last block up, the same with
+E_b the diagonal block of U and N_bj = E_b^{-1} U_bj (j > b).
 T() rounds to the arithmetic format and S() to the storage format of the
 computed components.  inv_T(B) is the inverse of the stored diagonal block
 B rounded once to T: it is formed in double-double by substitution on the
 columns of the identity (relative accuracy about kappa(B) 2^-104) and then
 rounded, so for T = fp32/fp64 it is the correctly rounded inverse except
 within that distance of a rounding boundary; for T = dd it is the
-double-double value itself.  Sums and products are evaluated in fp64 when
-T is fp32 or fp64 (for T = fp32: an accurate sum, then one rounding) and in
-double-double (pairwise sums) when T = dd.  For the u_f solves T = fp32
-and S = u_f when u_f is bf16/fp16 (a component can overflow to Inf, the
-case Algorithm 4 tests for after the SIR correction); T = S = u_f
-otherwise.  The last block holds the remaining n - 64 floor((n-1)/64) rows.
+double-double value itself.  The scaled off-diagonal blocks are computed
+once per factorisation: for T = fp32 and fp64, M_bj = T(inv_fp64(D_b) L_bj)
+with the 64-term sums in fp64; for T = dd, the dd inverse times L_bj with
+dd sums.  Sums in the solves are evaluated in fp64 when T is fp32 or fp64
+(for T = fp32: an accurate sum, then one rounding) and in double-double
+(pairwise sums) when T = dd.  For the u_f solves T = fp32 and S = u_f when
+u_f is bf16/fp16 (a component can overflow to Inf, the case Algorithm 4
+tests for after the SIR correction); T = S = u_f otherwise.  The last
+block holds the remaining n - 64 floor((n-1)/64) rows.
 """
 
 import numpy as np
@@ -97,16 +100,48 @@ def block_inverses(F, lower, arith, cache=None):
     raise ValueError(arith)
 
 
+def scaled_blocks(F, lower, arith, cache=None):
+    """The scaled off-diagonal block rows: for block b, M_b = D_b^{-1} F[b rows,
+    columns of the other blocks of the triangle] (columns before the block
+    for L, after it for U).  Returns a list over blocks (float64 values for
+    T = fp32/fp64, (hi, lo) pairs for T = dd)."""
+    key = ("ML" if lower else "MU", arith)
+    if cache is not None and key in cache:
+        return cache[key]
+    n = F.shape[0]
+    out = []
+    invs = block_inverses(F, lower, DD, cache)
+    with np.errstate(all="ignore"):
+        for b, (r0, r1) in enumerate(blocks(n)):
+            Fb = F[r0:r1, :r0] if lower else F[r0:r1, r1:]
+            Xh, Xl = invs[b]
+            if arith == DD:
+                m, k = Xh.shape
+                if Fb.shape[1] == 0:
+                    out.append((np.zeros((m, 0)), np.zeros((m, 0))))
+                    continue
+                # (m, k, cols): dd inverse entries times the exact factor entries
+                prods = dd_mul_d((Xh[:, :, None], Xl[:, :, None]), Fb[None, :, :])
+                out.append(dd_sum_pairwise(prods, axis=1))
+            else:
+                P = np.asarray(Xh + Xl, dtype=np.float64) @ Fb  # fp64 inverse, fp64 sums
+                out.append(_round(P, arith))
+    if cache is not None:
+        cache[key] = out
+    return out
+
+
 def lower_unit(F, c, arith, store, cache=None):
     """Solve L y = c, L = unit lower part of packed F (float64 stored values)."""
     n = F.shape[0]
     inv = block_inverses(F, True, arith, cache)
+    M = scaled_blocks(F, True, arith, cache)
     y = np.zeros(n)
     with np.errstate(all="ignore"):
         for b, (r0, r1) in enumerate(blocks(n)):
-            s = F[r0:r1, :r0] @ y[:r0] if r0 else 0.0
-            z = _round(c[r0:r1] - s, arith)
-            y[r0:r1] = _round(_round(inv[b] @ z, arith), store)
+            w = _round(inv[b] @ c[r0:r1], arith)
+            s = M[b] @ y[:r0] if r0 else 0.0
+            y[r0:r1] = _round(_round(w - s, arith), store)
     return y
 
 
@@ -114,27 +149,23 @@ def upper(F, c, arith, store, cache=None):
     """Solve U x = c, U = upper part of packed F."""
     n = F.shape[0]
     inv = block_inverses(F, False, arith, cache)
+    M = scaled_blocks(F, False, arith, cache)
     x = np.zeros(n)
     with np.errstate(all="ignore"):
         for b, (r0, r1) in reversed(list(enumerate(blocks(n)))):
-            s = F[r0:r1, r1:] @ x[r1:] if r1 < n else 0.0
-            z = _round(c[r0:r1] - s, arith)
-            x[r0:r1] = _round(_round(inv[b] @ z, arith), store)
+            w = _round(inv[b] @ c[r0:r1], arith)
+            s = M[b] @ x[r1:] if r1 < n else 0.0
+            x[r0:r1] = _round(_round(w - s, arith), store)
     return x
 
 
 # ------------------------------------------------------------ double-double
 
-def _dd_rowdot(F, r0, r1, c0, c1, xh, xl):
-    """sum_j F[i, j] x_j over j in [c0, c1) for rows [r0, r1), dd, pairwise."""
-    if c1 <= c0:
-        return np.zeros(r1 - r0), np.zeros(r1 - r0)
-    prods = dd_mul_d((xh[c0:c1][None, :], xl[c0:c1][None, :]), F[r0:r1, c0:c1])
-    return dd_sum_pairwise(prods, axis=1)
-
-
 def _dd_apply(inv, z):
-    """inverse block (dd) times z (dd): dd products, pairwise row sums."""
+    """dd matrix (hi, lo) times dd vector z: dd products, pairwise row sums."""
+    if inv[0].shape[1] == 0:
+        m = inv[0].shape[0]
+        return np.zeros(m), np.zeros(m)
     prods = dd_mul(inv, (z[0][None, :], z[1][None, :]))
     return dd_sum_pairwise(prods, axis=1)
 
@@ -143,26 +174,28 @@ def lower_unit_dd(F, c, cache=None):
     """L y = c with c and y in double-double (GMRES-IR operator, u = fp64)."""
     n = F.shape[0]
     inv = block_inverses(F, True, DD, cache)
+    M = scaled_blocks(F, True, DD, cache)
     yh = np.zeros(n)
     yl = np.zeros(n)
     with np.errstate(all="ignore"):
         for b, (r0, r1) in enumerate(blocks(n)):
-            s = _dd_rowdot(F, r0, r1, 0, r0, yh, yl)
-            z = dd_sub((c[0][r0:r1], c[1][r0:r1]), s)
-            yh[r0:r1], yl[r0:r1] = _dd_apply(inv[b], z)
+            w = _dd_apply(inv[b], (c[0][r0:r1], c[1][r0:r1]))
+            s = _dd_apply(M[b], (yh[:r0], yl[:r0]))
+            yh[r0:r1], yl[r0:r1] = dd_sub(w, s)
     return yh, yl
 
 
 def upper_dd(F, c, cache=None):
     n = F.shape[0]
     inv = block_inverses(F, False, DD, cache)
+    M = scaled_blocks(F, False, DD, cache)
     xh = np.zeros(n)
     xl = np.zeros(n)
     with np.errstate(all="ignore"):
         for b, (r0, r1) in reversed(list(enumerate(blocks(n)))):
-            s = _dd_rowdot(F, r0, r1, r1, n, xh, xl)
-            z = dd_sub((c[0][r0:r1], c[1][r0:r1]), s)
-            xh[r0:r1], xl[r0:r1] = _dd_apply(inv[b], z)
+            w = _dd_apply(inv[b], (c[0][r0:r1], c[1][r0:r1]))
+            s = _dd_apply(M[b], (xh[r1:], xl[r1:]))
+            xh[r0:r1], xl[r0:r1] = dd_sub(w, s)
     return xh, xl
 
 

@@ -348,3 +348,43 @@ def test_fp32_block_inverse_is_the_rounded_exact_inverse(lower):
         for i in range(m):
             assert X32[i, c] == round_q(x[i], "fp32")
             assert X64[i, c] == round_q(x[i], "fp64")
+
+
+def test_scaled_blocks_against_exact_rationals():
+    """M_bj = D_b^{-1} L_bj (and the U analogue): fp32 equal to the rounded
+    exact product, fp64 within the fp64 sum's bound, dd within 2^-98."""
+    from exact import round_q
+    rng = np.random.default_rng(27)
+    n = 70  # a full block and a ragged one
+    Fm = rng.uniform(-1, 1, (n, n))
+    Fm[np.arange(n), np.arange(n)] = np.sign(rng.standard_normal(n)) * rng.uniform(1, 2, n)
+    Q = [[Fraction(float(v)) for v in row] for row in Fm]
+
+    def exact_inv(r0, r1, lower):
+        m = r1 - r0
+        X = [[Fraction(0)] * m for _ in range(m)]
+        for c in range(m):
+            rows = range(m) if lower else range(m - 1, -1, -1)
+            for i in rows:
+                rhs = Fraction(int(i == c))
+                ks = range(i) if lower else range(i + 1, m)
+                rhs -= sum(Q[r0 + i][r0 + k] * X[k][c] for k in ks)
+                X[i][c] = rhs if lower else rhs / Q[r0 + i][r0 + i]
+        return X
+
+    for lower, (r0, r1), cols in [(True, (64, 70), range(0, 64)), (False, (0, 64), range(64, 70))]:
+        X = exact_inv(r0, r1, lower)
+        m = r1 - r0
+        exact = [[sum(X[i][k] * Q[r0 + k][c] for k in range(m)) for c in cols] for i in range(m)]
+        b = 1 if lower else 0
+        M32 = T.scaled_blocks(Fm, lower, F.FP32)[b]
+        M64 = T.scaled_blocks(Fm, lower, F.FP64)[b]
+        Mdd = T.scaled_blocks(Fm, lower, F.DD)[b]
+        for i in range(m):
+            for jc in range(len(cols)):
+                e = exact[i][jc]
+                assert M32[i, jc] == round_q(e, "fp32")
+                mag = sum(abs(X[i][k] * Q[r0 + k][cols[jc]]) for k in range(m))
+                assert abs(Fraction(float(M64[i, jc])) - e) <= Fraction(2) ** -46 * mag
+                got = Fraction(float(Mdd[0][i, jc])) + Fraction(float(Mdd[1][i, jc]))
+                assert abs(got - e) <= Fraction(2) ** -98 * mag
