@@ -109,6 +109,15 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _inputs_ready():
+    """The library works on its own streams; device inputs produced by torch
+    (copies, the column-major transpose above) are on torch's current
+    stream, so they are completed before the call.  Every library call
+    returns with its outputs complete."""
+    import torch
+    torch.cuda.current_stream().synchronize()
+
+
 class Factors:
     def __init__(self, ctx, handle, n, info, nonfinite):
         self.ctx, self.h, self.n, self.info, self.nonfinite = ctx, handle, n, info, nonfinite
@@ -130,6 +139,7 @@ class Factors:
         Bc = _colmajor(B) if B.shape[1] > 1 else B.contiguous()
         nrhs = B.shape[1]
         X = torch.empty((nrhs, self.n), dtype=torch.float64, device=B.device)
+        _inputs_ready()
         _check(_L.msir_factors_apply(self.ctx.h, self.h, nrhs, _ptr(Bc), self.n, _ptr(X), self.n,
                                      arith, store), "factors_apply")
         return X.t()
@@ -175,6 +185,7 @@ class Context:
         info = ctypes.c_int()
         nf = ctypes.c_int()
         p = params or params_default()
+        _inputs_ready()
         _check(_L.msir_factor(self.h, n, _ptr(Ac), n, u, uf, ctypes.byref(p), ctypes.byref(fh),
                               ctypes.byref(info), ctypes.byref(nf)), "factor")
         return Factors(self, fh, n, info.value, nf.value)
@@ -185,8 +196,10 @@ class Context:
         n = A.shape[0]
         r = torch.empty(2 * n if ur == DD else n, dtype=torch.float64, device=A.device)
         s = ctypes.c_double()
-        _check(_L.msir_residual(self.h, n, _ptr(Ac), n, u0, _ptr(x.contiguous()),
-                                _ptr(b.contiguous()), ur, _ptr(r), ctypes.byref(s)), "residual")
+        xc, bc = x.contiguous(), b.contiguous()
+        _inputs_ready()
+        _check(_L.msir_residual(self.h, n, _ptr(Ac), n, u0, _ptr(xc), _ptr(bc), ur, _ptr(r),
+                                ctypes.byref(s)), "residual")
         return r, s.value
 
     def solve(self, A, B, spec, params=None):
@@ -201,6 +214,7 @@ class Context:
         X = torch.empty((nrhs, n), dtype=torch.float64, device=A.device)
         reps = (Report * nrhs)()
         p = params or params_default()
+        _inputs_ready()
         st = _check(_L.msir_solve(self.h, n, nrhs, _ptr(Ac), n, _ptr(Bc), n, _ptr(X), n,
                                   triple(spec), ctypes.byref(p), reps), "solve")
         Xo = X.t()
@@ -237,6 +251,7 @@ class Context:
         tp = (Triple * cnt)(*[triple(s) for s in specs])
         reps = (Report * cnt)()
         p = params or params_default()
+        _inputs_ready()
         st = _check(_L.msir_solve_batched(self.h, cnt, ns, Ap, bp, xp, tp, ctypes.byref(p), reps),
                     "solve_batched")
         return xs, [report_to_dict(reps[i]) for i in range(cnt)], st

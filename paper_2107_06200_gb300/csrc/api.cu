@@ -164,6 +164,7 @@ struct Level {  // one factorisation of the current matrix
   float* inv32 = nullptr;    // inverses of the diagonal blocks (inv.cu)
   double* inv_hi = nullptr;
   double* inv_lo = nullptr;
+  int serial = 0;            // identifies this factorisation (scaled blocks follow it)
 };
 
 // Device workspace of one slot, sized for systems up to nmax.
@@ -194,6 +195,12 @@ struct Workspace {
   int ldv = 0;
   double *H, *yv, *red, *hred, *hvec;
   unsigned long long* ll = nullptr;  // substitution hand-off words
+  // scaled off-diagonal blocks of the current factorisation (built by the
+  // refinement kernel): fp32, fp64, dd high and low words; ldu x n each
+  float* M32 = nullptr;
+  double* M64 = nullptr;
+  double* Mdh = nullptr;
+  double* Mdl = nullptr;
   unsigned* bar = nullptr;
   RefState* st = nullptr;
   msir_report* rep = nullptr;
@@ -249,6 +256,10 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
   w.hred = (double*)take((size_t)G * (kcap + 1) * 8);
   w.hvec = (double*)take((size_t)(kcap + 1) * 8);
   w.ll = (unsigned long long*)take(ll_bytes(n));
+  w.M32 = (float*)take(ldu * n * 4);
+  w.M64 = (double*)take(ldu * n * 8);
+  w.Mdh = (double*)take(ldu * n * 8);
+  w.Mdl = (double*)take(ldu * n * 8);
   w.bar = (unsigned*)take(64);
   w.st = (RefState*)take(sizeof(RefState));
   w.rep = (msir_report*)take(sizeof(msir_report));
@@ -428,6 +439,8 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
   L.inv32 = w.inv32[l];
   L.inv_hi = w.inv_hi[l];
   L.inv_lo = w.inv_lo[l];
+  static std::atomic<int> serials{0};
+  L.serial = ++serials;
   CK(launch_inv_diag(fmt, L.F, ldf, n, L.inv32, L.inv_hi, L.inv_lo, st));
   *launches += 1;
   return MSIR_OK;
@@ -455,6 +468,7 @@ enum SlotStep { S_IDLE, S_FACTOR, S_REFINE, S_FINISH };
 struct Slot {
   cudaStream_t st = nullptr;
   Workspace w;
+  int m_serial = -1;          // factorisation whose scaled blocks the workspace holds
   Job* job = nullptr;
   SlotStep step = S_IDLE;
   cudaEvent_t ev = nullptr, e0 = nullptr, e1 = nullptr;
@@ -551,7 +565,8 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   a.d = w.d; a.w = w.w; a.V = w.V; a.ldv = w.ldv;
   a.H = w.H; a.yv = w.yv; a.red = w.red; a.hred = w.hred; a.hvec = w.hvec;
   a.ll = w.ll; a.bar = w.bar;
-  a.inv32 = L.inv32; a.inv_hi = L.inv_hi; a.inv_lo = L.inv_lo; a.err = w.iflags + 2; a.st = w.st; a.rep = w.rep;
+  a.inv32 = L.inv32; a.inv_hi = L.inv_hi; a.inv_lo = L.inv_lo;
+  a.M32 = w.M32; a.M64 = w.M64; a.Mdh = w.Mdh; a.Mdl = w.Mdl; a.err = w.iflags + 2; a.st = w.st; a.rep = w.rep;
   a.tsv = trsv_timers_enabled() ? w.tsv : nullptr;
   a.i_max = j.p.i_max;
   a.rho_thresh = j.p.rho_thresh;
@@ -660,6 +675,11 @@ static msir_status slot_enqueue_factor(msir_ctx* ctx, Slot& s, int fmt, bool squ
 static msir_status slot_enqueue_refine(msir_ctx* ctx, Slot& s) {
   RefineArgs a;
   fill_args(ctx, s, a, MODE_SOLVE);
+  // the scaled blocks in the workspace belong to one factorisation
+  if (s.m_serial != s.lv[s.cur].serial) {
+    s.state.mready = 0;
+    s.m_serial = s.lv[s.cur].serial;
+  }
   CK(cudaMemcpyAsync(s.w.st, &s.state, sizeof(RefState), cudaMemcpyHostToDevice, s.st));
   CK(cudaMemsetAsync(s.w.bar, 0, 64, s.st));
   CK(cudaEventRecord(s.e0, s.st));
@@ -790,6 +810,9 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
     }
     L.valid = false;
     L.failed = true;
+    if (getenv("MSIR_DEBUG_WAITS"))
+      fprintf(stderr, "[msir factor] n=%d format=%d squeeze=%d info=%d nonfinite=%d\n", j.n, s.try_fmt,
+              (int)s.try_squeeze, L.info, L.nonfinite);
     msir_status r;
     if (!s.try_squeeze && s.try_fmt != MSIR_FP64) {
       r = slot_enqueue_factor(ctx, s, s.try_fmt, true);
@@ -1105,10 +1128,17 @@ msir_status msir_factors_apply(msir_ctx* ctx, const msir_factors* fc, int nrhs, 
     a.ap_in = B_dev + (size_t)c * ldb;
     a.ap_out = X_dev + (size_t)c * ldx;
     st0.epoch = (unsigned)(2 * c);
+    if (s.m_serial != s.lv[s.cur].serial) {
+      st0.mready = 0;
+      s.m_serial = s.lv[s.cur].serial;
+    }
     CK(cudaMemcpyAsync(s.w.st, &st0, sizeof(st0), cudaMemcpyHostToDevice, s.st));
     CK(cudaMemsetAsync(s.w.bar, 0, 64, s.st));
     CK(launch_refine(s.u0, s.lv[s.cur].fmt, a, s.G, s.st));
     CK(cudaStreamSynchronize(s.st));
+    RefState back;
+    CK(cudaMemcpy(&back, s.w.st, sizeof(back), cudaMemcpyDeviceToHost));
+    st0.mready = back.mready;  // scaled blocks built by this launch stay valid
   }
   int flags[16];
   CK(cudaMemcpy(flags, s.w.iflags, sizeof(flags), cudaMemcpyDeviceToHost));

@@ -19,6 +19,10 @@ constexpr int kLLWords = 4;
 // Shared scratch of the substitutions: 8 warps x 64 staged values plus the
 // 64 values of z, for the widest value type (double-double, 16 bytes).
 constexpr int kTrsvSmem = (kRefThreads / 32 + 1) * kBlk * 16;
+// Shared staging of one tile of the scaled-block construction: inverse
+// (high and low words) and factor block, 64 x 65 doubles each.
+constexpr int kScLd = kBlk + 1;
+constexpr int kScaledSmem = 3 * kBlk * kScLd * 8;
 
 enum RefMode { MODE_SOLVE = 0, MODE_APPLY = 1, MODE_RESIDUAL = 2 };
 enum RefPhase {
@@ -37,6 +41,7 @@ struct RefState {
   int cged, status;
   int have_phi0;
   unsigned epoch;     // substitution epoch (one per triangular solve)
+  unsigned mready;    // scaled blocks built for the current factors: bit 0 fp32+fp64, bit 1 dd
   int nstages;
   int total_steps, total_gmres;
   double rho_max, delta_prev, phi0, phi;
@@ -86,6 +91,13 @@ struct RefineArgs {
   const float* inv32;      // inverses of the diagonal blocks of L and U:
   const double* inv_hi;    // [2][ceil(n/kBlk)][kBlk][kBlk], fp32 and dd
   const double* inv_lo;
+  // scaled off-diagonal blocks D_b^{-1} F_bj (j != b) of L (j < b) and U
+  // (j > b), row-major with leading dimension ldf, built in the kernel when a
+  // solve in that precision first needs them (RefState::mready)
+  float* M32;
+  double* M64;
+  double* Mdh;
+  double* Mdl;
   unsigned* bar;           // grid barrier counter (zeroed before launch)
   int* err;
   RefState* st;

@@ -33,6 +33,8 @@ struct Cx {
   int redbuf;
   unsigned long long* t_ns;  // per-phase timers (CTA 0, thread 0), shared memory
   unsigned char* tsm;        // shared scratch of the substitutions (kTrsvSmem bytes)
+  unsigned char* ssm;        // shared staging of the scaled-block construction (kScaledSmem)
+  unsigned mready;           // RefState::mready of this launch (uniform)
 };
 
 // Phase timer: CTA 0 / thread 0 accumulates %globaltimer deltas.
@@ -172,6 +174,71 @@ static __device__ double cta_reduce(double v, int op, int tid) {
 // second round trip is needed.  Epochs grow by one per triangular solve and
 // the payload buffer is zeroed whenever the epoch counter restarts.
 
+// N consecutive factor values of one row (N in {4, 8, 16}), widened.  The
+// first value's column is a multiple of N and rows start on 64-element
+// boundaries, so the N values are aligned to N * sizeof(F) bytes.
+__device__ __forceinline__ float h16_to_f(unsigned short b, __half*) { return __half2float(__ushort_as_half(b)); }
+__device__ __forceinline__ float h16_to_f(unsigned short b, __nv_bfloat16*) { return __uint_as_float((unsigned)b << 16); }
+
+template <typename F, int N> struct SegLd;
+template <int N> struct SegLd<float, N> {
+  template <typename Lt>
+  static __device__ __forceinline__ void ld(const float* p, Lt (&v)[N]) {
+#pragma unroll
+    for (int m = 0; m < N / 4; ++m) {
+      const float4 f = __ldg((const float4*)p + m);
+      v[4 * m] = (Lt)f.x; v[4 * m + 1] = (Lt)f.y; v[4 * m + 2] = (Lt)f.z; v[4 * m + 3] = (Lt)f.w;
+    }
+  }
+};
+template <int N> struct SegLd<double, N> {
+  template <typename Lt>
+  static __device__ __forceinline__ void ld(const double* p, Lt (&v)[N]) {
+#pragma unroll
+    for (int m = 0; m < N / 2; ++m) {
+      const double2 f = __ldg((const double2*)p + m);
+      v[2 * m] = (Lt)f.x; v[2 * m + 1] = (Lt)f.y;
+    }
+  }
+};
+// 16-bit formats: each 32-bit word holds two values, the lower address in
+// the low half
+template <typename H, int N> struct SegLdH {
+  template <typename Lt>
+  static __device__ __forceinline__ void ld(const H* p, Lt (&v)[N]) {
+    unsigned w[N / 2];
+    if (N >= 8) {
+#pragma unroll
+      for (int m = 0; m < N / 8; ++m) {
+        const uint4 u = __ldg((const uint4*)p + m);
+        w[4 * m] = u.x; w[4 * m + 1] = u.y; w[4 * m + 2] = u.z; w[4 * m + 3] = u.w;
+      }
+    } else {
+      const uint2 u = __ldg((const uint2*)p);
+      w[0] = u.x; w[1] = u.y;
+    }
+#pragma unroll
+    for (int k = 0; k < N / 2; ++k) {
+      v[2 * k] = (Lt)h16_to_f((unsigned short)(w[k] & 0xffffu), (H*)nullptr);
+      v[2 * k + 1] = (Lt)h16_to_f((unsigned short)(w[k] >> 16), (H*)nullptr);
+    }
+  }
+};
+template <int N> struct SegLd<__half, N> : SegLdH<__half, N> {};
+template <int N> struct SegLd<__nv_bfloat16, N> : SegLdH<__nv_bfloat16, N> {};
+
+// N consecutive factor values of one row, widened; zero outside the matrix.
+template <typename F, typename Lt, int N>
+__device__ __forceinline__ void load_seg(const F* LU, int ldf, int n, int row, int col, Lt (&v)[N]) {
+  if (row < n && col + N <= n) {
+    SegLd<F, N>::ld(LU + (size_t)row * ldf + col, v);
+  } else {
+#pragma unroll
+    for (int k = 0; k < N; ++k)
+      v[k] = (row < n && col + k < n) ? (Lt)to_f(LU[(size_t)row * ldf + col + k]) : (Lt)0;
+  }
+}
+
 // Accumulator policies.  V: value type of the solve; A: running sum of
 // products (fin() turns it into a V); L: factor element after widening;
 // I: inverse element; kW: 32-bit payload words per value.
@@ -206,6 +273,13 @@ struct AccF {
   static __device__ __forceinline__ V store(V v, int fmt) { return round_f(v, fmt); }
   static __device__ __forceinline__ V sx(V v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
   static __device__ __forceinline__ I inv(const RefineArgs& a, size_t o) { return __ldg(a.inv32 + o); }
+  // 16 consecutive scaled-block values of one row (zero outside the matrix)
+  using Tm = float;
+  template <int N>
+  static __device__ __forceinline__ void tile(const RefineArgs& a, int n, int row, int col, Tm (&v)[N]) {
+    load_seg<float, float, N>(a.M32, a.ldf, n, row, col, v);
+  }
+  static __device__ __forceinline__ A tfma(Tm m, V y, A acc) { return __fmaf_rn(m, y, acc); }
   static __device__ __forceinline__ unsigned word(V v, int) { return __float_as_uint(v); }
   static __device__ __forceinline__ V unword(const unsigned* w) { return __uint_as_float(w[0]); }
 };
@@ -231,6 +305,12 @@ struct AccD {
   static __device__ __forceinline__ V store(V v, int) { return v; }
   static __device__ __forceinline__ V sx(V v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
   static __device__ __forceinline__ I inv(const RefineArgs& a, size_t o) { return __ldg(a.inv_hi + o); }
+  using Tm = double;
+  template <int N>
+  static __device__ __forceinline__ void tile(const RefineArgs& a, int n, int row, int col, Tm (&v)[N]) {
+    load_seg<double, double, N>(a.M64, a.ldf, n, row, col, v);
+  }
+  static __device__ __forceinline__ A tfma(Tm m, V y, A acc) { return __fma_rn(m, y, acc); }
   static __device__ __forceinline__ unsigned word(V v, int k) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
     return k == 0 ? (unsigned)b : (unsigned)(b >> 32);
@@ -297,6 +377,16 @@ struct AccDD {
   static __device__ __forceinline__ I inv(const RefineArgs& a, size_t o) {
     return dd_t{__ldg(a.inv_hi + o), __ldg(a.inv_lo + o)};
   }
+  using Tm = dd_t;
+  template <int N>
+  static __device__ __forceinline__ void tile(const RefineArgs& a, int n, int row, int col, Tm (&v)[N]) {
+    double h[N], l[N];
+    load_seg<double, double, N>(a.Mdh, a.ldf, n, row, col, h);
+    load_seg<double, double, N>(a.Mdl, a.ldf, n, row, col, l);
+#pragma unroll
+    for (int k = 0; k < N; ++k) v[k] = dd_t{h[k], l[k]};
+  }
+  static __device__ __forceinline__ A tfma(Tm m, V y, A acc) { return ifma(m, y, acc); }
   static __device__ __forceinline__ unsigned word(V v, int k) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(k < 2 ? v.hi : v.lo);
     return (k & 1) ? (unsigned)(b >> 32) : (unsigned)b;
@@ -308,71 +398,6 @@ struct AccDD {
 };
 
 static_assert(kRefThreads == 4 * kBlk, "substitution thread layout");
-
-// N consecutive factor values of one row (N in {4, 8, 16}), widened.  The
-// first value's column is a multiple of N and rows start on 64-element
-// boundaries, so the N values are aligned to N * sizeof(F) bytes.
-__device__ __forceinline__ float h16_to_f(unsigned short b, __half*) { return __half2float(__ushort_as_half(b)); }
-__device__ __forceinline__ float h16_to_f(unsigned short b, __nv_bfloat16*) { return __uint_as_float((unsigned)b << 16); }
-
-template <typename F, int N> struct SegLd;
-template <int N> struct SegLd<float, N> {
-  template <typename Lt>
-  static __device__ __forceinline__ void ld(const float* p, Lt (&v)[N]) {
-#pragma unroll
-    for (int m = 0; m < N / 4; ++m) {
-      const float4 f = __ldg((const float4*)p + m);
-      v[4 * m] = (Lt)f.x; v[4 * m + 1] = (Lt)f.y; v[4 * m + 2] = (Lt)f.z; v[4 * m + 3] = (Lt)f.w;
-    }
-  }
-};
-template <int N> struct SegLd<double, N> {
-  template <typename Lt>
-  static __device__ __forceinline__ void ld(const double* p, Lt (&v)[N]) {
-#pragma unroll
-    for (int m = 0; m < N / 2; ++m) {
-      const double2 f = __ldg((const double2*)p + m);
-      v[2 * m] = (Lt)f.x; v[2 * m + 1] = (Lt)f.y;
-    }
-  }
-};
-// 16-bit formats: each 32-bit word holds two values, the lower address in
-// the low half
-template <typename H, int N> struct SegLdH {
-  template <typename Lt>
-  static __device__ __forceinline__ void ld(const H* p, Lt (&v)[N]) {
-    unsigned w[N / 2];
-    if (N >= 8) {
-#pragma unroll
-      for (int m = 0; m < N / 8; ++m) {
-        const uint4 u = __ldg((const uint4*)p + m);
-        w[4 * m] = u.x; w[4 * m + 1] = u.y; w[4 * m + 2] = u.z; w[4 * m + 3] = u.w;
-      }
-    } else {
-      const uint2 u = __ldg((const uint2*)p);
-      w[0] = u.x; w[1] = u.y;
-    }
-#pragma unroll
-    for (int k = 0; k < N / 2; ++k) {
-      v[2 * k] = (Lt)h16_to_f((unsigned short)(w[k] & 0xffffu), (H*)nullptr);
-      v[2 * k + 1] = (Lt)h16_to_f((unsigned short)(w[k] >> 16), (H*)nullptr);
-    }
-  }
-};
-template <int N> struct SegLd<__half, N> : SegLdH<__half, N> {};
-template <int N> struct SegLd<__nv_bfloat16, N> : SegLdH<__nv_bfloat16, N> {};
-
-// N consecutive factor values of one row, widened; zero outside the matrix.
-template <typename F, typename Lt, int N>
-__device__ __forceinline__ void load_seg(const F* LU, int ldf, int n, int row, int col, Lt (&v)[N]) {
-  if (row < n && col + N <= n) {
-    SegLd<F, N>::ld(LU + (size_t)row * ldf + col, v);
-  } else {
-#pragma unroll
-    for (int k = 0; k < N; ++k)
-      v[k] = (row < n && col + k < n) ? (Lt)to_f(LU[(size_t)row * ldf + col + k]) : (Lt)0;
-  }
-}
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
   unsigned long long v;
@@ -461,51 +486,133 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
   return true;
 }
 
+// Scaled off-diagonal blocks M_bj = D_b^{-1} F_bj (j != b; L below the
+// diagonal blocks, U above), formed by all CTAs of the grid once per
+// factorisation and precision, the first time a solve needs them.  One
+// 64x64 tile per step: the inverse of the diagonal block and the factor
+// block are staged in shared memory; thread (i, g) forms row i, columns
+// 16g .. 16g+15 of the product, 64 terms each.  fp32/fp64: fp64 inverse,
+// fp64 sums, stored as fp64 and rounded to fp32.  dd: dd inverse, sums
+// compensated as in the substitutions (Dot2 with the inverse's low word).
+template <typename F>
+__device__ __noinline__ bool build_scaled(Cx& cx, const RefineArgs& a, bool dd) {
+  double* Xh = (double*)cx.ssm;
+  double* Xl = Xh + kBlk * kScLd;
+  double* Fb = Xl + kBlk * kScLd;
+  const F* LU = (const F*)a.LU;
+  const int n = cx.n, nb = cx.nblk, ld = a.ldf;
+  const int i = cx.tid >> 2, cg = cx.tid & 3;
+  for (int t = cx.cta; t < nb * nb; t += cx.G) {
+    const int b = t / nb, j = t % nb;
+    if (b == j) continue;
+    const bool lower = j < b;
+    const size_t ib = ((size_t)(lower ? 0 : 1) * nb + b) * kBlk * kBlk;
+    const int r0 = b * kBlk, c0 = j * kBlk;
+    __syncthreads();  // the previous tile's staged values are no longer read
+    for (int e = cx.tid; e < kBlk * kBlk; e += kRefThreads) {
+      const int rr = e / kBlk, cc = e % kBlk;
+      Xh[rr * kScLd + cc] = __ldg(a.inv_hi + ib + e);
+      if (dd) Xl[rr * kScLd + cc] = __ldg(a.inv_lo + ib + e);
+      const int row = r0 + rr, col = c0 + cc;
+      Fb[rr * kScLd + cc] = (row < n && col < n) ? (double)to_f(LU[(size_t)row * ld + col]) : 0.0;
+    }
+    __syncthreads();
+    const int row = r0 + i;
+    if (!dd) {
+      double acc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) acc[q] = 0.0;
+      for (int k = 0; k < kBlk; ++k) {
+        const double x = Xh[i * kScLd + k];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = __fma_rn(x, Fb[k * kScLd + cg * 16 + q], acc[q]);
+      }
+      if (row < n) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int col = c0 + cg * 16 + q;
+          if (col < n) {
+            a.M64[(size_t)row * ld + col] = acc[q];
+            a.M32[(size_t)row * ld + col] = __double2float_rn(acc[q]);
+          }
+        }
+      }
+    } else {
+      double sh[16], sc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) sh[q] = sc[q] = 0.0;
+      for (int k = 0; k < kBlk; ++k) {
+        const double xh = Xh[i * kScLd + k], xl = Xl[i * kScLd + k];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const double f = Fb[k * kScLd + cg * 16 + q];
+          const dd_t p = two_prod(xh, f);
+          const double pl = __fma_rn(xl, f, p.lo);
+          const dd_t u = two_sum(sh[q], p.hi);
+          sh[q] = u.hi;
+          sc[q] = __dadd_rn(sc[q], __dadd_rn(u.lo, pl));
+        }
+      }
+      if (row < n) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+          const int col = c0 + cg * 16 + q;
+          if (col < n) {
+            const dd_t v = two_sum(sh[q], sc[q]);
+            a.Mdh[(size_t)row * ld + col] = v.hi;
+            a.Mdl[(size_t)row * ld + col] = v.lo;
+          }
+        }
+      }
+    }
+  }
+  return grid_barrier(a.bar, a.err, cx.G);
+}
+
 // One triangular solve (LOWER: L y = c, unit diagonal; else U z = y) over
-// all blocks of this CTA's team.
+// all blocks of this CTA's team, with the block rows scaled beforehand:
+// y_b = w_b - sum_j M_bj y_j, w_b = inv(D_b) c_b (the backward solve the
+// same with U).
 //
 // Teams: K CTAs (K in {1, 2, 4}) share each 64-row block, member m taking
 // rows m*64/K .. (m+1)*64/K - 1; teams own blocks t, t + T, t + 2T, ...
 // (T = floor(G / K) teams; CTAs beyond K*T idle).  Each row is handled by
 // 4 adjacent threads with 16 columns of every tile each; a member's 64/K
 // rows use the first 256/K threads (whole warps), the other warps only
-// take part in the barriers.  With K > 1 the members publish their rows of
-// z_b (tagged words, as for the solved values) and every working warp
-// gathers all 64 before applying the inverse: one more hand-off per block,
-// but each member does 1/K of the two 64x64 products, which is what limits
-// the fp64 and dd solves (GB300 issues about 2 fp64 lane operations per
-// clock per SM, so few threads per row keep the reductions cheap).
+// take part in the barriers.  Members need no exchange: each has all it
+// needs for its rows (w from all of c_b, the tiles' rows, the published y).
+// w_b is formed before the block's dependencies arrive, so the dependency
+// chain carries one tile product and a 4-lane sum per block.  The backward
+// solve takes y_b from the forward solve's published words (epoch - 1),
+// because its rows may have been solved by other members.
 //
 // Not inlined: its register-heavy loop then does not raise the pressure of
 // the rest of the kernel (the call costs a few register saves per solve).
 template <typename F, typename ACC, bool LOWER, int K>
 __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fmt, unsigned epoch) {
   using V = typename ACC::V;
-  using Lt = typename ACC::L;
   using I = typename ACC::I;
+  using Tm = typename ACC::Tm;
   constexpr int W = ACC::kW;
   constexpr int R = kBlk / K;               // rows per member
   constexpr int TPR = 4;                    // threads per row
   constexpr int NC = kBlk / TPR;            // columns per thread and tile
   constexpr int NACT = R * TPR;             // working threads (whole warps)
-  constexpr bool kPrefetchInv = W * NC <= 64;
   static_assert(NACT % 32 == 0 && NACT <= kRefThreads, "team shape");
-  V* s_stage = (V*)cx.tsm;                       // per warp: 64 staged values
-  V* s_z = s_stage + (kRefThreads / 32) * kBlk;  // z of the block (K = 1)
-  const F* LU = (const F*)a.LU;
-  const int ldf = a.ldf, n = cx.n;
+  V* s_stage = (V*)cx.tsm;                  // per warp: 64 staged values
+  const int n = cx.n;
   const bool act = cx.tid < NACT;
   const int r = act ? cx.tid / TPR : 0, seg = cx.tid % TPR;
   V* stage = s_stage + cx.warp * kBlk;
   const int tri = LOWER ? 0 : 1;
-  const double* in_hi = LOWER ? a.c_hi : a.y_hi;
-  const double* in_lo = LOWER ? a.c_lo : a.y_lo;
+  const double* in_hi = a.c_hi;  // forward solve input (backward: published y)
+  const double* in_lo = a.c_lo;
   double* out_hi = LOWER ? a.y_hi : a.z_hi;
   double* out_lo = LOWER ? a.y_lo : a.z_lo;
-  // hand-off words: [direction][y | z][block][64][W]
+  // hand-off words: [direction][block][64][W] (direction 0 forward, 1 backward)
   const size_t llblk = (size_t)kBlk * kLLWords;
-  unsigned long long* ll_y = a.ll + (size_t)(2 * tri) * cx.nblk * llblk;
-  unsigned long long* ll_z = a.ll + (size_t)(2 * tri + 1) * cx.nblk * llblk;
+  unsigned long long* ll_y = a.ll + (size_t)tri * cx.nblk * llblk;
+  const unsigned long long* ll_fwd = a.ll;
   const int T = cx.G / K;
   const int team = cx.cta / K, member = cx.cta % K;
   const int nmine = team < T && team < cx.nblk ? (cx.nblk - 1 - team) / T + 1 : 0;
@@ -517,35 +624,55 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
     const int row = r0 + rr;
     unsigned long long* ts = a.tsv ? a.tsv + ((LOWER ? 0 : 1) * (size_t)cx.nblk + b) * 3 : nullptr;
     if (ts && cx.tid == 0 && member == 0) ts[0] = gtimer();
-    // every lane of the row holds c_r: with K > 1 several lanes publish
-    // words of z_r
-    const V cr = (act && rr < nr) ? ACC::load(in_hi, in_lo, row) : ACC::zero();
-    const size_t inv_row = (((size_t)tri * cx.nblk + b) * kBlk + rr) * kBlk + seg * NC;
-    I xinv[kPrefetchInv ? NC : 1];
-    if (kPrefetchInv && act) {
+    bool ok = true;  // a failed wait ends the warp's work; the CTA leaves together below
+    // w_r = (row rr of inv(D_b)) c_b
+    typename ACC::A wa = ACC::azero();
+    if (act) {
+      const V* cs;
+      if (LOWER) {
+        V cv[NC];
 #pragma unroll
-      for (int k = 0; k < (kPrefetchInv ? NC : 1); ++k) xinv[k] = ACC::inv(a, inv_row + k);
+        for (int k = 0; k < NC; ++k) {
+          const int kk = seg * NC + k;
+          cv[k] = kk < nr ? ACC::load(in_hi, in_lo, r0 + kk) : ACC::zero();
+        }
+        const size_t inv_row = (((size_t)tri * cx.nblk + b) * kBlk + rr) * kBlk + seg * NC;
+#pragma unroll
+        for (int k = 0; k < NC; ++k) wa = ACC::ifma(ACC::inv(a, inv_row + k), cv[k], wa);
+      } else {
+        LLRaw<W> py;
+        ll_issue<W>(ll_fwd + (size_t)b * llblk, cx.lane, py);
+        ok = ll_complete<ACC>(ll_fwd + (size_t)b * llblk, epoch - 1, cx.lane, py, stage, a.err,
+                              (tri << 24) | (1 << 23) | (b << 12) | b);
+        cs = stage + seg * NC;
+        const size_t inv_row = (((size_t)tri * cx.nblk + b) * kBlk + rr) * kBlk + seg * NC;
+        if (ok) {
+#pragma unroll
+          for (int k = 0; k < NC; ++k) wa = ACC::ifma(ACC::inv(a, inv_row + k), cs[k], wa);
+        }
+      }
+#pragma unroll
+      for (int m = 1; m < TPR; m <<= 1) wa = ACC::merge(wa, ACC::ax(wa, m));
     }
+    const V wr = ACC::fin(wa);
     // dependencies in the order they become available
     const int ndep = LOWER ? b : cx.nblk - 1 - b;
     typename ACC::A acc = ACC::azero();
-    bool ok = true;  // a failed wait ends the warp's loop; the CTA leaves together below
-    if (ndep > 0 && act) {
+    if (ok && ndep > 0 && act) {
       // fp32/fp64: tile and payload loads one dependency ahead (double
       // buffer); dd: the next tile is loaded after the current one is used
-      // (its products, not the loads, bound the dd solve, and a second
-      // buffer of 16 doubles per thread would spill)
+      // (its products, not the loads, bound the dd solve)
       constexpr bool kDouble = W <= 2;
-      Lt tc[NC], tn[kDouble ? NC : 1];
+      Tm tc[NC], tn[kDouble ? NC : 1];
       LLRaw<W> pc, pn;
       int jb = LOWER ? 0 : cx.nblk - 1;
-      load_seg<F, Lt, NC>(LU, ldf, n, row, jb * kBlk + seg * NC, tc);
+      ACC::template tile<NC>(a, n, row, jb * kBlk + seg * NC, tc);
       ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
       for (int t = 0; t < ndep; ++t) {
         const int jn = LOWER ? jb + 1 : jb - 1;
         const bool more = t + 1 < ndep;
         if (kDouble && more) {
-          load_seg<F, Lt, NC>(LU, ldf, n, row, jn * kBlk + seg * NC, *(Lt(*)[NC])tn);
+          ACC::template tile<NC>(a, n, row, jn * kBlk + seg * NC, *(Tm(*)[NC])tn);
           ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
         }
         if (!ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err,
@@ -555,56 +682,25 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
         }
         const V* ys = stage + seg * NC;
 #pragma unroll
-        for (int k = 0; k < NC; ++k) acc = ACC::fma(tc[k], ys[k], acc);
+        for (int k = 0; k < NC; ++k) acc = ACC::tfma(tc[k], ys[k], acc);
         if (!more) break;
         if (kDouble) {
 #pragma unroll
           for (int k = 0; k < NC; ++k) tc[k] = tn[kDouble ? k : 0];
           pc = pn;
         } else {
-          load_seg<F, Lt, NC>(LU, ldf, n, row, jn * kBlk + seg * NC, tc);
+          ACC::template tile<NC>(a, n, row, jn * kBlk + seg * NC, tc);
           ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pc);
         }
         jb = jn;
       }
     }
-    // the TPR segments of the row: s_r, then z_r = c_r - s_r
-#pragma unroll
-    for (int m = 1; m < TPR; m <<= 1) acc = ACC::merge(acc, ACC::ax(acc, m));
-    const V sr = ACC::fin(acc);
     if (ts && cx.tid == 0 && member == 0) ts[1] = gtimer();
-    const V zr = rr < nr ? ACC::sub(cr, sr) : ACC::zero();
-    const V* zs;
-    if (K == 1) {
-      if (seg == 0) s_z[r] = zr;
-      if (__syncthreads_or(!ok)) return false;
-      zs = s_z + seg * NC;
-    } else {
-      if (__syncthreads_or(!ok)) return false;
-      bool zok = true;
-      if (act) {
-        if (seg < W)
-          st_relaxed_u64(ll_z + (size_t)b * llblk + (size_t)rr * W + seg,
-                         ((unsigned long long)epoch << 32) | ACC::word(zr, seg));
-        LLRaw<W> pz;
-        ll_issue<W>(ll_z + (size_t)b * llblk, cx.lane, pz);
-        zok = ll_complete<ACC>(ll_z + (size_t)b * llblk, epoch, cx.lane, pz, stage, a.err,
-                               (tri << 24) | (1 << 23) | (b << 12) | b);
-      }
-      if (__syncthreads_or(!zok)) return false;
-      zs = stage + seg * NC;
-    }
-    // y_r = (inverse row r) z, rounded to the storage format
-    if (act) {
-      typename ACC::A ya = ACC::azero();
+    if (act && ok) {
+      // the TPR segments of the row: s_r, then y_r = S(T(w_r - s_r))
 #pragma unroll
-      for (int k = 0; k < NC; ++k) {
-        const I x = kPrefetchInv ? xinv[kPrefetchInv ? k : 0] : ACC::inv(a, inv_row + k);
-        ya = ACC::ifma(x, zs[k], ya);
-      }
-#pragma unroll
-      for (int m = 1; m < TPR; m <<= 1) ya = ACC::merge(ya, ACC::ax(ya, m));
-      V y = ACC::store(ACC::fin(ya), store_fmt);
+      for (int m = 1; m < TPR; m <<= 1) acc = ACC::merge(acc, ACC::ax(acc, m));
+      V y = ACC::store(ACC::sub(wr, ACC::fin(acc)), store_fmt);
       if (rr >= nr) y = ACC::zero();
       // publish: segment k writes payload word k of the row (rows past n as 0)
       if (seg < W)
@@ -613,15 +709,15 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
       if (seg == 0 && rr < nr) ACC::save(out_hi, out_lo, row, y);
     }
     if (ts && cx.tid == 0 && member == 0) ts[2] = gtimer();
-    __syncthreads();  // staged values and s_z are reused by the next block
+    if (__syncthreads_or(!ok)) return false;  // staged values are reused by the next block
   }
   return true;
 }
 
 // Team size of a solve in arithmetic ACC: fp32 solves keep one CTA per
-// block (their products are cheap, the extra hand-off would dominate);
-// fp64 and dd solves use the largest K in {4, 2} whose teams cover every
-// block at once, else 1.
+// block (their products are cheap; teams need two grid barriers per
+// solve); fp64 and dd solves use the largest K in {4, 2} whose teams cover
+// every block at once, else 1.
 template <typename ACC>
 __device__ __forceinline__ int team_size(const Cx& cx) {
   if (ACC::kW == 1) return 1;
@@ -644,6 +740,12 @@ __device__ __forceinline__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt)
 // substitution.  Result in z (natural order, before the S*mu scaling).
 template <typename F, typename ACC>
 __device__ bool msolve(Cx& cx, const RefineArgs& a, int store_fmt) {
+  // scaled blocks of the current factors in this precision, once
+  const unsigned need = ACC::kW == 4 ? 2u : 1u;
+  if (!(cx.mready & need)) {
+    if (!build_scaled<F>(cx, a, need == 2u)) return false;
+    cx.mready |= need;
+  }
   // Rows of block b are prepared (c) and consumed (z) by CTA b mod G.  A
   // team of K > 1 CTAs spreads them over other CTAs, so c must be visible
   // grid-wide before the forward solve and z after the backward solve.
@@ -1052,12 +1154,13 @@ static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, doubl
 template <typename A0, typename F>
 __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* gsm = smem_raw + kTrsvSmem;  // GMRES scalars
+  unsigned char* gsm = smem_raw + kTrsvSmem + kScaledSmem;  // GMRES scalars
   __shared__ RefState S;
   __shared__ int s_act, s_reset, s_alg;
 
   Cx cx;
   cx.tsm = smem_raw;
+  cx.ssm = smem_raw + kTrsvSmem;
   cx.G = gridDim.x;
   cx.cta = blockIdx.x;
   cx.tid = threadIdx.x;
@@ -1069,6 +1172,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   if (cx.tid == 0) S = *a.st;
   __syncthreads();
   cx.epoch = S.epoch;
+  cx.mready = S.mready;
   cx.t_ns = S.t_ns;
   bool ok = true;
   const int ff = Fmt<F>::code;
@@ -1302,7 +1406,10 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
 finish:
   __syncthreads();
   if (!ok && cx.tid == 0) { S.phase = PH_ERROR; S.status = MSIR_ERR_TIMEOUT; }
-  if (cx.tid == 0) S.epoch = cx.epoch;
+  if (cx.tid == 0) {
+    S.epoch = cx.epoch;
+    S.mready = cx.mready;
+  }
   __syncthreads();
   if (cx.cta == 0 && cx.tid == 0) *a.st = S;
 }

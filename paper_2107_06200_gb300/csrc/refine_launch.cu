@@ -11,7 +11,7 @@ template <typename A0, typename F> void* refine_entry();
 // ---------------------------------------------------------- launchers
 
 size_t refine_smem_bytes(int kcap) {
-  return kTrsvSmem + sizeof(double) * (3 * ((size_t)kcap + 2) + 2 * ((size_t)kcap + 1));
+  return kTrsvSmem + kScaledSmem + sizeof(double) * (3 * ((size_t)kcap + 2) + 2 * ((size_t)kcap + 1));
 }
 
 template <typename A0, typename F>
