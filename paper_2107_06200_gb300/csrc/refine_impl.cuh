@@ -880,19 +880,34 @@ __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
   PhaseTimer pt(cx, 4);
   const A0* A = (const A0*)a.A;
   if (op == MSIR_FP32) {
+    // a warp's 8 rows together: v is loaded once per column and the eight
+    // rows' loads and sums are independent, so their latencies overlap
     for (int b = cx.cta; b < cx.nblk; b += cx.G) {
+      const int i0 = b * kBlk + cx.warp * 8;
+      if (i0 >= cx.n) continue;
+      const A0* rows[8];
+      float acc[8];
+#pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
-        const int i = b * kBlk + cx.warp * 8 + rr;
-        if (i >= cx.n) break;
-        const int ar = a.perm[i];
-        const A0* row = A + (size_t)ar * a.lda;
-        float acc = 0.0f;
-        for (int j = cx.lane; j < cx.n; j += 32) acc = __fmaf_rn((float)__ldg(row + j), (float)__ldcg(v + j), acc);
-        acc = warp_sum_f(acc);
-        if (cx.lane == 0) {
-          const float R = a.Rsc ? (float)a.Rsc[ar] : 1.0f;
-          ((float*)a.c_hi)[i] = __fmul_rn(acc, R);
-        }
+        const int i = min(i0 + rr, cx.n - 1);  // rows past n repeat the last one, never stored
+        rows[rr] = A + (size_t)a.perm[i] * a.lda;
+        acc[rr] = 0.0f;
+      }
+      for (int j = cx.lane; j < cx.n; j += 32) {
+        const float vj = (float)__ldcg(v + j);
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) acc[rr] = __fmaf_rn((float)__ldg(rows[rr] + j), vj, acc[rr]);
+      }
+#pragma unroll
+      for (int rr = 0; rr < 8; ++rr) acc[rr] = warp_sum_f(acc[rr]);
+      if (cx.lane < 8 && i0 + cx.lane < cx.n) {
+        float mine = acc[0];
+#pragma unroll
+        for (int rr = 1; rr < 8; ++rr)
+          if (cx.lane == rr) mine = acc[rr];
+        const int ar = a.perm[i0 + cx.lane];
+        const float R = a.Rsc ? (float)a.Rsc[ar] : 1.0f;
+        ((float*)a.c_hi)[i0 + cx.lane] = __fmul_rn(mine, R);
       }
     }
     __syncthreads();
@@ -954,14 +969,27 @@ __device__ bool cgs_reduce(Cx& cx, const RefineArgs& a, int kp1, U* s_h) {
 template <typename U>
 __device__ void cgs_partials(Cx& cx, const RefineArgs& a, const U* V, const U* w, int kp1) {
   PhaseTimer pt(cx, 3);
-  for (int j = cx.warp; j < kp1; j += kRefThreads / 32) {
-    const U* Vj = V + (size_t)j * a.ldv;
-    double acc = 0.0;
+  // four basis vectors per warp at a time: their loads and reductions are
+  // independent, so the latencies overlap (each sum keeps its order)
+  constexpr int kJ = 4;
+  for (int j0 = cx.warp * kJ; j0 < kp1; j0 += kJ * (kRefThreads / 32)) {
+    double acc[kJ];
+#pragma unroll
+    for (int q = 0; q < kJ; ++q) acc[q] = 0.0;
     for (int b = cx.cta; b < cx.nblk; b += cx.G)
-      for (int i = b * kBlk + cx.lane; i < min((b + 1) * kBlk, cx.n); i += 32)
-        acc = __fma_rn((double)__ldcg(Vj + i), (double)__ldcg(w + i), acc);
-    acc = warp_sum_d(acc);
-    if (cx.lane == 0) a.hred[(size_t)cx.cta * (a.kcap + 1) + j] = acc;
+      for (int i = b * kBlk + cx.lane; i < min((b + 1) * kBlk, cx.n); i += 32) {
+        const double wi = (double)__ldcg(w + i);
+#pragma unroll
+        for (int q = 0; q < kJ; ++q)
+          if (j0 + q < kp1) acc[q] = __fma_rn((double)__ldcg(V + (size_t)(j0 + q) * a.ldv + i), wi, acc[q]);
+      }
+#pragma unroll
+    for (int q = 0; q < kJ; ++q) acc[q] = warp_sum_d(acc[q]);
+    if (cx.lane == 0) {
+#pragma unroll
+      for (int q = 0; q < kJ; ++q)
+        if (j0 + q < kp1) a.hred[(size_t)cx.cta * (a.kcap + 1) + j0 + q] = acc[q];
+    }
   }
 }
 
@@ -1048,11 +1076,14 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     // Givens rotations (every CTA computes the same numbers)
     unsigned long long tg0 = (cx.cta == 0 && cx.tid == 0) ? gtimer() : 0;
     if (cx.tid == 0) {
+      // the entry carried from one rotation to the next stays in a register
+      U carry = s_h[0];
       for (int i = 0; i < k; ++i) {
-        const U x0 = s_h[i], x1 = s_h[i + 1];
+        const U x0 = carry, x1 = s_h[i + 1];
         s_h[i] = M::add(M::mul(sm_cs[i], x0), M::mul(sm_sn[i], x1));
-        s_h[i + 1] = M::add(M::mul(-sm_sn[i], x0), M::mul(sm_cs[i], x1));
+        carry = M::add(M::mul(-sm_sn[i], x0), M::mul(sm_cs[i], x1));
       }
+      s_h[k] = carry;
       const U f = s_h[k], g = hk1;
       U c, sn, r;
       if (g == (U)0) {
