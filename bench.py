@@ -36,6 +36,22 @@ UNIT = "TFLOP/s"
 WORKLOAD = "sweep_n2000"
 
 
+def max_over_ranks(ms, world, device=None):
+    """The job's time is the slowest rank's (all_reduce MAX; identity at N = 1)."""
+    if world <= 1:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(flops_per_rank_step, world, ms_per_step):
+    """Whole-job rate (TFLOP/s): every rank solves the full sweep each step
+    (weak scaling), so the job does world times a rank's work per step."""
+    return flops_per_rank_step * world / (ms_per_step * 1e-3) / 1e12
+
+
 def flops_equiv(n, nrhs=1):
     return 2.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs
 
@@ -279,12 +295,9 @@ def main():
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
     ms = ev0.elapsed_time(ev1)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world, dev)
     ms_per_step = ms / args.steps
-    value = fl_step * world / (ms_per_step * 1e-3) / 1e12
+    value = whole_job_rate(fl_step, world, ms_per_step)
 
     # accuracy of the last step (every system must reach nbe <= 2 u0)
     u0s = {"fp32": 2.0 ** -24, "fp64": 2.0 ** -53}

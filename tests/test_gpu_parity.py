@@ -287,6 +287,28 @@ def test_batched_multiblock_ctas_through_stage_switches(ctx, M):
             assert r["nbe"] <= 2 * uu
 
 
+def test_batched_small_systems_workload(ctx, M):
+    """The first 64 systems of the 4096-system batched workload (n uniform
+    in [32, 512], kappa log-uniform in [1e1, 1e6], (half, single, double)):
+    every one converges to nbe <= 2 u, and a sample matches solving alone."""
+    systems = batched_systems(4096, seed=0)[:64]
+    As, bs = [], []
+    for (n, kappa, seed) in systems:
+        A, B, _ = randsvd_system(n, kappa, seed)
+        As.append(to_dev(A))
+        bs.append(to_dev(B[:, 0].copy()))
+    xs, reps, st = ctx.solve_batched(As, bs, HSD)
+    assert st == M.OK
+    for A, b, x, r in zip(As, bs, xs, reps):
+        assert r["cged"] and r["nbe"] <= 2 * 2.0 ** -24
+        Ah, bh = A.cpu().numpy(), b.cpu().numpy()
+        Au, bu = OF.fl(Ah, OF.FP32).astype(np.float64), OF.fl(bh, OF.FP32).astype(np.float64)
+        assert OX.nbe(Au, bu, x.cpu().numpy()) <= 2 * 2.0 ** -24
+    for i in range(0, 64, 8):
+        x1, r1, s1 = ctx.solve(As[i], bs[i], HSD)
+        assert [g[:4] for g in stages_of(reps[i])] == [g[:4] for g in stages_of(r1[0])]
+
+
 def test_server_results_match_solve(ctx, M):
     import time
     srv = M.Server(ctx, max_slots=4)

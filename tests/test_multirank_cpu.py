@@ -1,0 +1,56 @@
+"""The bench's multi-rank path (one process per GPU, weak scaling, max over
+ranks) exercised with two gloo ranks on the CPU.  Systems are independent
+units, so ranks exchange nothing but the barrier and the timing reduction."""
+
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, q):
+    import torch
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        ms = 100.0 + 50.0 * rank           # rank 1 is the slow one
+        got = bench.max_over_ranks(ms, world, torch.device("cpu"))
+        dist.barrier()
+        rate = bench.whole_job_rate(bench.flops_equiv(2000) * 14, world, got)
+        q.put((rank, got, rate))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_and_weak_rate_with_two_gloo_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    assert [r[1] for r in res] == [150.0, 150.0]     # both ranks see the slowest time
+    expect = bench_rate = (2.0 / 3.0 * 2000 ** 3 + 2.0 * 2000 ** 2) * 14 * 2 / 0.150 / 1e12
+    assert res[0][2] == pytest.approx(expect) and res[1][2] == pytest.approx(bench_rate)
+
+
+def test_single_rank_is_identity():
+    import bench
+    assert bench.max_over_ranks(12.5, 1) == 12.5
+    assert bench.whole_job_rate(1e12, 1, 1000.0) == pytest.approx(1.0)
