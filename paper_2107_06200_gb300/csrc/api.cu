@@ -1284,12 +1284,12 @@ msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n, const dou
   }
   int nmax = 0;
   for (int i = 0; i < count; ++i) nmax = std::max(nmax, n[i]);
-  // Concurrency: each system gets about 1.2 CTAs per 64-row block (at least
+  // Concurrency: each system gets about 7/6 CTAs per 64-row block (at least
   // 16): its substitution chains need a CTA per block, and the rest of the
   // SMs are better spent on other systems than on wider grids (the
   // measured optimum for the n = 2000 sweep is 4 systems of 38 CTAs).
   const int nblk_max = (nmax + kBlk - 1) / kBlk;
-  const int per_sys = std::max(16, (6 * nblk_max + 4) / 5);
+  const int per_sys = std::max(16, (7 * nblk_max + 5) / 6);
   int nslots = std::max(1, std::min(count, std::min(32, ctx->num_sms / per_sys)));
   if (const char* e = getenv("MSIR_BATCH_SLOTS")) {  // tuning override of the concurrency
     const int v = atoi(e);

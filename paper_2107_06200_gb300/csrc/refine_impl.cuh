@@ -574,12 +574,12 @@ __device__ __noinline__ bool build_scaled(Cx& cx, const RefineArgs& a, bool dd) 
 // y_b = w_b - sum_j M_bj y_j, w_b = inv(D_b) c_b (the backward solve the
 // same with U).
 //
-// Teams: K CTAs (K in {1, 2, 4}) share each 64-row block, member m taking
-// rows m*64/K .. (m+1)*64/K - 1; teams own blocks t, t + T, t + 2T, ...
-// (T = floor(G / K) teams; CTAs beyond K*T idle).  Each row is handled by
-// 4 adjacent threads with 16 columns of every tile each; a member's 64/K
-// rows use the first 256/K threads (whole warps), the other warps only
-// take part in the barriers.  Members need no exchange: each has all it
+// Teams: K CTAs (K in {1, 2, 4, 8}) share each 64-row block, member m
+// taking rows m*64/K .. (m+1)*64/K - 1; teams own blocks t, t + T, t + 2T,
+// ... (T = floor(G / K) teams; CTAs beyond K*T idle).  Each row is handled
+// by TPR adjacent threads with 64/TPR columns of every tile each (TPR = 4,
+// or 8 and 16 for K = 4 and 8 so that at least 4 warps work); the other
+// warps only take part in the barriers.  Members need no exchange: each has all it
 // needs for its rows (w from all of c_b, the tiles' rows, the published y).
 // w_b is formed before the block's dependencies arrive, so the dependency
 // chain carries one tile product and a 4-lane sum per block.  The backward
@@ -595,10 +595,12 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
   using Tm = typename ACC::Tm;
   constexpr int W = ACC::kW;
   constexpr int R = kBlk / K;               // rows per member
-  constexpr int TPR = 4;                    // threads per row
+  // threads per row: 4, or more so that a member keeps at least 4 warps
+  // busy (one per SM sub-partition; each has its own fp64 unit)
+  constexpr int TPR = R * 4 >= 128 ? 4 : 128 / R;
   constexpr int NC = kBlk / TPR;            // columns per thread and tile
   constexpr int NACT = R * TPR;             // working threads (whole warps)
-  static_assert(NACT % 32 == 0 && NACT <= kRefThreads, "team shape");
+  static_assert(NACT % 32 == 0 && NACT <= kRefThreads && NC >= 4, "team shape");
   V* s_stage = (V*)cx.tsm;                  // per warp: 64 staged values
   const int n = cx.n;
   const bool act = cx.tid < NACT;
@@ -716,13 +718,17 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
 
 // Team size of a solve in arithmetic ACC: fp32 solves keep one CTA per
 // block (their products are cheap; teams need two grid barriers per
-// solve); fp64 and dd solves use the largest K in {4, 2} whose teams cover
-// every block at once, else 1.
+// solve); fp64 and dd solves use the largest K in {8, 4, 2} for which each
+// team owns at most two blocks, else 1 (the products of a block, not the
+// hand-offs, bound these solves, so splitting them pays even when a team
+// then works through two blocks).
 template <typename ACC>
 __device__ __forceinline__ int team_size(const Cx& cx) {
   if (ACC::kW == 1) return 1;
-  if (cx.G >= 4 * cx.nblk) return 4;
-  if (cx.G >= 2 * cx.nblk) return 2;
+  const int half = (cx.nblk + 1) / 2;
+  if (cx.G / 8 >= half) return 8;
+  if (cx.G / 4 >= half) return 4;
+  if (cx.G / 2 >= half) return 2;
   return 1;
 }
 
@@ -730,6 +736,7 @@ template <typename F, typename ACC, bool LOWER>
 __device__ __forceinline__ bool trsv(Cx& cx, const RefineArgs& a, int store_fmt) {
   const unsigned epoch = ++cx.epoch;
   const int K = team_size<ACC>(cx);
+  if (ACC::kW > 1 && K == 8) return trsv_team<F, ACC, LOWER, 8>(cx, a, store_fmt, epoch);
   if (ACC::kW > 1 && K == 4) return trsv_team<F, ACC, LOWER, 4>(cx, a, store_fmt, epoch);
   if (ACC::kW > 1 && K == 2) return trsv_team<F, ACC, LOWER, 2>(cx, a, store_fmt, epoch);
   return trsv_team<F, ACC, LOWER, 1>(cx, a, store_fmt, epoch);
