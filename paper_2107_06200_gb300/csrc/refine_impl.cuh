@@ -945,11 +945,27 @@ __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
   return grid_barrier(a.bar, a.err, cx.G);
 }
 
-// out_i = fl_u(z_i * S_i * mu) for my rows
+// GMRES's vector work (Gram-Schmidt, norms, basis updates) uses a flat
+// partition: CTA c owns the contiguous rows [c*chunk, (c+1)*chunk) with
+// chunk = ceil(n / G), so every CTA shares it (the substitutions' block
+// partition leaves all but n/64 CTAs without rows).  Grid barriers separate
+// the phases that hand rows between the two partitions.
+__device__ __forceinline__ void flat_rows(const Cx& cx, int& r0, int& r1) {
+  const int chunk = (cx.n + cx.G - 1) / cx.G;
+  r0 = min(cx.n, cx.cta * chunk);
+  r1 = min(cx.n, r0 + chunk);
+}
+
+// out_i = fl_u(z_i * S_i * mu), flat rows (after the substitution's rows
+// are visible grid-wide)
 template <typename U>
-__device__ void finish_solve(Cx& cx, const RefineArgs& a, U* out, int arith) {
-  FOR_MY_ROWS(cx, i) out[i] = UA<U>::rnd(get_z(a, arith, i) * cscale(a, i));
+__device__ bool finish_solve(Cx& cx, const RefineArgs& a, U* out, int arith) {
+  if (!grid_barrier(a.bar, a.err, cx.G)) return false;
+  int r0, r1;
+  flat_rows(cx, r0, r1);
+  for (int i = r0 + cx.tid; i < r1; i += kRefThreads) out[i] = UA<U>::rnd(get_z(a, arith, i) * cscale(a, i));
   __syncthreads();
+  return true;
 }
 
 // Two-stage grid reduction of the (k+1) Gram-Schmidt partial sums; the
@@ -976,38 +992,40 @@ __device__ bool cgs_reduce(Cx& cx, const RefineArgs& a, int kp1, U* s_h) {
 template <typename U>
 __device__ void cgs_partials(Cx& cx, const RefineArgs& a, const U* V, const U* w, int kp1) {
   PhaseTimer pt(cx, 3);
-  // four basis vectors per warp at a time: their loads and reductions are
-  // independent, so the latencies overlap (each sum keeps its order)
-  constexpr int kJ = 4;
-  for (int j0 = cx.warp * kJ; j0 < kp1; j0 += kJ * (kRefThreads / 32)) {
-    double acc[kJ];
-#pragma unroll
-    for (int q = 0; q < kJ; ++q) acc[q] = 0.0;
-    for (int b = cx.cta; b < cx.nblk; b += cx.G)
-      for (int i = b * kBlk + cx.lane; i < min((b + 1) * kBlk, cx.n); i += 32) {
-        const double wi = (double)__ldcg(w + i);
-#pragma unroll
-        for (int q = 0; q < kJ; ++q)
-          if (j0 + q < kp1) acc[q] = __fma_rn((double)__ldcg(V + (size_t)(j0 + q) * a.ldv + i), wi, acc[q]);
-      }
-#pragma unroll
-    for (int q = 0; q < kJ; ++q) acc[q] = warp_sum_d(acc[q]);
-    if (cx.lane == 0) {
-#pragma unroll
-      for (int q = 0; q < kJ; ++q)
-        if (j0 + q < kp1) a.hred[(size_t)cx.cta * (a.kcap + 1) + j0 + q] = acc[q];
-    }
+  // one thread per basis vector: its dot product with w over this CTA's
+  // flat rows, in row order (the loads are independent of the running sum)
+  int r0, r1;
+  flat_rows(cx, r0, r1);
+  for (int j = cx.tid; j < kp1; j += kRefThreads) {
+    const U* Vj = V + (size_t)j * a.ldv;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int i = r0; i < r1; ++i) acc = __fma_rn((double)__ldcg(Vj + i), (double)__ldcg(w + i), acc);
+    a.hred[(size_t)cx.cta * (a.kcap + 1) + j] = acc;
   }
 }
 
-// w_i = fl_u(w_i - sum_j V_j[i] h_j), the sum in fp64
+// sum_j V_j[i] c_j for row i by one warp (lanes over j, then a warp sum);
+// the result is in every lane
+template <typename U>
+__device__ __forceinline__ double basis_row_dot(const RefineArgs& a, const U* V, int i, int kp1, const U* c,
+                                                int lane) {
+  double acc = 0.0;
+#pragma unroll 4
+  for (int j = lane; j < kp1; j += 32) acc = __fma_rn((double)__ldcg(V + (size_t)j * a.ldv + i), (double)c[j], acc);
+  return warp_sum_d(acc);
+}
+
+// w_i = fl_u(w_i - sum_j V_j[i] h_j), the sum in fp64; flat rows, a warp
+// per row
 template <typename U>
 __device__ void cgs_update(Cx& cx, const RefineArgs& a, const U* V, U* w, int kp1, const U* s_h) {
   PhaseTimer pt(cx, 3);
-  FOR_MY_ROWS(cx, i) {
-    double acc = 0.0;
-    for (int j = 0; j < kp1; ++j) acc = __fma_rn((double)__ldcg(V + (size_t)j * a.ldv + i), (double)s_h[j], acc);
-    w[i] = UA<U>::rnd(__dsub_rn((double)w[i], acc));
+  int r0, r1;
+  flat_rows(cx, r0, r1);
+  for (int i = r0 + cx.warp; i < r1; i += kRefThreads / 32) {
+    const double acc = basis_row_dot<U>(a, V, i, kp1, s_h, cx.lane);
+    if (cx.lane == 0) w[i] = UA<U>::rnd(__dsub_rn((double)w[i], acc));
   }
   __syncthreads();
 }
@@ -1015,7 +1033,9 @@ __device__ void cgs_update(Cx& cx, const RefineArgs& a, const U* V, U* w, int kp
 template <typename U>
 __device__ bool grid_sum_sq(Cx& cx, const RefineArgs& a, const U* w, double& out) {
   double ss = 0.0;
-  FOR_MY_ROWS(cx, i) {
+  int r0, r1;
+  flat_rows(cx, r0, r1);
+  for (int i = r0 + cx.tid; i < r1; i += kRefThreads) {
     const double wv = (double)w[i];
     ss = __fma_rn(wv, wv, ss);
   }
@@ -1046,17 +1066,18 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
       put_c(a, op, i, scaled_r(a, i, s, ur, u) * rscale(a, a.perm[i]), 0.0);
   __syncthreads();
   if (!msolve_arith<F>(cx, a, op, op)) return false;
-  finish_solve<U>(cx, a, w, op);
+  if (!finish_solve<U>(cx, a, w, op)) return false;
   double ss;
   if (!grid_sum_sq<U>(cx, a, w, ss)) return false;
   const U beta = M::sqrt_(M::rnd(ss));
   if (!isfinite((double)beta)) { out.nonfinite = true; return true; }
+  int f0, f1;
+  flat_rows(cx, f0, f1);
   if (beta == (U)0) {
-    FOR_MY_ROWS(cx, i) a.d[i] = 0.0;
-    __syncthreads();
-    return true;
+    for (int i = f0 + cx.tid; i < f1; i += kRefThreads) a.d[i] = 0.0;
+    return grid_barrier(a.bar, a.err, cx.G);  // d is read by the block partition
   }
-  FOR_MY_ROWS(cx, i) V[i] = M::div(w[i], beta);
+  for (int i = f0 + cx.tid; i < f1; i += kRefThreads) V[i] = M::div(w[i], beta);
   if (cx.tid == 0) sm_g[0] = beta;
   __syncthreads();
   int kdone = 0;
@@ -1065,7 +1086,7 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     if (!grid_barrier(a.bar, a.err, cx.G)) return false;
     if (!apply_A<A0, U>(cx, a, V + (size_t)k * a.ldv, op)) return false;
     if (!msolve_arith<F>(cx, a, op, op)) return false;
-    finish_solve<U>(cx, a, w, op);
+    if (!finish_solve<U>(cx, a, w, op)) return false;
     // classical Gram-Schmidt, twice
     cgs_partials<U>(cx, a, V, w, k + 1);
     if (!cgs_reduce<U>(cx, a, k + 1, s_h)) return false;
@@ -1117,7 +1138,7 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     const double relres = s_bc[0];
     kdone = k + 1;
     if (hk1 != (U)0 && isfinite((double)hk1)) {
-      FOR_MY_ROWS(cx, i) V[(size_t)(k + 1) * a.ldv + i] = M::div(w[i], hk1);
+      for (int i = f0 + cx.tid; i < f1; i += kRefThreads) V[(size_t)(k + 1) * a.ldv + i] = M::div(w[i], hk1);
     }
     __syncthreads();
     if (!isfinite(relres) || relres <= tau || hk1 == (U)0) break;
@@ -1134,14 +1155,12 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
   if (!grid_barrier(a.bar, a.err, cx.G)) return false;
   for (int j = cx.tid; j < kdone; j += kRefThreads) s_h[j] = (U)__ldcg(a.yv + j);
   __syncthreads();
-  FOR_MY_ROWS(cx, i) {
-    double acc = 0.0;
-    for (int j = 0; j < kdone; ++j) acc = __fma_rn((double)__ldcg(V + (size_t)j * a.ldv + i), (double)s_h[j], acc);
-    a.d[i] = (double)M::rnd(acc);
+  for (int i = f0 + cx.warp; i < f1; i += kRefThreads / 32) {
+    const double acc = basis_row_dot<U>(a, V, i, kdone, s_h, cx.lane);
+    if (cx.lane == 0) a.d[i] = (double)M::rnd(acc);
   }
-  __syncthreads();
   out.k = kdone;
-  return true;
+  return grid_barrier(a.bar, a.err, cx.G);  // d is read by the block partition
 }
 
 // -------------------------------------------------------------- kernel
