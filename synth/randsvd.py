@@ -46,20 +46,32 @@ def _algebra_torch(G1, G2, sigma, device):
     return A
 
 
-def randsvd_system(n, kappa, seed, nrhs=1, graded=False, device=None):
+def singular_values(n, kappa, mode=3):
+    """randsvd's singular values: mode 3 geometric, sigma_i = kappa^(-(i-1)/(n-1));
+    mode 2 one small value, sigma = (1, ..., 1, 1/kappa)."""
+    if n == 1:
+        return np.ones(1)
+    if mode == 3:
+        return float(kappa) ** (-np.arange(n, dtype=np.float64) / (n - 1))
+    if mode == 2:
+        s = np.ones(n)
+        s[-1] = 1.0 / float(kappa)
+        return s
+    raise ValueError(f"randsvd mode {mode} not provided")
+
+
+def randsvd_system(n, kappa, seed, nrhs=1, graded=False, device=None, mode=3):
     """Return (A, B, X) as float64 numpy arrays (A row-major n x n, B and X n x nrhs).
 
     ``device``: a torch device string to run the QR/products there (the
-    result is copied back to host memory)."""
+    result is copied back to host memory).  ``mode``: the singular value
+    distribution (3 geometric, 2 one small value); the draws are the same."""
     rng = np.random.default_rng(seed)
     G1 = rng.standard_normal((n, n))
     G2 = rng.standard_normal((n, n))
     X = rng.standard_normal((n, nrhs))
     g = rng.uniform(-4.0, 4.0, n) if graded else None
-    if n == 1:
-        sigma = np.ones(1)
-    else:
-        sigma = float(kappa) ** (-np.arange(n, dtype=np.float64) / (n - 1))
+    sigma = singular_values(n, kappa, mode)
     if device is not None:
         import torch
         A_t = _algebra_torch(G1, G2, sigma, device)

@@ -177,20 +177,27 @@ def _hook(ctx, A, u0, first_uf, nb, nbo):
     return hook
 
 
+HDQ = "fp16,fp64,dd"  # (half, double, quad) with double-double for quad
+
+# (n, kappa, triple, graded, randsvd mode)
 MSIR_CASES = [
-    (100, 1e2, HSD, False), (100, 1e5, HSD, False), (100, 1e9, SDQ, False),
-    (300, 1e2, BSD, False), (300, 1e4, HSD, False), (300, 1e6, HSD, False),
-    (260, 1e8, SDQ, False), (300, 1e2, HSD, True), (129, 1e3, HSD, False),
-    (2000, 1e2, HSD, False),
+    (100, 1e2, HSD, False, 3), (100, 1e5, HSD, False, 3), (100, 1e9, SDQ, False, 3),
+    (300, 1e2, BSD, False, 3), (300, 1e4, HSD, False, 3), (300, 1e6, HSD, False, 3),
+    (260, 1e8, SDQ, False, 3), (300, 1e2, HSD, True, 3), (129, 1e3, HSD, False, 3),
+    (2000, 1e2, HSD, False, 3),
+    # the paper's (half, double, quad) combination: fp16 factors, u = fp64
+    (100, 1e4, HDQ, False, 3), (100, 1e8, HDQ, False, 3), (200, 1e10, HDQ, False, 3),
+    # randsvd mode 2: one small singular value
+    (100, 1e4, HSD, False, 2), (200, 1e6, HSD, False, 2), (200, 1e10, SDQ, False, 2),
 ]
 
 
-@pytest.mark.parametrize("n,kappa,spec,graded", MSIR_CASES)
-def test_msir_parity_with_oracle(ctx, M, n, kappa, spec, graded):
+@pytest.mark.parametrize("n,kappa,spec,graded,mode", MSIR_CASES)
+def test_msir_parity_with_oracle(ctx, M, n, kappa, spec, graded, mode):
     """Same seeded system; the oracle refines with the GPU's own factors at
     every u_f level (so that LU near-ties do not mask the refinement).
     Stage sequence equal, steps +-1, nbe <= 2 u0, ferr <= 2x oracle."""
-    A, B, _ = randsvd_system(n, kappa, 0, graded=graded)
+    A, B, _ = randsvd_system(n, kappa, 0, graded=graded, mode=mode)
     b = B[:, 0]
     x, reps, st = ctx.solve(to_dev(A), to_dev(b), spec)
     rep = reps[0]
