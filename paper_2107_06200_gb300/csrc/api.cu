@@ -277,11 +277,12 @@ static int kcap_of(int n, double kmax_frac) {
 // block (fp64 and double-double substitutions split each block over a team
 // of CTAs), and enough CTAs that the O(n^2) fp64 work (residual, u^2
 // operator) is spread over the SMs; never more than the SMs.
-static int refine_grid(msir_ctx* ctx, int n, int share) {
+static int refine_grid(msir_ctx* ctx, int n, int share, int kcap) {
   const int nblk = (n + kBlk - 1) / kBlk;
   const long long work = ((long long)n * n + 16383) / 16384;
   int g = (int)std::min<long long>(ctx->num_sms, std::max<long long>(4LL * nblk, work));
-  if (share > 1) g = std::max(1, std::min(g, ctx->num_sms / share));
+  (void)kcap;
+  if (share > 1) g = std::max(1, std::min(g, ctx->num_sms / share));  // systems running together split the SMs
   return g;
 }
 
@@ -709,7 +710,7 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
   s.job = job;
   Job& j = *job;
   s.u0 = j.t.u;
-  s.G = refine_grid(ctx, j.n, share);
+  s.G = refine_grid(ctx, j.n, share, kcap_of(j.n, j.p.kmax_frac));
   const int kcap = kcap_of(j.n, j.p.kmax_frac);
   msir_status r = ws_alloc(s.w, std::max(j.n, s.w.nmax), std::max(kcap, s.w.kcapmax),
                            std::max(s.G, s.w.G), s.st);
@@ -1025,7 +1026,7 @@ msir_status msir_factor(msir_ctx* ctx, int n, const double* A_dev, int lda, int 
   Slot& s = f->slot;
   s.job = &f->job;
   s.u0 = u;
-  s.G = refine_grid(ctx, n, 1);
+  s.G = refine_grid(ctx, n, 1, 1);
   r = ws_alloc(s.w, n, kcap_of(n, p.kmax_frac), s.G, s.st);
   if (r == MSIR_OK) r = cuda_status(ingest_matrix(A_dev, lda, n, u, s.w.Au, s.w.ldu, s.st));
   if (r == MSIR_OK) r = slot_enqueue_factor(ctx, s, uf, false);
@@ -1160,7 +1161,7 @@ msir_status msir_residual(msir_ctx* ctx, int n, const double* A_dev, int lda, in
   j.t = msir_triple{MSIR_FP64, u0, ur};
   s.job = &j;
   s.u0 = u0;
-  s.G = refine_grid(ctx, n, 1);
+  s.G = refine_grid(ctx, n, 1, 1);
   if (r == MSIR_OK) r = ws_alloc(s.w, n, 1, s.G, s.st);
   if (r == MSIR_OK) {
     ingest_matrix(A_dev, lda, n, u0, s.w.Au, s.w.ldu, s.st);

@@ -19,10 +19,11 @@ constexpr int kLLWords = 4;
 // Shared scratch of the substitutions: 8 warps x 64 staged values plus the
 // 64 values of z, for the widest value type (double-double, 16 bytes).
 constexpr int kTrsvSmem = (kRefThreads / 32 + 1) * kBlk * 16;
-// Shared staging of one tile of the scaled-block construction: inverse
-// (high and low words) and factor block, 64 x 65 doubles each.
+// Shared staging of the scaled-block construction: half the inner
+// dimension of one tile at a time (inverse high and low words, 64 x 33
+// doubles each; factor rows, 32 x 65 doubles).
 constexpr int kScLd = kBlk + 1;
-constexpr int kScaledSmem = 3 * kBlk * kScLd * 8;
+constexpr int kScaledSmem = (2 * kBlk * (kBlk / 2 + 1) + (kBlk / 2) * kScLd) * 8;
 
 enum RefMode { MODE_SOLVE = 0, MODE_APPLY = 1, MODE_RESIDUAL = 2 };
 enum RefPhase {

@@ -490,15 +490,19 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
 // diagonal blocks, U above), formed by all CTAs of the grid once per
 // factorisation and precision, the first time a solve needs them.  One
 // 64x64 tile per step: the inverse of the diagonal block and the factor
-// block are staged in shared memory; thread (i, g) forms row i, columns
+// block are staged in shared memory (half the inner dimension at a time);
+// thread (i, g) forms row i, columns
 // 16g .. 16g+15 of the product, 64 terms each.  fp32/fp64: fp64 inverse,
 // fp64 sums, stored as fp64 and rounded to fp32.  dd: dd inverse, sums
 // compensated as in the substitutions (Dot2 with the inverse's low word).
 template <typename F>
 __device__ __noinline__ bool build_scaled(Cx& cx, const RefineArgs& a, bool dd) {
-  double* Xh = (double*)cx.ssm;
-  double* Xl = Xh + kBlk * kScLd;
-  double* Fb = Xl + kBlk * kScLd;
+  // staging of half the inner dimension at a time: inverse columns k0..k0+31
+  // (high, low words) and factor rows k0..k0+31; the sums keep k order
+  constexpr int KH = kBlk / 2;
+  double* Xh = (double*)cx.ssm;       // 64 x (KH + 1)
+  double* Xl = Xh + kBlk * (KH + 1);  // 64 x (KH + 1)
+  double* Fb = Xl + kBlk * (KH + 1);  // KH x kScLd
   const F* LU = (const F*)a.LU;
   const int n = cx.n, nb = cx.nblk, ld = a.ldf;
   const int i = cx.tid >> 2, cg = cx.tid & 3;
@@ -508,60 +512,56 @@ __device__ __noinline__ bool build_scaled(Cx& cx, const RefineArgs& a, bool dd) 
     const bool lower = j < b;
     const size_t ib = ((size_t)(lower ? 0 : 1) * nb + b) * kBlk * kBlk;
     const int r0 = b * kBlk, c0 = j * kBlk;
-    __syncthreads();  // the previous tile's staged values are no longer read
-    for (int e = cx.tid; e < kBlk * kBlk; e += kRefThreads) {
-      const int rr = e / kBlk, cc = e % kBlk;
-      Xh[rr * kScLd + cc] = __ldg(a.inv_hi + ib + e);
-      if (dd) Xl[rr * kScLd + cc] = __ldg(a.inv_lo + ib + e);
-      const int row = r0 + rr, col = c0 + cc;
-      Fb[rr * kScLd + cc] = (row < n && col < n) ? (double)to_f(LU[(size_t)row * ld + col]) : 0.0;
-    }
-    __syncthreads();
     const int row = r0 + i;
-    if (!dd) {
-      double acc[16];
+    double sh[16], sc[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) acc[q] = 0.0;
-      for (int k = 0; k < kBlk; ++k) {
-        const double x = Xh[i * kScLd + k];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) acc[q] = __fma_rn(x, Fb[k * kScLd + cg * 16 + q], acc[q]);
+    for (int q = 0; q < 16; ++q) sh[q] = sc[q] = 0.0;
+    for (int k0 = 0; k0 < kBlk; k0 += KH) {
+      __syncthreads();  // the previous staging is no longer read
+      for (int e = cx.tid; e < kBlk * KH; e += kRefThreads) {
+        const int rr = e / KH, kk = e % KH;
+        Xh[rr * (KH + 1) + kk] = __ldg(a.inv_hi + ib + (size_t)rr * kBlk + k0 + kk);
+        if (dd) Xl[rr * (KH + 1) + kk] = __ldg(a.inv_lo + ib + (size_t)rr * kBlk + k0 + kk);
       }
-      if (row < n) {
+      for (int e = cx.tid; e < KH * kBlk; e += kRefThreads) {
+        const int kk = e / kBlk, cc = e % kBlk;
+        const int frow = r0 + k0 + kk, col = c0 + cc;
+        Fb[kk * kScLd + cc] = (frow < n && col < n) ? (double)to_f(LU[(size_t)frow * ld + col]) : 0.0;
+      }
+      __syncthreads();
+      if (!dd) {
+        for (int kk = 0; kk < KH; ++kk) {
+          const double x = Xh[i * (KH + 1) + kk];
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int col = c0 + cg * 16 + q;
-          if (col < n) {
-            a.M64[(size_t)row * ld + col] = acc[q];
-            a.M32[(size_t)row * ld + col] = __double2float_rn(acc[q]);
+          for (int q = 0; q < 16; ++q) sh[q] = __fma_rn(x, Fb[kk * kScLd + cg * 16 + q], sh[q]);
+        }
+      } else {
+        for (int kk = 0; kk < KH; ++kk) {
+          const double xh = Xh[i * (KH + 1) + kk], xl = Xl[i * (KH + 1) + kk];
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const double f = Fb[kk * kScLd + cg * 16 + q];
+            const dd_t p = two_prod(xh, f);
+            const double pl = __fma_rn(xl, f, p.lo);
+            const dd_t u = two_sum(sh[q], p.hi);
+            sh[q] = u.hi;
+            sc[q] = __dadd_rn(sc[q], __dadd_rn(u.lo, pl));
           }
         }
       }
-    } else {
-      double sh[16], sc[16];
+    }
+    if (row < n) {
 #pragma unroll
-      for (int q = 0; q < 16; ++q) sh[q] = sc[q] = 0.0;
-      for (int k = 0; k < kBlk; ++k) {
-        const double xh = Xh[i * kScLd + k], xl = Xl[i * kScLd + k];
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const double f = Fb[k * kScLd + cg * 16 + q];
-          const dd_t p = two_prod(xh, f);
-          const double pl = __fma_rn(xl, f, p.lo);
-          const dd_t u = two_sum(sh[q], p.hi);
-          sh[q] = u.hi;
-          sc[q] = __dadd_rn(sc[q], __dadd_rn(u.lo, pl));
-        }
-      }
-      if (row < n) {
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-          const int col = c0 + cg * 16 + q;
-          if (col < n) {
-            const dd_t v = two_sum(sh[q], sc[q]);
-            a.Mdh[(size_t)row * ld + col] = v.hi;
-            a.Mdl[(size_t)row * ld + col] = v.lo;
-          }
+      for (int q = 0; q < 16; ++q) {
+        const int col = c0 + cg * 16 + q;
+        if (col >= n) continue;
+        if (!dd) {
+          a.M64[(size_t)row * ld + col] = sh[q];
+          a.M32[(size_t)row * ld + col] = __double2float_rn(sh[q]);
+        } else {
+          const dd_t v = two_sum(sh[q], sc[q]);
+          a.Mdh[(size_t)row * ld + col] = v.hi;
+          a.Mdl[(size_t)row * ld + col] = v.lo;
         }
       }
     }
@@ -1209,6 +1209,9 @@ static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, doubl
 }
 
 template <typename A0, typename F>
+// One CTA per SM.  (Two per SM, with 128 registers per thread, let
+// concurrent systems share SMs, but measured slower: spinning and fp64 work
+// of one system then slow the other's.)
 __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   unsigned char* gsm = smem_raw + kTrsvSmem + kScaledSmem;  // GMRES scalars
