@@ -1104,9 +1104,26 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     // Givens rotations (every CTA computes the same numbers)
     unsigned long long tg0 = (cx.cta == 0 && cx.tid == 0) ? gtimer() : 0;
     if (cx.tid == 0) {
-      // the entry carried from one rotation to the next stays in a register
+      // the entry carried from one rotation to the next stays in a register;
+      // the operands of four rotations are loaded ahead of their use
       U carry = s_h[0];
-      for (int i = 0; i < k; ++i) {
+      int i = 0;
+      for (; i + 4 <= k; i += 4) {
+        U cs[4], sn[4], x1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          cs[q] = sm_cs[i + q];
+          sn[q] = sm_sn[i + q];
+          x1[q] = s_h[i + q + 1];
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const U x0 = carry;
+          s_h[i + q] = M::add(M::mul(cs[q], x0), M::mul(sn[q], x1[q]));
+          carry = M::add(M::mul(-sn[q], x0), M::mul(cs[q], x1[q]));
+        }
+      }
+      for (; i < k; ++i) {
         const U x0 = carry, x1 = s_h[i + 1];
         s_h[i] = M::add(M::mul(sm_cs[i], x0), M::mul(sm_sn[i], x1));
         carry = M::add(M::mul(-sm_sn[i], x0), M::mul(sm_cs[i], x1));
