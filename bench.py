@@ -36,6 +36,35 @@ UNIT = "TFLOP/s"
 WORKLOAD = "sweep_n2000"
 
 
+def measure_gemv(ctx, dev, n=8192, kappa=1e3):
+    """HBM rate of the refinement kernel's operator A_u v (fp32 A_u, fp32 v):
+    one (half, single, double) solve at n = 8192, whose SGMRES-IR stage
+    applies the operator once per GMRES iteration.  Algorithmic bytes per
+    application: the n x n fp32 A_u (the vector is L2-resident); time: the
+    kernel's own operator-phase timer (CTA 0; every CTA does the same share).
+    A_u (268 MB) is larger than L2, so each application streams it from HBM."""
+    import torch
+    from synth import randsvd_system
+    A, B, _ = randsvd_system(n, kappa, 0, device=str(dev))
+    At = torch.from_numpy(A).to(dev)
+    bt = torch.from_numpy(B[:, 0].copy()).to(dev)
+    del A, B
+    ctx.solve(At, bt, "fp16,fp32,fp64")
+    x, reps, st = ctx.solve(At, bt, "fp16,fp32,fp64")
+    r = reps[0]
+    iters = r["total_gmres_iters"]
+    t_op = r["t_phase_ms"][4] * 1e-3
+    if iters <= 0 or t_op <= 0:
+        return None
+    achieved = n * n * 4.0 * iters / t_op / 1e9
+    peak, kind = peaks()
+    del At, bt, x
+    torch.cuda.empty_cache()
+    return {"kernel": "refine_kernel operator A_u v (fp32)", "n": n, "applications": iters,
+            "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "peak_source": kind, "stages": r["steps"]}
+
+
 def max_over_ranks(ms, world, device=None):
     """The job's time is the slowest rank's (all_reduce MAX; identity at N = 1)."""
     if world <= 1:
@@ -209,6 +238,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gemv", action="store_true", help="skip the operator bandwidth measurement")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                     help="run one untimed solve of a named small case (for ncu captures) and exit")
     ap.add_argument("--sequential", action="store_true",
@@ -350,6 +380,8 @@ def main():
         fp64_s, fp64_val = float("nan"), None
         print(f"fp64 LU comparator unavailable: {exc}", file=sys.stderr)
 
+    gemv = measure_gemv(ctx, dev) if (rank == 0 and not args.no_gemv) else None
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = run_cpu_baseline()
@@ -376,6 +408,7 @@ def main():
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind},
             "time_split_ms": {"factor": fac_ms, "refine": ref_ms},
             "cpu_baseline": cpu,
+            "gemv": gemv,
             "clocks": clk.summary(),
             "gpu_launches": launches,
             "wall_s": wall,

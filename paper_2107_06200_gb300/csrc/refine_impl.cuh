@@ -87,20 +87,93 @@ template <> struct AV<double> {
   static __device__ __forceinline__ double ld(const double* p) { return __ldg(p); }
 };
 
-// Row dot products a_row . x, one warp, result on every lane.
-template <typename A0>
-__device__ double row_dot_d(const A0* row, const double* x, int n, int lane) {
+// Four consecutive values widened to double from a 16-byte aligned
+// address: matrix rows through the read-only path, vectors through L2
+// (they are rewritten during the kernel).
+template <typename T> struct Ld4;
+template <> struct Ld4<float> {
+  static __device__ __forceinline__ void row(const float* p, double (&v)[4]) {
+    const float4 f = __ldg((const float4*)p);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+  }
+  static __device__ __forceinline__ void vec(const float* p, double (&v)[4]) {
+    const float4 f = __ldcg((const float4*)p);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+  }
+};
+template <> struct Ld4<double> {
+  static __device__ __forceinline__ void row(const double* p, double (&v)[4]) {
+    const double2 f = __ldg((const double2*)p), g = __ldg((const double2*)p + 1);
+    v[0] = f.x; v[1] = f.y; v[2] = g.x; v[3] = g.y;
+  }
+  static __device__ __forceinline__ void vec(const double* p, double (&v)[4]) {
+    const double2 f = __ldcg((const double2*)p), g = __ldcg((const double2*)p + 1);
+    v[0] = f.x; v[1] = f.y; v[2] = g.x; v[3] = g.y;
+  }
+};
+
+// Four consecutive values as float (fp32 paths: no fp64 conversions).
+template <typename T>
+__device__ __forceinline__ void ld4f_row(const T* p, float (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 f = __ldg((const float4*)p);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (float)__ldg(p + q);
+  }
+}
+template <typename T>
+__device__ __forceinline__ void ld4f_vec(const T* p, float (&v)[4]) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 f = __ldcg((const float4*)p);
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = (float)__ldcg(p + q);
+  }
+}
+
+// Row dot products a_row . x by one warp (result on every lane).  Lanes
+// take four consecutive columns at a time with 16-byte loads, several
+// steps in flight, so that a warp streams its row at HBM speed; rows start
+// on 64-element boundaries, x is checked for 16-byte alignment.
+template <typename A0, typename X>
+__device__ double row_dot_d(const A0* row, const X* x, int n, int lane) {
   double acc = 0.0;
-  for (int j = lane; j < n; j += 32) acc = __fma_rn(AV<A0>::ld(row + j), __ldcg(x + j), acc);
+  const int n4 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) ? (n & ~3) : 0;
+#pragma unroll 4
+  for (int j = lane * 4; j < n4; j += 128) {
+    double av[4], xv[4];
+    Ld4<A0>::row(row + j, av);
+    Ld4<X>::vec(x + j, xv);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc = __fma_rn(av[q], xv[q], acc);
+  }
+  for (int j = n4 + lane; j < n; j += 32) acc = __fma_rn(AV<A0>::ld(row + j), (double)__ldcg(x + j), acc);
   return warp_sum_d(acc);
 }
 // Compensated (twice-working-precision) dot product, result as dd.
-template <typename A0>
-__device__ dd_t row_dot_dd(const A0* row, const double* x, int n, int lane) {
+template <typename A0, typename X>
+__device__ dd_t row_dot_dd(const A0* row, const X* x, int n, int lane) {
   double s = 0.0, c = 0.0;
-  for (int j = lane; j < n; j += 32) {
-    dd_t p = two_prod(AV<A0>::ld(row + j), __ldcg(x + j));
-    dd_t t = two_sum(s, p.hi);
+  const int n4 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) ? (n & ~3) : 0;
+#pragma unroll 2
+  for (int j = lane * 4; j < n4; j += 128) {
+    double av[4], xv[4];
+    Ld4<A0>::row(row + j, av);
+    Ld4<X>::vec(x + j, xv);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const dd_t p = two_prod(av[q], xv[q]);
+      const dd_t t = two_sum(s, p.hi);
+      s = t.hi;
+      c = __dadd_rn(c, __dadd_rn(t.lo, p.lo));
+    }
+  }
+  for (int j = n4 + lane; j < n; j += 32) {
+    const dd_t p = two_prod(AV<A0>::ld(row + j), (double)__ldcg(x + j));
+    const dd_t t = two_sum(s, p.hi);
     s = t.hi;
     c = __dadd_rn(c, __dadd_rn(t.lo, p.lo));
   }
@@ -900,7 +973,21 @@ __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
         rows[rr] = A + (size_t)a.perm[i] * a.lda;
         acc[rr] = 0.0f;
       }
-      for (int j = cx.lane; j < cx.n; j += 32) {
+      // four consecutive columns per lane and step, 16-byte loads
+      const int n4 = ((reinterpret_cast<uintptr_t>(v) & 15) == 0) ? (cx.n & ~3) : 0;
+#pragma unroll 2
+      for (int j = cx.lane * 4; j < n4; j += 128) {
+        float vv[4];
+        ld4f_vec<U>(v + j, vv);
+#pragma unroll
+        for (int rr = 0; rr < 8; ++rr) {
+          float av[4];
+          ld4f_row<A0>(rows[rr] + j, av);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[rr] = __fmaf_rn(av[q], vv[q], acc[rr]);
+        }
+      }
+      for (int j = n4 + cx.lane; j < cx.n; j += 32) {
         const float vj = (float)__ldcg(v + j);
 #pragma unroll
         for (int rr = 0; rr < 8; ++rr) acc[rr] = __fmaf_rn((float)__ldg(rows[rr] + j), vj, acc[rr]);
@@ -926,19 +1013,10 @@ __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
     const A0* row = A + (size_t)ar * a.lda;
     const double R = rscale(a, ar);
     if (op == MSIR_DD) {
-      double sh = 0.0, sc = 0.0;
-      for (int j = cx.lane; j < cx.n; j += 32) {
-        const dd_t p = two_prod((double)__ldg(row + j), (double)__ldcg(v + j));
-        const dd_t t = two_sum(sh, p.hi);
-        sh = t.hi;
-        sc = __dadd_rn(sc, __dadd_rn(t.lo, p.lo));
-      }
-      const dd_t tt = warp_sum_dd(fast_two_sum(sh, sc));
+      const dd_t tt = row_dot_dd<A0, U>(row, v, cx.n, cx.lane);
       if (cx.lane == 0) { a.c_hi[i] = tt.hi * R; a.c_lo[i] = tt.lo * R; }
     } else {
-      double acc = 0.0;
-      for (int j = cx.lane; j < cx.n; j += 32) acc = __fma_rn((double)__ldg(row + j), (double)__ldcg(v + j), acc);
-      acc = warp_sum_d(acc);
+      const double acc = row_dot_d<A0, U>(row, v, cx.n, cx.lane);
       if (cx.lane == 0) a.c_hi[i] = acc * R;
     }
   }
