@@ -333,7 +333,13 @@ def main():
     u0s = {"fp32": 2.0 ** -24, "fp64": 2.0 ** -53}
     nbe_ok = all(r["cged"] and r["nbe"] <= 2 * u0s[s.split(",")[1]]
                  for r, s in zip(all_reps[-1], specs))
-    lat = sorted(r["t_factor_ms"] + r["t_refine_ms"] for reps in all_reps for r in reps)
+    # per-system latency (device time of factorisations and refinement) over
+    # at least 200 solves: the timed steps, then further untimed steps
+    lat = [r["t_factor_ms"] + r["t_refine_ms"] for reps in all_reps for r in reps]
+    tl = time.perf_counter()
+    while len(lat) < 200 and time.perf_counter() - tl < 20.0:
+        _, reps_x, _ = step()
+        lat.extend(r["t_factor_ms"] + r["t_refine_ms"] for r in reps_x)
     p50 = float(np.percentile(lat, 50))
     p99 = float(np.percentile(lat, 99))
 
@@ -365,9 +371,11 @@ def main():
 
     # comparator: plain fp64 LU solve of the same systems on the same GPU
     def fp64_step():
+        xs64 = []
         for A, b in zip(As, bs):
             LU, piv = torch.linalg.lu_factor(A)
-            torch.linalg.lu_solve(LU, piv, b[:, None])
+            xs64.append(torch.linalg.lu_solve(LU, piv, b[:, None])[:, 0])
+        return xs64
     try:
         fp64_step()
         torch.cuda.synchronize()
@@ -376,8 +384,14 @@ def main():
         torch.cuda.synchronize()
         fp64_s = time.perf_counter() - tf
         fp64_val = fl_step / fp64_s / 1e12
+        # its normwise backward error, for comparison with the 2 u0 target
+        fp64_nbe = 0.0
+        for A, b, x64 in zip(As, bs, fp64_step()):
+            r64 = b - A @ x64
+            fp64_nbe = max(fp64_nbe, float(torch.max(torch.abs(r64)) / (
+                torch.max(torch.abs(A).sum(1)) * torch.max(torch.abs(x64)) + torch.max(torch.abs(b)))))
     except Exception as exc:  # e.g. torch's linalg library not loadable in this environment
-        fp64_s, fp64_val = float("nan"), None
+        fp64_s, fp64_val, fp64_nbe = float("nan"), None, None
         print(f"fp64 LU comparator unavailable: {exc}", file=sys.stderr)
 
     gemv = measure_gemv(ctx, dev) if (rank == 0 and not args.no_gemv) else None
@@ -396,11 +410,13 @@ def main():
                        "triples": ["fp16,fp32,fp64", "fp32,fp64,dd"], "graded": "both",
                        "l2": "inputs larger than L2 (14 fp64 2000x2000 matrices per step)",
                        "parallelism": f"weak x{world}", "mode": "sequential msir_solve" if args.sequential else "msir_solve_batched"},
-            "latency_ms": {"p50": p50, "p99": p99},
+            "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat)},
             "all_converged_nbe_le_2u0": nbe_ok,
             "fp64_lu": {"value": fp64_val, "unit": UNIT,
                         "ms_per_step": None if fp64_val is None else fp64_s * 1e3,
-                        "impl": "torch.linalg.lu_factor+lu_solve float64"},
+                        "nbe_max": fp64_nbe,
+                        "impl": "torch.linalg.lu_factor+lu_solve float64",
+                        "versions": {"torch": torch.__version__, "cuda": torch.version.cuda}},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "roofline": {"bound": "hbm", "kernel": "refine_kernel (persistent refinement)",

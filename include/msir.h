@@ -24,8 +24,11 @@
  *   - The caller owns every buffer it passes; the library never frees them
  *     and keeps no pointer to them after the call returns.  The library owns
  *     contexts, factor objects and servers; each has a destroy call.
- *   - Work is ordered on the context's CUDA stream.  Calls that return a
- *     report synchronise that stream before returning.
+ *   - Work is ordered after the context's CUDA stream: device inputs must be
+ *     complete on that stream (or on the host) when a call starts; work a
+ *     caller enqueued on other streams is not waited for.  Every call except
+ *     msir_residual_noalloc returns with its outputs complete (it
+ *     synchronises the streams it used).
  *   - No call throws across this interface.  Every call returns an
  *     msir_status; on error nothing is written to the caller's outputs
  *     except where a call says otherwise.
