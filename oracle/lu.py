@@ -46,15 +46,18 @@ def _argmax_abs(col):
     return int(np.argmax(a))  # first occurrence -> smallest row on ties
 
 
-def default_blocking(fmt_f):
+def default_blocking(fmt_f, n=0):
     """Default (nb, nbo): inner panel width and outer block width (the same
     defaults as the GPU library, which reports the values it used).
 
     The panel is held in the arithmetic precision while it is factored, so it
-    is narrower when that precision is fp64."""
+    is narrower when that precision is fp64.  From n = 4096 the outer blocks
+    are 128 wide: the trailing matrix is stored in u_f after every outer
+    block, so fewer, wider blocks round it fewer times."""
+    nbo = 128 if n >= 4096 else 64
     if fmt_f == FP64:
-        return 16, 64
-    return 32, 64
+        return 16, nbo
+    return 32, nbo
 
 
 def _panel(F, kk, w, T, fmt_f, ipiv, trace=None):
@@ -132,7 +135,7 @@ def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None):
     index of the first exactly-zero pivot, 0 if none."""
     A = np.asarray(A)
     n = A.shape[0]
-    dnb, dnbo = default_blocking(fmt_f)
+    dnb, dnbo = default_blocking(fmt_f, n)
     nb = nb or dnb
     nbo = nbo or nb * -(-dnbo // nb)
     if nbo % nb:
