@@ -333,6 +333,28 @@ static bool lu_timers_enabled() {
   return v == 1;
 }
 
+// CTAs of the panel's cluster: enough to hold the panel in shared memory,
+// and otherwise one per kPanelRows rows, up to 16 for panels of more than
+// 4096 rows and up to 8 below (a smaller cluster finds free SMs sooner
+// beside the persistent refinement kernels of concurrent solves).
+// MSIR_PANEL_CTAS and MSIR_PANEL_ROWS override the cap and the row count
+// (tuning only).
+static int env_int(const char* name, int dflt, int lo, int hi) {
+  const char* e = getenv(name);
+  if (!e) return dflt;
+  const int v = atoi(e);
+  return v >= lo && v <= hi ? v : dflt;
+}
+static int panel_ctas(int m, int Rmax) {
+  static const int kPanelCtas = env_int("MSIR_PANEL_CTAS", 0, 1, 16);
+  static const int kPanelRows = env_int("MSIR_PANEL_ROWS", 192, 32, 4096);
+  const int cap = kPanelCtas > 0 ? kPanelCtas : (m > 4096 ? 16 : 8);
+  int C = (m + Rmax - 1) / Rmax;
+  if (C > 16) return -1;
+  C = std::max(C, std::min(cap, (m + kPanelRows - 1) / kPanelRows));
+  return std::max(1, std::min(C, 16));
+}
+
 // Enqueue the LU of fl_fmt(A_u) (optionally squeezed) into level slot l.
 // The host reads info / nonfinite after the stream reaches the end.
 static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l, int fmt, int nb,
@@ -375,10 +397,8 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
   for (int k = 0; k < n; k += nbo) {
     const int W = std::min(nbo, n - k);
     const int m = n - k;
-    int C = (m + Rmax - 1) / Rmax;
-    if (C > 16) return MSIR_ERR_UNSUPPORTED;
-    C = std::max(C, std::min(8, (m + 191) / 192));
-    C = std::max(1, std::min(C, 16));
+    const int C = panel_ctas(m, Rmax);
+    if (C < 0) return MSIR_ERR_UNSUPPORTED;
     PanelArgs pa;
     pa.A = L.F;
     pa.lda = ldf;

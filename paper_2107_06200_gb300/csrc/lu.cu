@@ -73,6 +73,16 @@ __device__ __forceinline__ void warp_argmax(T& v, int& i) {
     if (better(ov, oi, v, i)) { v = ov; i = oi; }
   }
 }
+// The same order for float by two warp reductions: v is -2 (no candidate),
+// -1 (NaN) or a non-negative float, whose bits order like its values, so
+// the key 0 / 1 / bits + 2 is monotone in v; the smallest index among the
+// lanes holding the largest key wins.
+__device__ __forceinline__ void warp_argmax(float& v, int& i) {
+  const unsigned key = v == -2.f ? 0u : v == -1.f ? 1u : __float_as_uint(v) + 2u;
+  const unsigned mk = __reduce_max_sync(0xffffffffu, key);
+  i = __reduce_min_sync(0xffffffffu, key == mk ? i : INT_MAX);
+  v = mk == 0u ? -2.f : mk == 1u ? -1.f : __uint_as_float(mk - 2u);
+}
 
 // ------------------------------------------------------------------ panel
 
@@ -80,9 +90,11 @@ __device__ __forceinline__ void warp_argmax(T& v, int& i) {
 // barrier of the column loop, 2 pivot search + push, 3 rank-1 update,
 // 4 panel store + permutation maps, 5 inner interchanges + substitution,
 // 6 inner update, 7 panel load.
+// They add up in shared memory and reach a.tdbg once, at the kernel's end,
+// so that the measurement keeps global-memory round trips off the loop.
 #define PT_BEGIN(id) unsigned long long _t##id = (a.tdbg && rank == 0 && tid == 0) ? gtimer() : 0
 #define PT_END(id) \
-  if (a.tdbg && rank == 0 && tid == 0) a.tdbg[id] += gtimer() - _t##id
+  if (a.tdbg && rank == 0 && tid == 0) s_tacc[id] += gtimer() - _t##id
 
 constexpr int kInnerRows = 8;   // rows per warp step of the inner update
 
@@ -119,8 +131,10 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
   __shared__ T s_wv[NW];
   __shared__ int s_wi[NW];
   __shared__ int s_cnt, s_ocnt, s_nf;
+  __shared__ unsigned long long s_tacc[8];
 
   if (tid == 0) { s_ocnt = W; s_nf = 0; }
+  if (tid < 8) s_tacc[tid] = 0;
   for (int s = tid; s < W; s += blockDim.x) { opos[s] = s; oval[s] = s; }
   __syncthreads();
 
@@ -172,16 +186,15 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
           cl.map_shared_rank(cand_v, lane)[buf * 16 + rank] = v;
           cl.map_shared_rank(cand_i, lane)[buf * 16 + rank] = i;
         }
-        const bool valid = i != INT_MAX;
-        const int lb = i - my0;
-        for (int idx = lane; idx < C * w; idx += 32) {
-          const int d = idx / w, c = idx % w;
-          cl.map_shared_rank(cand_row, d)[(buf * 16 + rank) * NBM + c] = valid ? P[lb * ldp + c] : (T)0;
+        // lane c sends column c of the candidate row (w <= 32)
+        if (lane < w) {
+          const T val = i != INT_MAX ? P[(i - my0) * ldp + lane] : (T)0;
+          for (int d = 0; d < C; ++d) cl.map_shared_rank(cand_row, d)[(buf * 16 + rank) * NBM + lane] = val;
         }
       } else if (warp == 1 && ownj == rank) {
-        for (int idx = lane; idx < C * w; idx += 32) {
-          const int d = idx / w, c = idx % w;
-          cl.map_shared_rank(jrow, d)[buf * NBM + c] = P[(j - my0) * ldp + c];
+        if (lane < w) {
+          const T val = P[(j - my0) * ldp + lane];
+          for (int d = 0; d < C; ++d) cl.map_shared_rank(jrow, d)[buf * NBM + lane] = val;
         }
       }
       PT_END(2);
@@ -204,15 +217,58 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
       PT_BEGIN(3);
       const T piv = prow[j];
       if (piv != (T)0) {
+        // pivot row and each updated row staged in registers, so that the
+        // loads of a row are not ordered behind its stores.  Columns go in
+        // chunks of 8: a chunk left of column j+1 is skipped (a uniform
+        // branch), one right of it runs unpredicated.
         for (int li = tid; li < nloc; li += blockDim.x) {
           const int gi = my0 + li;
           if (gi > j) {
             T* row = P + li * ldp;
             const T l = div_rn(row[j], piv);
-            row[j] = l;
+            if (w == NBM) {
 #pragma unroll
-            for (int c = 1; c < NBM; ++c)
-              if (c > j && c < w) row[c] = sub_rn(row[c], mul_rn(l, prow[c]));
+              for (int c0 = 0; c0 < NBM; c0 += 8) {
+                if (c0 + 7 <= j) continue;
+                T rv[8], pv[8];
+                if (c0 > j) {
+#pragma unroll
+                  for (int q = 0; q < 8; ++q) {
+                    rv[q] = row[c0 + q];
+                    pv[q] = prow[c0 + q];
+                  }
+#pragma unroll
+                  for (int q = 0; q < 8; ++q) rv[q] = sub_rn(rv[q], mul_rn(l, pv[q]));
+#pragma unroll
+                  for (int q = 0; q < 8; ++q) row[c0 + q] = rv[q];
+                } else {
+#pragma unroll
+                  for (int q = 0; q < 8; ++q)
+                    if (c0 + q > j) {
+                      rv[q] = row[c0 + q];
+                      pv[q] = prow[c0 + q];
+                    }
+#pragma unroll
+                  for (int q = 0; q < 8; ++q)
+                    if (c0 + q > j) rv[q] = sub_rn(rv[q], mul_rn(l, pv[q]));
+#pragma unroll
+                  for (int q = 0; q < 8; ++q)
+                    if (c0 + q > j) row[c0 + q] = rv[q];
+                }
+              }
+            } else {
+              T rv[NBM];
+#pragma unroll
+              for (int c = 1; c < NBM; ++c)
+                if (c > j && c < w) rv[c] = row[c];
+#pragma unroll
+              for (int c = 1; c < NBM; ++c)
+                if (c > j && c < w) rv[c] = sub_rn(rv[c], mul_rn(l, prow[c]));
+#pragma unroll
+              for (int c = 1; c < NBM; ++c)
+                if (c > j && c < w) row[c] = rv[c];
+            }
+            row[j] = l;
           }
         }
       } else if (rank == 0 && tid == 0) {
@@ -226,13 +282,34 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
     // round the panel to F in place, store it, and record its pivots
     PT_BEGIN(4);
     int nf = 0;
+    // full-width panels are written with 16-byte stores (a row segment of
+    // NBM values starts on a 16-byte boundary: kk is a multiple of nb and
+    // lda of 64); the last, narrower panel of a block element by element
+    constexpr int kPer16 = 16 / (int)sizeof(F);
     for (int li = tid; li < nloc; li += blockDim.x) {
       F* dst = A + (size_t)(kk + my0 + li) * lda + kk;
-      for (int c = 0; c < w; ++c) {
-        const F v = store_rn<F>(P[li * ldp + c]);
-        dst[c] = v;
-        P[li * ldp + c] = (T)to_f(v);
-        if (!isfinite(to_f(v))) nf = 1;
+      if (w == NBM) {
+#pragma unroll
+        for (int c0 = 0; c0 < NBM; c0 += kPer16) {
+          unsigned char bytes[16];
+#pragma unroll
+          for (int q = 0; q < kPer16; ++q) {
+            const F v = store_rn<F>(P[li * ldp + c0 + q]);
+            memcpy(bytes + q * sizeof(F), &v, sizeof(F));
+            P[li * ldp + c0 + q] = (T)to_f(v);
+            if (!isfinite(to_f(v))) nf = 1;
+          }
+          uint4 pk;
+          memcpy(&pk, bytes, 16);
+          *reinterpret_cast<uint4*>(dst + c0) = pk;
+        }
+      } else {
+        for (int c = 0; c < w; ++c) {
+          const F v = store_rn<F>(P[li * ldp + c]);
+          dst[c] = v;
+          P[li * ldp + c] = (T)to_f(v);
+          if (!isfinite(to_f(v))) nf = 1;
+        }
       }
     }
     if (nf) s_nf = 1;
@@ -382,6 +459,7 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
   }
 
   if (s_nf) atomicExch(a.nonfinite, 1);
+  if (a.tdbg && rank == 0 && tid < 8) a.tdbg[tid] += s_tacc[tid];
   if (rank == 0) {
     const int oc = s_ocnt;
     for (int s = tid; s < oc; s += blockDim.x) {
