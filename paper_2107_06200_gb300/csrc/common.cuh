@@ -95,6 +95,18 @@ __device__ __forceinline__ dd_t fast_two_sum(double a, double b) {
   double e = __dsub_rn(b, __dsub_rn(s, a));
   return {s, e};
 }
+// The sum and error of two_sum in three fp64 instructions: Dekker's
+// FastTwoSum is exact once its first operand is the larger in magnitude,
+// and the magnitudes are ordered here on the bit patterns (integer
+// instructions; the order of non-negative doubles is that of their bits).
+__device__ __forceinline__ dd_t two_sum_ord(double a, double b) {
+  const unsigned long long ia = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+  const unsigned long long ib = (unsigned long long)__double_as_longlong(b) & 0x7fffffffffffffffull;
+  const bool ab = ia >= ib;
+  const double x = ab ? a : b, y = ab ? b : a;
+  const double s = __dadd_rn(x, y);
+  return {s, __dsub_rn(y, __dsub_rn(s, x))};
+}
 __device__ __forceinline__ dd_t two_prod(double a, double b) {
   double p = __dmul_rn(a, b);
   double e = __fma_rn(a, b, -p);

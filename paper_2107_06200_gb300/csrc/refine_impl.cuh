@@ -166,14 +166,14 @@ __device__ dd_t row_dot_dd(const A0* row, const X* x, int n, int lane) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const dd_t p = two_prod(av[q], xv[q]);
-      const dd_t t = two_sum(s, p.hi);
+      const dd_t t = two_sum_ord(s, p.hi);
       s = t.hi;
       c = __dadd_rn(c, __dadd_rn(t.lo, p.lo));
     }
   }
   for (int j = n4 + lane; j < n; j += 32) {
     const dd_t p = two_prod(AV<A0>::ld(row + j), (double)__ldcg(x + j));
-    const dd_t t = two_sum(s, p.hi);
+    const dd_t t = two_sum_ord(s, p.hi);
     s = t.hi;
     c = __dadd_rn(c, __dadd_rn(t.lo, p.lo));
   }
@@ -433,13 +433,13 @@ struct AccDD {
   static __device__ __forceinline__ A fma(L l, V y, A acc) {
     const dd_t p = two_prod(l, y.hi);
     const double pl = __fma_rn(l, y.lo, p.lo);
-    const dd_t t = two_sum(acc.s, p.hi);
+    const dd_t t = two_sum_ord(acc.s, p.hi);
     return DDAcc{t.hi, __dadd_rn(acc.c, __dadd_rn(t.lo, pl))};
   }
   static __device__ __forceinline__ A ifma(I x, V z, A acc) {
     const dd_t p = two_prod(x.hi, z.hi);
     const double pl = __fma_rn(x.hi, z.lo, __fma_rn(x.lo, z.hi, p.lo));
-    const dd_t t = two_sum(acc.s, p.hi);
+    const dd_t t = two_sum_ord(acc.s, p.hi);
     return DDAcc{t.hi, __dadd_rn(acc.c, __dadd_rn(t.lo, pl))};
   }
   static __device__ __forceinline__ V fin(A acc) { return two_sum(acc.s, acc.c); }
@@ -616,7 +616,7 @@ __device__ __noinline__ bool build_scaled(Cx& cx, const RefineArgs& a, bool dd) 
             const double f = Fb[kk * kScLd + cg * 16 + q];
             const dd_t p = two_prod(xh, f);
             const double pl = __fma_rn(xl, f, p.lo);
-            const dd_t u = two_sum(sh[q], p.hi);
+            const dd_t u = two_sum_ord(sh[q], p.hi);
             sh[q] = u.hi;
             sc[q] = __dadd_rn(sc[q], __dadd_rn(u.lo, pl));
           }
