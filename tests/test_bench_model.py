@@ -1,0 +1,52 @@
+"""The bench's work models for the refinement kernel's roofline, against
+closed forms written out per stage (no GPU)."""
+
+import pytest
+
+import bench
+
+
+def _st(alg, uf, u, ur, steps, iters=()):
+    return {"alg": alg, "uf": uf, "u": u, "ur": ur, "steps": steps, "gmres_iters": list(iters)}
+
+
+def test_fp64_flops_sir_in_low_precision_counts_only_the_residual():
+    n = 100
+    rep = {"stages": [_st("SIR", "fp16", "fp32", "fp64", 3)]}
+    # residual in fp64: n^2 FMAs (2 flops) per step; fp32 substitutions: none
+    assert bench.refine_fp64_flops(rep, n) == 3 * 2 * n * n
+
+
+def test_fp64_flops_gmres_ir_in_dd():
+    n, k = 64, 3
+    rep = {"stages": [_st("GMRES-IR", "fp32", "fp64", "dd", 1, [k])]}
+    per_step = 8 * n * n + 12 * n * n            # dd residual, w0 = M^-1 r in dd
+    per_iter = [(8 + 12) * n * n + 8 * n * (j + 1) for j in range(k)]
+    assert bench.refine_fp64_flops(rep, n) == per_step + sum(per_iter)
+
+
+def test_fp64_flops_sgmres_in_fp32_counts_cgs_and_residual():
+    n, k = 50, 2
+    rep = {"stages": [_st("SGMRES-IR", "fp16", "fp32", "fp64", 1, [k])]}
+    # operator and substitutions in fp32: only the fp64 residual and CGS2 sums
+    assert bench.refine_fp64_flops(rep, n) == 2 * n * n + 8 * n * 1 + 8 * n * 2
+
+
+def test_fp64_flops_sir_after_escalation_to_fp64_factors():
+    n = 10
+    rep = {"stages": [_st("SIR", "fp64", "fp64", "dd", 2)]}
+    assert bench.refine_fp64_flops(rep, n) == 2 * (8 + 2) * n * n
+
+
+def test_fp64_peak_from_unit_counts_and_clock():
+    assert bench.fp64_peak_tflops(2070.0) == pytest.approx(2 * 2 * 152 * 2.07e9 / 1e12)
+
+
+@pytest.mark.parametrize("fp64_flops,bound", [(1e12, "alu"), (1e6, "hbm")])
+def test_roofline_takes_the_larger_model_time(fp64_flops, bound):
+    line = bench.roofline_line(1e9, fp64_flops, 100.0, 0.1, 6779.4, "measured", 1.25, 4.0)
+    assert line["bound"] == bound
+    top = line["fp64"] if bound == "alu" else line["hbm"]
+    assert line["achieved"] == top["achieved"] and line["frac"] == pytest.approx(top["frac"])
+    assert line["frac_of_gpu_share"] == pytest.approx(line["frac"] * 4.0)
+    assert line["traffic"] is None
