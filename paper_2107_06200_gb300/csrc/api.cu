@@ -194,7 +194,7 @@ struct Workspace {
   void* Ut = nullptr;
   int* map = nullptr;       // map_pos | map_val | map_cnt
   int* iflags = nullptr;    // info, nonfinite, err
-  double *x, *xn, *x0, *xbest, *r_hi, *r_lo, *c_hi, *c_lo, *y_hi, *y_lo, *z_hi, *z_lo, *d, *w;
+  double *x, *xn, *x0, *xbest, *r_hi, *r_lo, *c_hi, *c_lo, *y_hi, *y_lo, *z_hi, *z_lo, *d, *w, *vk;
   double* V = nullptr;
   int ldv = 0;
   double *H, *yv, *red, *hred, *hvec;
@@ -250,10 +250,10 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
   w.map = (int*)take((4 * 256 + 8) * 4);
   w.iflags = (int*)take(32 * 4);
   double** vecs[] = {&w.x, &w.xn, &w.x0, &w.xbest, &w.r_hi, &w.r_lo, &w.c_hi,
-                     &w.c_lo, &w.y_hi, &w.y_lo, &w.z_hi, &w.z_lo, &w.d, &w.w};
+                     &w.c_lo, &w.y_hi, &w.y_lo, &w.z_hi, &w.z_lo, &w.d, &w.w, &w.vk};
   for (double** v : vecs) *v = (double*)take(n * 8);
-  w.ldv = (int)round_up((size_t)n, 32);
-  w.V = (double*)take((size_t)(kcap + 1) * w.ldv * 8);
+  w.ldv = (int)round_up((size_t)kcap + 1, 32);
+  w.V = (double*)take((size_t)n * w.ldv * 8);
   w.H = (double*)take((size_t)(kcap + 1) * kcap * 8);
   w.yv = (double*)take((size_t)(kcap + 1) * 8);
   w.red = (double*)take((size_t)2 * G * kRedW * 8);
@@ -587,7 +587,7 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   a.x = w.x; a.xn = w.xn; a.x0 = w.x0; a.xbest = w.xbest;
   a.r_hi = w.r_hi; a.r_lo = w.r_lo; a.c_hi = w.c_hi; a.c_lo = w.c_lo;
   a.y_hi = w.y_hi; a.y_lo = w.y_lo; a.z_hi = w.z_hi; a.z_lo = w.z_lo;
-  a.d = w.d; a.w = w.w; a.V = w.V; a.ldv = w.ldv;
+  a.d = w.d; a.w = w.w; a.V = w.V; a.ldv = w.ldv; a.vk = w.vk;
   a.H = w.H; a.yv = w.yv; a.red = w.red; a.hred = w.hred; a.hvec = w.hvec;
   a.ll = w.ll; a.bar = w.bar;
   a.inv32 = L.inv32; a.inv_hi = L.inv_hi; a.inv_lo = L.inv_lo;

@@ -81,8 +81,9 @@ struct RefineArgs {
   double* z_lo;
   double* d;               // correction
   double* w;               // GMRES work vector
-  double* V;               // Krylov basis: vector j at V + j*ldv
-  int ldv;
+  double* V;               // Krylov basis in u, row-major: entry j of row i at
+  int ldv;                 //   V + i*ldv (ldv >= kcap + 1)
+  double* vk;              // the newest basis vector, contiguous (operator input)
   double* H;               // rotated Hessenberg, column-major (kcap+1) x kcap
   double* yv;              // GMRES least-squares solution (kcap)
   double* red;             // reduction scratch: 2 * gridDim.x * kRedW

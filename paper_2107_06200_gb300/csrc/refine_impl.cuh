@@ -1074,11 +1074,12 @@ __device__ void cgs_partials(Cx& cx, const RefineArgs& a, const U* V, const U* w
   // flat rows, in row order (the loads are independent of the running sum)
   int r0, r1;
   flat_rows(cx, r0, r1);
+  // (the basis is row-major, so a warp's loads of one row are coalesced)
   for (int j = cx.tid; j < kp1; j += kRefThreads) {
-    const U* Vj = V + (size_t)j * a.ldv;
     double acc = 0.0;
 #pragma unroll 8
-    for (int i = r0; i < r1; ++i) acc = __fma_rn((double)__ldcg(Vj + i), (double)__ldcg(w + i), acc);
+    for (int i = r0; i < r1; ++i)
+      acc = __fma_rn((double)__ldcg(V + (size_t)i * a.ldv + j), (double)__ldcg(w + i), acc);
     a.hred[(size_t)cx.cta * (a.kcap + 1) + j] = acc;
   }
 }
@@ -1090,7 +1091,8 @@ __device__ __forceinline__ double basis_row_dot(const RefineArgs& a, const U* V,
                                                 int lane) {
   double acc = 0.0;
 #pragma unroll 4
-  for (int j = lane; j < kp1; j += 32) acc = __fma_rn((double)__ldcg(V + (size_t)j * a.ldv + i), (double)c[j], acc);
+  const U* Vi = V + (size_t)i * a.ldv;
+  for (int j = lane; j < kp1; j += 32) acc = __fma_rn((double)__ldcg(Vi + j), (double)c[j], acc);
   return warp_sum_d(acc);
 }
 
@@ -1135,6 +1137,7 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
   U* sm_g = sm_sn + kcap + 1;   // kcap + 2
   U* s_h = sm_g + kcap + 2;     // 2 (kcap + 1)
   U* V = (U*)a.V;
+  U* vk = (U*)a.vk;
   U* w = (U*)a.w;
   out.k = 0;
   out.nonfinite = false;
@@ -1155,14 +1158,18 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     for (int i = f0 + cx.tid; i < f1; i += kRefThreads) a.d[i] = 0.0;
     return grid_barrier(a.bar, a.err, cx.G);  // d is read by the block partition
   }
-  for (int i = f0 + cx.tid; i < f1; i += kRefThreads) V[i] = M::div(w[i], beta);
+  for (int i = f0 + cx.tid; i < f1; i += kRefThreads) {
+    const U v = M::div(w[i], beta);
+    V[(size_t)i * a.ldv] = v;
+    vk[i] = v;
+  }
   if (cx.tid == 0) sm_g[0] = beta;
   __syncthreads();
   int kdone = 0;
   for (int k = 0; k < kcap; ++k) {
     // full V_k needed by the matrix-vector product
     if (!grid_barrier(a.bar, a.err, cx.G)) return false;
-    if (!apply_A<A0, U>(cx, a, V + (size_t)k * a.ldv, op)) return false;
+    if (!apply_A<A0, U>(cx, a, vk, op)) return false;
     if (!msolve_arith<F>(cx, a, op, op)) return false;
     if (!finish_solve<U>(cx, a, w, op)) return false;
     // classical Gram-Schmidt, twice
@@ -1233,7 +1240,11 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     const double relres = s_bc[0];
     kdone = k + 1;
     if (hk1 != (U)0 && isfinite((double)hk1)) {
-      for (int i = f0 + cx.tid; i < f1; i += kRefThreads) V[(size_t)(k + 1) * a.ldv + i] = M::div(w[i], hk1);
+      for (int i = f0 + cx.tid; i < f1; i += kRefThreads) {
+        const U v = M::div(w[i], hk1);
+        V[(size_t)i * a.ldv + k + 1] = v;
+        vk[i] = v;
+      }
     }
     __syncthreads();
     if (!isfinite(relres) || relres <= tau || hk1 == (U)0) break;
