@@ -1077,35 +1077,50 @@ __device__ void cgs_partials(Cx& cx, const RefineArgs& a, const U* V, const U* w
   // (the basis is row-major, so a warp's loads of one row are coalesced)
   for (int j = cx.tid; j < kp1; j += kRefThreads) {
     double acc = 0.0;
-#pragma unroll 8
+#pragma unroll 16
     for (int i = r0; i < r1; ++i)
       acc = __fma_rn((double)__ldcg(V + (size_t)i * a.ldv + j), (double)__ldcg(w + i), acc);
     a.hred[(size_t)cx.cta * (a.kcap + 1) + j] = acc;
   }
 }
 
-// sum_j V_j[i] c_j for row i by one warp (lanes over j, then a warp sum);
-// the result is in every lane
+// sum_j V_j[i] c_j for the rows i0 .. i0+kRows-1 (those below r1) by one
+// warp: lane l sums j = l, l+32, ... in order, then a butterfly over the
+// lanes.  The rows' loads and reductions are independent, so their
+// latencies overlap.  Lane q < kRows returns row i0+q.
+constexpr int kRows = 8;
 template <typename U>
-__device__ __forceinline__ double basis_row_dot(const RefineArgs& a, const U* V, int i, int kp1, const U* c,
-                                                int lane) {
-  double acc = 0.0;
-#pragma unroll 4
-  const U* Vi = V + (size_t)i * a.ldv;
-  for (int j = lane; j < kp1; j += 32) acc = __fma_rn((double)__ldcg(Vi + j), (double)c[j], acc);
-  return warp_sum_d(acc);
+__device__ __forceinline__ double basis_rows_dot(const RefineArgs& a, const U* V, int i0, int r1, int kp1,
+                                                 const U* c, int lane) {
+  double acc[kRows];
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) acc[q] = 0.0;
+  for (int j = lane; j < kp1; j += 32) {
+    const double cj = (double)c[j];
+#pragma unroll
+    for (int q = 0; q < kRows; ++q)
+      if (i0 + q < r1) acc[q] = __fma_rn((double)__ldcg(V + (size_t)(i0 + q) * a.ldv + j), cj, acc[q]);
+  }
+  double mine = 0.0;
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) {
+    const double t = warp_sum_d(acc[q]);
+    if (lane == q) mine = t;
+  }
+  return mine;
 }
 
-// w_i = fl_u(w_i - sum_j V_j[i] h_j), the sum in fp64; flat rows, a warp
-// per row
+// w_i = fl_u(w_i - sum_j V_j[i] h_j), the sum in fp64; flat rows, kRows
+// rows per warp at a time
 template <typename U>
 __device__ void cgs_update(Cx& cx, const RefineArgs& a, const U* V, U* w, int kp1, const U* s_h) {
   PhaseTimer pt(cx, 3);
   int r0, r1;
   flat_rows(cx, r0, r1);
-  for (int i = r0 + cx.warp; i < r1; i += kRefThreads / 32) {
-    const double acc = basis_row_dot<U>(a, V, i, kp1, s_h, cx.lane);
-    if (cx.lane == 0) w[i] = UA<U>::rnd(__dsub_rn((double)w[i], acc));
+  for (int i0 = r0 + cx.warp * kRows; i0 < r1; i0 += (kRefThreads / 32) * kRows) {
+    const double acc = basis_rows_dot<U>(a, V, i0, r1, kp1, s_h, cx.lane);
+    const int i = i0 + cx.lane;
+    if (cx.lane < kRows && i < r1) w[i] = UA<U>::rnd(__dsub_rn((double)w[i], acc));
   }
   __syncthreads();
 }
@@ -1261,9 +1276,10 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
   if (!grid_barrier(a.bar, a.err, cx.G)) return false;
   for (int j = cx.tid; j < kdone; j += kRefThreads) s_h[j] = (U)__ldcg(a.yv + j);
   __syncthreads();
-  for (int i = f0 + cx.warp; i < f1; i += kRefThreads / 32) {
-    const double acc = basis_row_dot<U>(a, V, i, kdone, s_h, cx.lane);
-    if (cx.lane == 0) a.d[i] = (double)M::rnd(acc);
+  for (int i0 = f0 + cx.warp * kRows; i0 < f1; i0 += (kRefThreads / 32) * kRows) {
+    const double acc = basis_rows_dot<U>(a, V, i0, f1, kdone, s_h, cx.lane);
+    const int i = i0 + cx.lane;
+    if (cx.lane < kRows && i < f1) a.d[i] = (double)M::rnd(acc);
   }
   out.k = kdone;
   return grid_barrier(a.bar, a.err, cx.G);  // d is read by the block partition
