@@ -153,6 +153,36 @@ __device__ double row_dot_d(const A0* row, const X* x, int n, int lane) {
   for (int j = n4 + lane; j < n; j += 32) acc = __fma_rn(AV<A0>::ld(row + j), (double)__ldcg(x + j), acc);
   return warp_sum_d(acc);
 }
+// row_dot_d for NR rows at once (the same sums, row by row): x is loaded
+// once for all rows, and the rows' chains and reductions are independent,
+// so one warp keeps more loads and fp64 work in flight.  (The dd product
+// keeps one row per warp: it is bound by fp64 throughput, not latency.)
+template <typename A0, typename X, int NR>
+__device__ void rows_dot_d(const A0* const (&row)[NR], const X* x, int n, int lane, double (&out)[NR]) {
+  double acc[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) acc[r] = 0.0;
+  const int n4 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) ? (n & ~3) : 0;
+#pragma unroll 2
+  for (int j = lane * 4; j < n4; j += 128) {
+    double xv[4];
+    Ld4<X>::vec(x + j, xv);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      double av[4];
+      Ld4<A0>::row(row[r] + j, av);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[r] = __fma_rn(av[q], xv[q], acc[r]);
+    }
+  }
+  for (int j = n4 + lane; j < n; j += 32) {
+    const double xj = (double)__ldcg(x + j);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = __fma_rn(AV<A0>::ld(row[r] + j), xj, acc[r]);
+  }
+#pragma unroll
+  for (int r = 0; r < NR; ++r) out[r] = warp_sum_d(acc[r]);
+}
 // Compensated (twice-working-precision) dot product, result as dd.
 template <typename A0, typename X>
 __device__ dd_t row_dot_dd(const A0* row, const X* x, int n, int lane) {
@@ -1008,16 +1038,29 @@ __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
     return true;
   }
   const int nw = cx.G * (kRefThreads / 32);
-  for (int i = cx.cta * (kRefThreads / 32) + cx.warp; i < cx.n; i += nw) {
-    const int ar = a.perm[i];
-    const A0* row = A + (size_t)ar * a.lda;
-    const double R = rscale(a, ar);
-    if (op == MSIR_DD) {
-      const dd_t tt = row_dot_dd<A0, U>(row, v, cx.n, cx.lane);
-      if (cx.lane == 0) { a.c_hi[i] = tt.hi * R; a.c_lo[i] = tt.lo * R; }
-    } else {
-      const double acc = row_dot_d<A0, U>(row, v, cx.n, cx.lane);
-      if (cx.lane == 0) a.c_hi[i] = acc * R;
+  if (op == MSIR_DD) {
+    for (int i = cx.cta * (kRefThreads / 32) + cx.warp; i < cx.n; i += nw) {
+      const int ar = a.perm[i];
+      const dd_t tt = row_dot_dd<A0, U>(A + (size_t)ar * a.lda, v, cx.n, cx.lane);
+      if (cx.lane == 0) {
+        const double R = rscale(a, ar);
+        a.c_hi[i] = tt.hi * R;
+        a.c_lo[i] = tt.lo * R;
+      }
+    }
+    return grid_barrier(a.bar, a.err, cx.G);
+  }
+  // fp64: two rows per warp at a time (rows i and i + nw); a missing second
+  // row repeats the first and is not stored
+  for (int i = cx.cta * (kRefThreads / 32) + cx.warp; i < cx.n; i += 2 * nw) {
+    const int i2 = i + nw < cx.n ? i + nw : i;
+    const int ar[2] = {a.perm[i], a.perm[i2]};
+    const A0* const rows[2] = {A + (size_t)ar[0] * a.lda, A + (size_t)ar[1] * a.lda};
+    double acc[2];
+    rows_dot_d<A0, U, 2>(rows, v, cx.n, cx.lane, acc);
+    if (cx.lane == 0) {
+      a.c_hi[i] = acc[0] * rscale(a, ar[0]);
+      if (i2 != i) a.c_hi[i2] = acc[1] * rscale(a, ar[1]);
     }
   }
   return grid_barrier(a.bar, a.err, cx.G);
