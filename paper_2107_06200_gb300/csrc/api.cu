@@ -597,6 +597,13 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   a.rho_thresh = j.p.rho_thresh;
   a.kmax = j.p.kmax_frac * j.n;
   a.kcap = kcap_of(j.n, j.p.kmax_frac);
+  // MSIR_TEAM_K (1, 2, 4 or 8) fixes the fp64/dd substitution team size
+  // (tuning only; the default rule is in team_size)
+  static const int team_k = [] {
+    const int v = env_int("MSIR_TEAM_K", 0, 1, 8);
+    return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
+  }();
+  a.team_k = team_k;
   a.tau = j.p.tau;
   a.gamma = j.p.gamma;
   a.conv = j.p.conv;

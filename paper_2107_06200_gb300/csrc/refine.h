@@ -109,6 +109,7 @@ struct RefineArgs {
   double rho_thresh;
   double kmax;
   int kcap;
+  int team_k;              // substitution team size for fp64/dd (0: the rule in team_size)
   double tau;              // <= 0: by u
   double gamma;
   int conv;

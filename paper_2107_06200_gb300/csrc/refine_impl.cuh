@@ -29,6 +29,7 @@ namespace msir {
 
 struct Cx {
   int G, cta, tid, lane, warp, n, nblk;
+  int team_k;  // RefineArgs::team_k
   unsigned epoch;
   int redbuf;
   unsigned long long* t_ns;  // per-phase timers (CTA 0, thread 0), shared memory
@@ -828,6 +829,7 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
 template <typename ACC>
 __device__ __forceinline__ int team_size(const Cx& cx) {
   if (ACC::kW == 1) return 1;
+  if (cx.team_k > 0) return cx.team_k <= cx.G ? cx.team_k : 1;
   const int half = (cx.nblk + 1) / 2;
   if (cx.G / 8 >= half) return 8;
   if (cx.G / 4 >= half) return 4;
@@ -1393,6 +1395,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   cx.warp = threadIdx.x >> 5;
   cx.n = a.n;
   cx.nblk = (a.n + kBlk - 1) / kBlk;
+  cx.team_k = a.team_k;
   cx.redbuf = 0;
   if (cx.tid == 0) S = *a.st;
   __syncthreads();
