@@ -1248,10 +1248,27 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
     const U hk1 = M::sqrt_(M::rnd(ww));
     // Givens rotations (every CTA computes the same numbers)
     unsigned long long tg0 = (cx.cta == 0 && cx.tid == 0) ? gtimer() : 0;
-    if (cx.tid == 0) {
-      // the entry carried from one rotation to the next stays in a register;
+    // the entry carried from one rotation to the next stays in a register
+    U carry = (U)0;
+    if constexpr (sizeof(U) == 8) {
+      // fp64: the four products of a rotation on lanes 0-3 of warp 0 (lane
+      // q: cs x0, sn x1, -sn x0, cs x1), then lanes 0 and 2 add their pairs:
+      // two fp64 instructions on the chain per rotation instead of six
+      if (cx.warp == 0) {
+        const int q = cx.lane & 3;
+        carry = s_h[0];
+        for (int i = 0; i < k; ++i) {
+          const U cs = sm_cs[i], sn = sm_sn[i], x1 = s_h[i + 1];
+          const U ml = q == 1 ? sn : (q == 2 ? -sn : cs);
+          const U p = M::mul(ml, (q & 1) ? x1 : carry);
+          const U t = M::add(p, __shfl_down_sync(0xffffffffu, p, 1));
+          if (cx.lane == 0) s_h[i] = t;
+          carry = __shfl_sync(0xffffffffu, t, 2);
+        }
+      }
+    } else if (cx.tid == 0) {
       // the operands of four rotations are loaded ahead of their use
-      U carry = s_h[0];
+      carry = s_h[0];
       int i = 0;
       for (; i + 4 <= k; i += 4) {
         U cs[4], sn[4], x1[4];
@@ -1273,6 +1290,8 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
         s_h[i] = M::add(M::mul(sm_cs[i], x0), M::mul(sm_sn[i], x1));
         carry = M::add(M::mul(-sm_sn[i], x0), M::mul(sm_cs[i], x1));
       }
+    }
+    if (cx.tid == 0) {
       s_h[k] = carry;
       const U f = s_h[k], g = hk1;
       U c, sn, r;
@@ -1290,12 +1309,12 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
       sm_g[k] = M::mul(c, gk);
       sm_g[k + 1] = M::mul(-sn, gk);
       s_bc[0] = fabs((double)sm_g[k + 1]) / (double)beta;
-      if (cx.cta == 0) {
-        double* Hk = a.H + (size_t)k * (kcap + 1);
-        for (int i = 0; i <= k; ++i) Hk[i] = (double)s_h[i];
-      }
     }
     __syncthreads();
+    if (cx.cta == 0) {
+      double* Hk = a.H + (size_t)k * (kcap + 1);
+      for (int i = cx.tid; i <= k; i += kRefThreads) Hk[i] = (double)s_h[i];
+    }
     if (cx.cta == 0 && cx.tid == 0) cx.t_ns[6] += gtimer() - tg0;
     const double relres = s_bc[0];
     kdone = k + 1;
