@@ -228,11 +228,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const int ab = tl & 1;
       const uint32_t aph = (uint32_t)(tl >> 1) & 1u;
-      if (!mbar_wait(smem_u32(&tfull_bar[ab]), aph, &s_abort, a.err)) break;
-      tc_fence_after();
       const int tm = t % tiles_m, tn = t / tiles_m;
       const int row = tm * TC_BM + q * 32 + lane;
-#pragma unroll 1
+      // this row's C in full 32-column chunks, loaded before the
+      // accumulator is waited for (C does not depend on it), so the four
+      // chunks' loads overlap each other and the tile's MMAs
+      uint4 craw[TC_BN / 32][4];
+#pragma unroll
+      for (int cc = 0; cc < TC_BN / 32; ++cc) {
+        const int col0 = tn * TC_BN + cc * 32;
+        if (row < a.M && col0 + 32 <= a.N) {
+          const uint4* src = (const uint4*)(C + (size_t)row * a.ldc + col0);
+#pragma unroll
+          for (int v = 0; v < 4; ++v) craw[cc][v] = src[v];
+        }
+      }
+      if (!mbar_wait(smem_u32(&tfull_bar[ab]), aph, &s_abort, a.err)) break;
+      tc_fence_after();
+#pragma unroll
       for (int cc = 0; cc < TC_BN / 32; ++cc) {
         uint32_t r[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(ab * TC_BN + cc * 32), r);
@@ -242,7 +255,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           if (col0 + 32 <= a.N) {
             uint4 raw[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) raw[v] = ((const uint4*)crow)[v];
+            for (int v = 0; v < 4; ++v) raw[v] = craw[cc][v];
             F* h = (F*)raw;
 #pragma unroll
             for (int e = 0; e < 32; ++e)
