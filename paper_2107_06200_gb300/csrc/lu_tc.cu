@@ -135,6 +135,22 @@ template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(floa
   return __float2bfloat16_rn(v);
 }
 
+// One epilogue row's C in full 32-column chunks of tile column tn (the
+// chunks that reach past N are left alone; the epilogue reads them itself).
+template <typename F>
+__device__ __forceinline__ void load_c_row(const F* C, int ldc, int M, int N, int row, int tn,
+                                           uint4 (&dst)[TC_BN / 32][4]) {
+#pragma unroll
+  for (int cc = 0; cc < TC_BN / 32; ++cc) {
+    const int col0 = tn * TC_BN + cc * 32;
+    if (row < M && col0 + 32 <= N) {
+      const uint4* src = (const uint4*)(C + (size_t)row * ldc + col0);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) dst[cc][v] = src[v];
+    }
+  }
+}
+
 template <typename F>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     lu_update_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -225,24 +241,27 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const int q = warp & 3;  // TMEM lane quarter this warp may access
     F* C = (F*)a.C;
     int tl = 0;
+    // this row's C is loaded one tile ahead (C does not depend on the
+    // accumulator, and tiles' C regions are disjoint): the loads of the
+    // next tile are in flight while this one waits for its accumulator and
+    // is written back
+    uint4 cnext[TC_BN / 32][4];
+    if ((int)blockIdx.x < ntiles)
+      load_c_row<F>(C, a.ldc, a.M, a.N, ((int)blockIdx.x % tiles_m) * TC_BM + q * 32 + lane,
+                    (int)blockIdx.x / tiles_m, cnext);
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++tl) {
       const int ab = tl & 1;
       const uint32_t aph = (uint32_t)(tl >> 1) & 1u;
       const int tm = t % tiles_m, tn = t / tiles_m;
       const int row = tm * TC_BM + q * 32 + lane;
-      // this row's C in full 32-column chunks, loaded before the
-      // accumulator is waited for (C does not depend on it), so the four
-      // chunks' loads overlap each other and the tile's MMAs
       uint4 craw[TC_BN / 32][4];
 #pragma unroll
-      for (int cc = 0; cc < TC_BN / 32; ++cc) {
-        const int col0 = tn * TC_BN + cc * 32;
-        if (row < a.M && col0 + 32 <= a.N) {
-          const uint4* src = (const uint4*)(C + (size_t)row * a.ldc + col0);
+      for (int cc = 0; cc < TC_BN / 32; ++cc)
 #pragma unroll
-          for (int v = 0; v < 4; ++v) craw[cc][v] = src[v];
-        }
-      }
+        for (int v = 0; v < 4; ++v) craw[cc][v] = cnext[cc][v];
+      const int t2 = t + (int)gridDim.x;
+      if (t2 < ntiles)
+        load_c_row<F>(C, a.ldc, a.M, a.N, (t2 % tiles_m) * TC_BM + q * 32 + lane, t2 / tiles_m, cnext);
       if (!mbar_wait(smem_u32(&tfull_bar[ab]), aph, &s_abort, a.err)) break;
       tc_fence_after();
 #pragma unroll
