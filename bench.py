@@ -176,6 +176,12 @@ def refine_bytes(rep, n):
     return tot
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per refinement
+# launch, from one ncu capture of this bench's launch list (104 refinement
+# launches of four steps, serialised by the profiler), taken with the
+# refinement kernel as it stands; None once that kernel changes.
+REFINE_DRAM_BYTES_PER_LAUNCH = 2.430e9
+
 # fp64 pipe: 2 FMA lanes per SM per clock (the nominal 1.25 TFLOP/s over
 # 152 SMs at 2070 MHz), an FMA counted as 2 flops
 FP64_FMA_LANES_PER_SM = 2
@@ -226,7 +232,8 @@ def roofline_line(ref_bytes, ref_fp64, hbm_ach, fp64_ach, hbm_pk, hbm_kind, fp64
     fp64 = {"achieved": fp64_ach, "peak": fp64_pk, "unit": "TFLOP/s", "frac": fp64_ach / fp64_pk,
             "peak_source": "derived: 2 fp64 FMA lanes/SM/clock x 152 SMs x 2070 MHz", "model_s": t_fp64}
     top = ({"bound": "alu", "pipe": "fp64"} | fp64) if t_fp64 > t_hbm else ({"bound": "hbm"} | hbm)
-    top.update({"kernel": "refine_kernel (persistent refinement)", "traffic": None,
+    top.update({"kernel": "refine_kernel (persistent refinement)", "traffic": REFINE_DRAM_BYTES_PER_LAUNCH,
+                "traffic_unit": "bytes per launch (ncu, launches serialised)",
                 "concurrency": concurrency, "frac_of_gpu_share": top["frac"] * concurrency,
                 "hbm": hbm, "fp64": fp64})
     return top
