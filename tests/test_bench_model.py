@@ -50,3 +50,16 @@ def test_roofline_takes_the_larger_model_time(fp64_flops, bound):
     assert line["achieved"] == top["achieved"] and line["frac"] == pytest.approx(top["frac"])
     assert line["frac_of_gpu_share"] == pytest.approx(line["frac"] * 4.0)
     assert line["traffic"] is None or line["traffic"] > 0
+
+
+def test_refine_bytes_per_step_and_per_iteration():
+    n, k = 40, 3
+    # u = fp32 with a 16-bit factor: A_u read in fp32 (4 B), factors 2 B
+    rep = {"stages": [_st("SIR", "fp16", "fp32", "fp64", 2),
+                      _st("SGMRES-IR", "fp16", "fp32", "fp64", 1, [k])]}
+    sir = 2 * (n * n * 4 + n * n * 2)
+    gm = 1 * (n * n * 4 + n * n * 2) + sum(n * n * 4 + n * n * 2 + 4.0 * n * (j + 1) * 4 for j in range(k))
+    assert bench.refine_bytes(rep, n) == sir + gm
+    # u = fp64 (A_u in fp64), fp32 factors, dd residual
+    rep = {"stages": [_st("GMRES-IR", "fp32", "fp64", "dd", 1, [1])]}
+    assert bench.refine_bytes(rep, n) == (n * n * 8 + n * n * 4) + (n * n * 8 + n * n * 4 + 4.0 * n * 8)
