@@ -274,6 +274,20 @@ PROFILE_CASES = {
 }
 
 
+DATA = "synthetic (randsvd, geometric singular values, seeded)"
+
+
+def bench_config(world, sequential=False):
+    """The workload both arms report (the reference arm times the oracle on
+    the same configuration)."""
+    from synth import workloads
+    return {"workload": WORKLOAD, "systems": len(list(workloads(WORKLOAD))), "n": 2000, "nrhs": 1,
+            "triples": ["fp16,fp32,fp64", "fp32,fp64,dd"], "graded": "both",
+            "l2": "inputs larger than L2 (14 fp64 2000x2000 matrices per step)",
+            "parallelism": f"weak x{world}",
+            "mode": "sequential msir_solve" if sequential else "msir_solve_batched"}
+
+
 def run_profile_case(name):
     """One solve (after one warm-up solve) of a named case, untimed: the
     command that profiler captures of the kernels run."""
@@ -330,8 +344,8 @@ def main():
             "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16+f32+f64+dd", "data": "synthetic",
-            "config": {"workload": WORKLOAD},
+            "dtype": "f16+f32+f64+dd", "data": DATA,
+            "config": bench_config(args.gpus),
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -476,11 +490,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64+dd",
-            "data": "synthetic (randsvd, geometric singular values, seeded)",
-            "config": {"workload": WORKLOAD, "systems": len(systems), "n": 2000, "nrhs": 1,
-                       "triples": ["fp16,fp32,fp64", "fp32,fp64,dd"], "graded": "both",
-                       "l2": "inputs larger than L2 (14 fp64 2000x2000 matrices per step)",
-                       "parallelism": f"weak x{world}", "mode": "sequential msir_solve" if args.sequential else "msir_solve_batched"},
+            "data": DATA,
+            "config": bench_config(world, args.sequential),
             "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat)},
             "all_converged_nbe_le_2u0": nbe_ok,
             "fp64_lu": {"value": fp64_val, "unit": UNIT,
