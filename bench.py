@@ -277,6 +277,117 @@ PROFILE_CASES = {
 DATA = "synthetic (randsvd, geometric singular values, seeded)"
 
 
+# ---------------------------------------------------------------- serving
+
+def request_bytes(n):
+    """Device bytes a submitted request holds until it is done (the server
+    copies A, b and x at submission)."""
+    return 8 * n * n + 16 * n
+
+
+def run_serving(server, systems, times, picks, duration_s, byte_cap, clock=time.perf_counter,
+                sleep=time.sleep):
+    """Open-loop load: request i is submitted at times[i] (seconds from the
+    start) for pool system picks[i]; outstanding requests are polled until
+    duration_s.  An arrival whose device copy would take the outstanding
+    requests above byte_cap is rejected and counted (the client's
+    back-pressure), not submitted.
+
+    server: submit(A, b, spec) -> ticket; poll(ticket, n) -> (state, x,
+    report, latency_ms), state 2 = done.  systems: (A, b, spec) host arrays.
+    Returns one record per arrival: t (arrival), n, spec, status ('rejected',
+    'pending', 'done', 'error'), and for finished ones latency_ms (the
+    library's arrival-to-done time), cged and t_done."""
+    t0 = clock()
+    records, pending = [], {}
+    used, i = 0, 0
+    while True:
+        now = clock() - t0
+        if now >= duration_s:
+            break
+        while i < len(times) and times[i] <= now:
+            A, b, spec = systems[picks[i]]
+            n = A.shape[0]
+            rec = {"t": times[i], "n": n, "spec": spec, "status": "rejected", "latency_ms": None,
+                   "cged": None, "t_done": None}
+            need = request_bytes(n)
+            if used + need <= byte_cap:
+                pending[server.submit(A, b, spec)] = rec
+                rec["status"] = "pending"
+                used += need
+            records.append(rec)
+            i += 1
+        for tk in list(pending):
+            rec = pending[tk]
+            state, _, rep, lat = server.poll(tk, rec["n"])
+            if state == 2:
+                ok = rep is not None and rep.get("call_status", 0) >= 0
+                rec.update(status="done" if ok else "error", latency_ms=lat,
+                           cged=bool(rep["cged"]) if ok else False, t_done=clock() - t0)
+                used -= request_bytes(rec["n"])
+                del pending[tk]
+        gap = times[i] - (clock() - t0) if i < len(times) else 0.002
+        sleep(min(max(gap, 0.0), 0.002))
+    return records
+
+
+def serving_summary(records, warmup_s, duration_s):
+    """Throughput counts the solves finished inside [warmup_s, duration_s);
+    latency percentiles cover the requests that arrived in that window and
+    finished; requests still queued or running at the end are reported, not
+    dropped."""
+    window = duration_s - warmup_s
+    arrived = [r for r in records if r["t"] >= warmup_s]
+    finished = [r for r in arrived if r["status"] == "done"]
+    done_in_window = [r for r in records if r["status"] == "done" and warmup_s <= r["t_done"] < duration_s]
+    lat = sorted(r["latency_ms"] for r in finished)
+
+    def pct(q):
+        return float(np.percentile(lat, q)) if lat else None
+
+    return {"arrivals": len(arrived), "rejected": sum(r["status"] == "rejected" for r in arrived),
+            "errors": sum(r["status"] == "error" for r in arrived),
+            "unfinished": sum(r["status"] == "pending" for r in arrived),
+            "solves_per_s": len(done_in_window) / window,
+            "rate": sum(flops_equiv(r["n"]) for r in done_in_window) / window / 1e12,
+            "latency_ms": {"p50": pct(50), "p99": pct(99), "samples": len(lat)},
+            "all_converged": all(r["cged"] for r in finished)}
+
+
+def run_serve_bench(args):
+    """The serving workload: Poisson arrivals at args.rate over args.duration
+    seconds (the first args.serve_warmup untimed) from a pool of args.pool
+    pre-generated systems; one JSON line."""
+    import torch
+    import paper_2107_06200_gb300 as M
+    from synth import serving_pool, poisson_arrivals, randsvd_system
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    pool = serving_pool(args.pool, seed=0, n_lo=args.nmin, n_hi=args.nmax)
+    systems = []
+    for (n, kappa, spec, seed) in pool:
+        A, B, _ = randsvd_system(n, kappa, seed, device="cuda:0" if n > 1000 else None)
+        systems.append((np.asfortranarray(A), np.ascontiguousarray(B[:, 0]), spec))
+    times, picks = poisson_arrivals(args.rate, args.duration, len(systems), seed=0)
+    ctx = M.Context(0)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.9 * free)
+    srv = M.Server(ctx, hbm_budget_bytes=budget // 2, max_slots=args.max_slots)
+    try:
+        recs = run_serving(srv, systems, times, picks, args.duration, byte_cap=budget // 2)
+    finally:
+        srv.close()
+        ctx.close()
+    line = {"mode": "serving", "unit": UNIT, "data": DATA,
+            "config": {"workload": "serving_poisson", "rate_per_s": args.rate, "duration_s": args.duration,
+                       "warmup_s": args.serve_warmup, "pool": args.pool, "n_range": [args.nmin, args.nmax],
+                       "log10_kappa_range": [2, 10], "triples": ["fp16,fp32,fp64", "bf16,fp32,fp64", "fp32,fp64,dd"],
+                       "max_slots": args.max_slots, "hbm_budget_bytes": budget // 2,
+                       "client_byte_cap": budget // 2}}
+    line.update(serving_summary(recs, args.serve_warmup, args.duration))
+    print(json.dumps(line))
+
+
 def bench_config(world, sequential=False):
     """The workload both arms report (the reference arm times the oracle on
     the same configuration)."""
@@ -320,9 +431,21 @@ def main():
                     help="run one untimed solve of a named small case (for ncu captures) and exit")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the systems one after another with msir_solve instead of msir_solve_batched")
+    ap.add_argument("--serve", action="store_true",
+                    help="run the serving workload (Poisson arrivals into msir_server) instead of the sweep")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    ap.add_argument("--duration", type=float, default=65.0, help="serving: seconds of arrivals")
+    ap.add_argument("--serve-warmup", type=float, default=5.0, help="serving: untimed first seconds")
+    ap.add_argument("--pool", type=int, default=512, help="serving: pre-generated systems")
+    ap.add_argument("--nmin", type=int, default=256)
+    ap.add_argument("--nmax", type=int, default=8192)
+    ap.add_argument("--max-slots", type=int, default=8, help="serving: concurrent solves")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args.profile_case)
+        return
+    if args.serve:
+        run_serve_bench(args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -4,4 +4,5 @@ This package draws matrices and right-hand sides only; it contains none of
 the solver's arithmetic.  See ``synth.randsvd`` for the recipe.
 """
 
-from .randsvd import randsvd_system, batched_systems, workloads  # noqa: F401
+from .randsvd import (randsvd_system, batched_systems, workloads, serving_pool,  # noqa: F401
+                      poisson_arrivals)

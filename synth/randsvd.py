@@ -102,10 +102,47 @@ def batched_systems(count, seed=0, n_lo=32, n_hi=512, logk_lo=1.0, logk_hi=6.0):
     return [(int(n), float(k), 1000 + j) for j, (n, k) in enumerate(zip(ns, ks))]
 
 
-# Named workloads: (n, kappa, triple name, graded) lists.
 HSD = "fp16,fp32,fp64"
 BSD = "bf16,fp32,fp64"
 SDQ = "fp32,fp64,dd"
+
+
+def serving_pool(count, seed=0, n_lo=256, n_hi=8192, logk_lo=2.0, logk_hi=10.0):
+    """Sizes, condition numbers and triples of the serving workload's pool.
+
+    A generator default_rng(seed) draws, for j = 0..count-1 in turn,
+    n_j = round(exp(uniform(ln n_lo, ln n_hi))), kappa_j =
+    10^uniform(logk_lo, logk_hi) and a triple uniformly from (half, single,
+    double), (bfloat16, single, double) and (single, double, double-double);
+    system j is randsvd_system(n_j, kappa_j, seed=5000 + j)."""
+    rng = np.random.default_rng(seed)
+    triples = (HSD, BSD, SDQ)
+    out = []
+    for j in range(count):
+        n = int(round(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi)))))
+        kappa = float(10.0 ** rng.uniform(logk_lo, logk_hi))
+        out.append((n, kappa, triples[int(rng.integers(3))], 5000 + j))
+    return out
+
+
+def poisson_arrivals(rate, duration, pool_size, seed=0):
+    """Arrival times (seconds from the start) of a Poisson process of the
+    given rate over [0, duration), and for each arrival the pool index it
+    requests (uniform).  Exponential gaps and indices come from
+    default_rng(seed + 1), alternately."""
+    rng = np.random.default_rng(seed + 1)
+    times, picks = [], []
+    t = 0.0
+    while True:
+        t += float(rng.exponential(1.0 / rate))
+        if t >= duration:
+            break
+        times.append(t)
+        picks.append(int(rng.integers(pool_size)))
+    return times, picks
+
+
+# Named workloads: (n, kappa, triple name, graded) lists.
 
 
 def workloads(name):
