@@ -252,7 +252,13 @@ msir_status msir_server_create(msir_ctx* ctx, size_t hbm_budget_bytes, int max_s
                                msir_server** out);
 
 /* Queues one request.  A_host (column-major, lda) and b_host are host
- * memory, copied before the call returns.  *ticket receives an id. */
+ * memory, copied before the call returns.  *ticket receives an id.
+ * The copy is made on the device (8 n^2 + 16 n bytes, outside
+ * hbm_budget_bytes) and held while the request waits in the queue, so a
+ * caller that submits faster than the server solves bounds its own
+ * outstanding requests.  Errors: MSIR_ERR_INVALID for bad arguments,
+ * MSIR_ERR_NOMEM / MSIR_ERR_CUDA when the device copy fails (nothing is
+ * queued then). */
 msir_status msir_server_submit(msir_server* s, int n, const double* A_host, int lda,
                                const double* b_host, msir_triple t, const msir_params* params,
                                uint64_t* ticket);
