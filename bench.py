@@ -19,7 +19,6 @@ With N > 1 (torchrun) every rank solves the full sweep (weak scaling).
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys

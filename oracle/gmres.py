@@ -30,7 +30,7 @@ import math
 
 import numpy as np
 
-from .formats import FP32, FP64, DD, fl, dd, two_prod, dd_sum_pairwise, dd_to_fp64, square_of
+from .formats import FP32, DD, fl, dd, two_prod, dd_sum_pairwise, dd_to_fp64
 from . import trsv as trsv_mod
 
 

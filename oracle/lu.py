@@ -37,7 +37,7 @@ with row j at step j.
 
 import numpy as np
 
-from .formats import BF16, FP16, FP32, FP64, fl, arith_dtype
+from .formats import FP64, fl, arith_dtype
 
 
 def _argmax_abs(col):

@@ -55,8 +55,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .formats import (FP32, FP64, DD, BF16, FP16, fl, u_of, next_uf, square_of,
-                      arith_dtype)
+from .formats import FP32, FP64, fl, u_of, next_uf, square_of, arith_dtype
 from . import lu as lu_mod
 from . import trsv as trsv_mod
 from . import residual as res_mod

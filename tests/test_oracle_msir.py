@@ -1,7 +1,6 @@
 """Pins for the oracle's stage controller and whole MSIR runs (Algorithm 4)."""
 
 import math
-import os
 
 import numpy as np
 import pytest
