@@ -206,7 +206,11 @@ msir_status msir_residual(msir_ctx* ctx, int n, const double* A_dev, int lda, in
  * and the call does not wait for it.  Its only scratch is a file-scope
  * device array (about 8 KB per GPU, held until the process exits); the
  * first call on a device looks up that array's device address, so make the
- * first call on each device before any stream capture.  Calls share the
+ * first call on each device before any stream capture.  The address is kept
+ * for the life of the process: after cudaDeviceReset on a device, do not
+ * call this entry point on that device again.  If a CUDA error from earlier
+ * work is pending on the calling thread, the call returns MSIR_ERR_CUDA
+ * without launching.  Calls share the
  * scratch: calls that overlap on the GPU (different streams, or different
  * host threads on one device) race.  n must be at most 131072
  * (MSIR_ERR_INVALID otherwise).  Never allocates or frees device memory. */

@@ -26,10 +26,23 @@ arithmetic precision T and whose matrix is stored in u_f between blocks
   - the swaps are applied to the columns outside the panel;
   - U12 = L11^{-1} A12 by forward substitution in T with the stored L11,
     the same rounded product-then-difference in ascending order, stored fl_f;
-  - A22 <- fl_f(fl_T(A22 - L21 U12)) where the sum over the nb products is
-    evaluated in fp64 (for stored bf16/fp16/fp32 operands every product is
-    exact in fp64; this models an fp32 tensor-core or SIMT accumulation up
-    to fp32 rounding).  For u_f = fp64 the sum is an fp64 matrix product.
+  - the trailing columns of the outer block are updated in T: for each
+    element a fused multiply-add chain acc = fma_T(l_im, u_mj, acc) over
+    the panel's nb columns in ascending m, starting from zero, then
+    fl_f(fl_T(a_ij - acc)) (``native.chain_update``): every term rounded
+    once in T, which is what a dot product "in precision T" does.
+* After the outer block, its interchanges reach the other columns, U12 is
+  formed by the same substitution with the nbo x nbo unit lower block, and
+  the trailing matrix A22 <- A22 - L21 U12 (K = nbo) is updated
+  - for u_f = bf16 / fp16 (tensor-core update): fl_f(fl_32(A22 - S)) where
+    S is the sum of the K products evaluated in fp64 (products of stored
+    bf16/fp16 values are exact there); this models fp32 tensor-core
+    accumulation up to fp32 rounding, whose order the hardware does not fix;
+  - for u_f = fp32 / fp64: the fused multiply-add chain in T = u_f over the
+    K products in ascending order, then fl_T(A22 - acc), as above.  Sec. 3
+    simulates a precision by rounding after each operation, and an LU "in
+    single" accumulates in single; an exact sum rounded once would be a
+    more accurate factorisation than the one Algorithm 4 names.
 
 Pivots are returned LAPACK-style: ``ipiv[j]`` is the (0-based) row swapped
 with row j at step j.
@@ -37,7 +50,8 @@ with row j at step j.
 
 import numpy as np
 
-from .formats import FP64, fl, arith_dtype
+from .formats import FP64, FP16, BF16, fl, arith_dtype
+from .native import chain_update
 
 
 def _argmax_abs(col):
@@ -107,17 +121,21 @@ def _trsm(F, r0, w, c0, c1, T, fmt_f):
     F[r0:r0 + w, c0:c1] = fl(X, fmt_f).astype(np.float64)
 
 
-def _update(F, r0, w, c0, c1, fmt_f):
-    """A[r0+w:, c0:c1] <- fl_f(fl_T(A - L21 U12)), the sum over w in fp64."""
+def _update(F, r0, w, c0, c1, fmt_f, tensor_core=False):
+    """A[r0+w:, c0:c1] <- A - L21 U12, K = w (see the module docstring):
+    tensor_core (bf16/fp16 outer update): fl_f(fl_32(A - sum in fp64));
+    otherwise the fused multiply-add chain in T, then fl_f(fl_T(A - acc))."""
     if c1 <= c0 or r0 + w >= F.shape[0]:
         return
     L21 = F[r0 + w:, r0:r0 + w]
     U12 = F[r0:r0 + w, c0:c1]
-    upd = F[r0 + w:, c0:c1] - L21 @ U12
-    if fmt_f == FP64:
-        F[r0 + w:, c0:c1] = upd
+    C = F[r0 + w:, c0:c1]
+    if tensor_core:
+        upd = (C - L21 @ U12).astype(np.float32)
     else:
-        F[r0 + w:, c0:c1] = fl(upd.astype(np.float32), fmt_f).astype(np.float64)
+        T = arith_dtype(fmt_f)
+        upd = chain_update(C.astype(T), L21.astype(T), U12.astype(T))
+    F[r0 + w:, c0:c1] = fl(upd, fmt_f).astype(np.float64)
 
 
 def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None):
@@ -158,7 +176,7 @@ def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None):
             _swap_cols(F, ipiv, k, W, 0, k)
             _swap_cols(F, ipiv, k, W, k + W, n)
             _trsm(F, k, W, k + W, n, T, fmt_f)
-            _update(F, k, W, k + W, n, fmt_f)
+            _update(F, k, W, k + W, n, fmt_f, tensor_core=fmt_f in (FP16, BF16))
     return F, ipiv, info
 
 

@@ -116,6 +116,9 @@ extern "C" msir_status msir_residual_noalloc(int n, const double* A_dev, int lda
   if (n <= 0 || lda < n || !A_dev || !x_dev || !b_dev || !r_dev || !s_dev) return MSIR_ERR_INVALID;
   if (n > kNaMaxN) return MSIR_ERR_INVALID;
   if ((u0 != MSIR_FP32 && u0 != MSIR_FP64) || (ur != MSIR_FP64 && ur != MSIR_DD)) return MSIR_ERR_INVALID;
+  // an error left pending by earlier work on this thread would otherwise be
+  // read back below as this launch's failure: report it before launching
+  if (cudaPeekAtLastError() != cudaSuccess) return MSIR_ERR_CUDA;
   cudaError_t e = cudaSuccess;
   NoallocScratch* scr = scratch_for_current_device(&e);
   if (!scr) return MSIR_ERR_CUDA;
