@@ -80,6 +80,23 @@ def whole_job_rate(flops_per_rank_step, world, ms_per_step):
     return flops_per_rank_step * world / (ms_per_step * 1e-3) / 1e12
 
 
+def lpt_partition(costs, world):
+    """Longest-processing-time-first partition of independent units over
+    `world` ranks: units in decreasing cost (ties by index) each go to the
+    rank with the least load so far (ties to the lower rank).  Returns one
+    sorted index list per rank.  Every rank computes the same partition from
+    the same list, so no exchange is needed; the largest load exceeds the
+    smallest by at most the largest single cost."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return [sorted(p) for p in parts]
+
+
 def flops_equiv(n, nrhs=1):
     return 2.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs
 

@@ -277,6 +277,15 @@ msir_status msir_server_poll(msir_server* s, uint64_t ticket, int* state, double
 /* Stops the worker after the requests in flight finish; frees everything. */
 msir_status msir_server_destroy(msir_server* s);
 
+/* Measurement helper; the paper has no counterpart.  Measures the fused
+ * multiply-add throughput of device `device` in fmt (FP64 or FP32): one
+ * launch of independent fma chains over every SM (iters dependent steps
+ * per chain), timed with CUDA events.  *tflops = 2 * fmas / time / 1e12,
+ * *seconds = the launch's time.  It is the measured peak that the refinement
+ * kernel's fp64 work is compared with.  Blocks until the launch is done;
+ * allocates nothing on the device. */
+msir_status msir_probe_fma_rate(int device, int fmt, int iters, double* tflops, double* seconds);
+
 /* Short text for a status code (static storage). */
 const char* msir_status_string(int status);
 

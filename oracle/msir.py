@@ -198,8 +198,10 @@ class Controller:
         delta = s * dnorm
         with np.errstate(all="ignore"):
             z = delta / xnorm if xnorm > 0 else math.inf
-            v = delta / self.delta_prev if math.isfinite(self.delta_prev) else 0.0
-        self.rho_max = max(self.rho_max, v)
+            # IEEE division: 0/0 is NaN (two zero corrections in a row), x/0 is Inf
+            v = float(np.float64(delta) / np.float64(self.delta_prev)) if math.isfinite(self.delta_prev) else 0.0
+        # rho_max = maxNum(rho_max, v): a NaN ratio leaves it unchanged
+        self.rho_max = self.rho_max if math.isnan(v) else max(self.rho_max, v)
         phi = z / (1.0 - self.rho_max) if self.rho_max < 1.0 else math.inf
         self.phi = phi
         if self.phi0 is None:

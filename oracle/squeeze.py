@@ -13,8 +13,9 @@ it is exact unless it under- or overflows:
   mu = 2^floor(log2(theta * xmax)), theta = 0.1, xmax the largest finite
   value of u_f;
 and B = mu R A S is the matrix that is factored.  A zero row or column keeps
-a unit scaling.  The solve with the scaled factors is
-A^{-1} c = mu S B^{-1} R c.
+a unit scaling.  The solve with the scaled factors follows the cited
+method: A x = c becomes B y = mu R c with x = S y, so mu scales the
+right-hand side before the low-precision solve (x = S B^{-1} (mu R c)).
 """
 
 import math

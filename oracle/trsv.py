@@ -200,25 +200,31 @@ def upper_dd(F, c, cache=None):
 
 
 def solve_factored(fac, c, arith, store):
-    """x = mu * S * U^{-1} L^{-1} P R c with the (possibly squeezed) factors.
+    """x = S U^{-1} L^{-1} P (mu R c) with the (possibly squeezed) factors.
 
     ``fac`` is an ``msir.Factorization``; ``c`` float64 (arith FP32/FP64) or a
-    dd pair (arith DD).  The power-of-two scalings R, S, mu are exact unless
-    they under- or overflow.  Returns float64 values (or a dd pair)."""
+    dd pair (arith DD).  With squeezed factors of B = mu R A S, A x = c is
+    B y = mu R c with x = S y (the cited squeezing method's solve): mu scales
+    the right-hand side before it is rounded to the solve's storage format,
+    which keeps mu R c, and y, inside the range of bf16 / fp16 when A's
+    entries are far from 1 (R c alone would underflow there).  The
+    power-of-two scalings are exact unless they under- or overflow.  Returns
+    float64 values (or a dd pair)."""
     perm = fac.perm
     cache = fac.inv_cache
+    scale = fac.R * fac.mu if fac.R is not None else None
     if arith == DD:
-        ch = c[0] * fac.R if fac.R is not None else c[0]
-        cl = c[1] * fac.R if fac.R is not None else c[1]
+        ch = c[0] * scale if scale is not None else c[0]
+        cl = c[1] * scale if scale is not None else c[1]
         y = lower_unit_dd(fac.F, (ch[perm], cl[perm]), cache)
         x = upper_dd(fac.F, y, cache)
         if fac.S is not None:
-            x = (x[0] * fac.S * fac.mu, x[1] * fac.S * fac.mu)
+            x = (x[0] * fac.S, x[1] * fac.S)
         return x
-    cc = c * fac.R if fac.R is not None else c
+    cc = c * scale if scale is not None else c
     cc = _round(cc, store)
     y = lower_unit(fac.F, cc[perm], arith, store, cache)
     x = upper(fac.F, y, arith, store, cache)
     if fac.S is not None:
-        x = x * fac.S * fac.mu
+        x = x * fac.S
     return x

@@ -18,7 +18,7 @@ from ._lib import (BF16, FP16, FP32, FP64, DD, CONV_COMBINED, CONV_EST, ALG_NAME
 _L = _lib.load()
 
 __all__ = ["Context", "Server", "MsirError", "triple", "params_default", "report_to_dict",
-           "stage_string", "BF16", "FP16", "FP32", "FP64", "DD", "lib_path"]
+           "stage_string", "probe_fma_rate", "BF16", "FP16", "FP32", "FP64", "DD", "lib_path"]
 
 
 def lib_path():
@@ -55,6 +55,15 @@ def params_default(**kw):
             raise KeyError(k)
         setattr(p, k, v)
     return p
+
+
+def probe_fma_rate(device=0, fmt=FP64, iters=1 << 16):
+    """Measured fused multiply-add throughput (TFLOP/s, seconds) of the fp64
+    or fp32 pipe (msir_probe_fma_rate)."""
+    tf, sec = ctypes.c_double(), ctypes.c_double()
+    _check(_L.msir_probe_fma_rate(device, fmt, iters, ctypes.byref(tf), ctypes.byref(sec)),
+           "probe_fma_rate")
+    return tf.value, sec.value
 
 
 def stage_string(stages):

@@ -24,7 +24,7 @@ EXPORTED = [
     "msir_params_default", "msir_create", "msir_destroy", "msir_factor", "msir_factors_destroy",
     "msir_factors_export", "msir_factors_apply", "msir_residual", "msir_solve", "msir_solve_host",
     "msir_solve_batched", "msir_server_create", "msir_server_submit", "msir_server_poll",
-    "msir_server_destroy", "msir_status_string", "msir_residual_noalloc",
+    "msir_server_destroy", "msir_status_string", "msir_residual_noalloc", "msir_probe_fma_rate",
 ]
 
 
@@ -88,6 +88,7 @@ def load(path=LIB_PATH):
         "msir_server_destroy": [P],
         "msir_status_string": [I],
         "msir_residual_noalloc": [I, P, I, I, P, P, I, P, P, P],
+        "msir_probe_fma_rate": [I, I, I, pD, pD],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -214,6 +214,9 @@ struct Workspace {
 
 // bytes of the substitution hand-off buffer for size n (zeroed whenever the
 // substitution epoch restarts)
+// ints of one outer block's permutation map (map_pos | map_val | map_cnt)
+constexpr int kMapInts = 4 * 256 + 8;
+
 static size_t ll_bytes(int n) {
   return (size_t)4 * ((n + kBlk - 1) / kBlk) * kBlk * kLLWords * sizeof(unsigned long long);
 }
@@ -247,7 +250,7 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
     w.inv_lo[l] = ninv ? (double*)take(ninv * 8) : nullptr;
   }
   w.Ut = take((size_t)n * 256 * 2);
-  w.map = (int*)take((4 * 256 + 8) * 4);
+  w.map = (int*)take(2 * kMapInts * 4);  // two outer blocks' maps (look-ahead)
   w.iflags = (int*)take(32 * 4);
   double** vecs[] = {&w.x, &w.xn, &w.x0, &w.xbest, &w.r_hi, &w.r_lo, &w.c_hi,
                      &w.c_lo, &w.y_hi, &w.y_lo, &w.z_hi, &w.z_lo, &w.d, &w.w, &w.vk};
@@ -324,6 +327,13 @@ static bool trsv_timers_enabled();
 
 // MSIR_LU_TIMERS=1: the panel kernel accumulates section timers that the
 // factor call prints to stderr (diagnostics only).
+// MSIR_LU_LOOKAHEAD=0 turns the look-ahead off (the same arithmetic, one
+// stream; for timing comparisons).
+static bool lu_no_lookahead() {
+  const char* e = getenv("MSIR_LU_LOOKAHEAD");
+  return e && e[0] == '0';
+}
+
 static bool lu_timers_enabled() {
   static int v = -1;
   if (v < 0) {
@@ -355,10 +365,32 @@ static int panel_ctas(int m, int Rmax) {
   return std::max(1, std::min(C, 16));
 }
 
+// Streams and events of one LU: the panel of the next outer block runs on
+// `aux` (higher priority) while the current block's remaining trailing
+// update runs on the main stream (look-ahead).
+struct LuStreams {
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ready = nullptr;   // next block's columns updated (main -> aux)
+  cudaEvent_t panel = nullptr;   // next block's panel factored (aux -> main)
+};
+
 // Enqueue the LU of fl_fmt(A_u) (optionally squeezed) into level slot l.
 // The host reads info / nonfinite after the stream reaches the end.
+//
+// Right-looking blocked GEPP with a look-ahead of one outer block: for block
+// k (columns [k, k+W)), after its panel:
+//   main: interchanges + U12 + trailing update of the next block's columns
+//         [k+W, k+2W) only, then record `ready`;
+//   aux:  wait `ready`, factor the panel of block k+W, record `panel`;
+//   main: interchanges of the columns left of the block, U12 and trailing
+//         update of the columns [k+2W, n) (with SMs left free for the
+//         panel), then wait `panel` before block k+W continues.
+// The panel of block k+W reads and writes only its own columns, which the
+// rest of block k's work does not touch, so the two run concurrently; the
+// two blocks' permutation maps live in separate buffers.
 static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l, int fmt, int nb,
-                              int nbo, bool squeeze, Level& L, cudaStream_t st, int* launches) {
+                              int nbo, bool squeeze, Level& L, cudaStream_t st, const LuStreams& ls,
+                              int* launches) {
   const int ldf = w.ldu;
   L = Level();
   L.fmt = fmt;
@@ -394,58 +426,69 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
   const size_t fixed = panel_smem_bytes(fmt, 0, nb, nbo);
   const size_t budget = std::min<size_t>((size_t)ctx->max_dyn_smem, 220 * 1024);
   const int Rmax = (int)((budget - fixed) / ((size_t)(nb + 1) * ts));
-  for (int k = 0; k < n; k += nbo) {
-    const int W = std::min(nbo, n - k);
+  const bool lookahead = ls.aux != nullptr && !lu_no_lookahead();
+
+  auto panel_args = [&](int k, PanelArgs& pa, int& C) -> msir_status {
     const int m = n - k;
-    const int C = panel_ctas(m, Rmax);
+    C = panel_ctas(m, Rmax);
     if (C < 0) return MSIR_ERR_UNSUPPORTED;
-    PanelArgs pa;
+    int* map = w.map + ((k / nbo) & 1) * kMapInts;
     pa.A = L.F;
     pa.lda = ldf;
     pa.n = n;
     pa.k = k;
-    pa.W = W;
+    pa.W = std::min(nbo, n - k);
     pa.nb = nb;
     pa.R_cap = (m + C - 1) / C;
     pa.ipiv = L.ipiv;
     pa.info = w.iflags + 0;
     pa.nonfinite = w.iflags + 1;
-    pa.map_pos = w.map;
-    pa.map_val = w.map + 2 * nbo;
-    pa.map_cnt = w.map + 4 * nbo;
+    pa.map_pos = map;
+    pa.map_val = map + 2 * nbo;
+    pa.map_cnt = map + 4 * nbo;
     pa.tdbg = lu_timers_enabled() ? (unsigned long long*)(w.iflags + 8) : nullptr;
-    CK(launch_panel(fmt, pa, C, st));
+    return MSIR_OK;
+  };
+  // interchanges / U12 / update of block k on the columns [c0, c1) right of
+  // it (and the interchanges left of it if left); max_ctas limits the
+  // tensor-core update's persistent grid
+  auto block_columns = [&](int k, const PanelArgs& pa, bool left, int c0, int c1, int max_ctas,
+                           cudaStream_t s2) -> msir_status {
+    const int W = pa.W;
+    const int ncols = std::max(0, c1 - c0);
+    const int nleft = left ? k : 0;
+    if (nleft == 0 && ncols == 0) return MSIR_OK;
+    SwapTrsmArgs sa;
+    sa.A = L.F;
+    sa.lda = ldf;
+    sa.n = n;
+    sa.k = k;
+    sa.W = W;
+    sa.do_left = left ? 1 : 0;
+    sa.c_begin = c0;
+    sa.c_end = c0 + ncols;
+    sa.map_pos = pa.map_pos;
+    sa.map_val = pa.map_val;
+    sa.map_cnt = pa.map_cnt;
+    sa.Ut = (tc && ncols > 0) ? w.Ut : nullptr;
+    sa.ldut = nbo;
+    sa.nonfinite = w.iflags + 1;
+    const int tiles = (nleft + 31) / 32 + (ncols + 31) / 32;
+    CK(launch_swap_trsm(fmt, sa, std::max(1, std::min(tiles, ctx->num_sms)), s2));
     *launches += 1;
-    const int nright = n - k - W;
-    if (k > 0 || nright > 0) {
-      SwapTrsmArgs sa;
-      sa.A = L.F;
-      sa.lda = ldf;
-      sa.n = n;
-      sa.k = k;
-      sa.W = W;
-      sa.map_pos = pa.map_pos;
-      sa.map_val = pa.map_val;
-      sa.map_cnt = pa.map_cnt;
-      sa.Ut = (tc && nright > 0) ? w.Ut : nullptr;
-      sa.ldut = nbo;
-      sa.nonfinite = w.iflags + 1;
-      const int tiles = (k + 31) / 32 + (nright + 31) / 32;
-      CK(launch_swap_trsm(fmt, sa, std::max(1, std::min(tiles, ctx->num_sms)), st));
-      *launches += 1;
-    }
-    if (nright > 0) {
+    if (ncols > 0) {
       if (tc) {
         TcUpdateArgs ta;
-        ta.C = (char*)L.F + ((size_t)(k + W) * ldf + (k + W)) * 2;
+        ta.C = (char*)L.F + ((size_t)(k + W) * ldf + c0) * 2;
         ta.ldc = ldf;
-        ta.M = nright;
-        ta.N = nright;
+        ta.M = n - k - W;
+        ta.N = ncols;
         ta.a_row0 = k + W;
         ta.a_col0 = k;
+        ta.b_row0 = c0 - (k + W);
         ta.K = W;
         ta.err = w.iflags + 2;
-        CK(launch_update_tc(fmt, &tmA, &tmB, ta, ctx->num_sms, st));
+        CK(launch_update_tc(fmt, &tmA, &tmB, ta, max_ctas, s2));
         *launches += 1;
       } else {
         UpdateArgs ua;
@@ -454,10 +497,51 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
         ua.n = n;
         ua.k = k;
         ua.W = W;
-        CK(launch_update_simt(fmt, ua, st));
+        ua.c_begin = c0;
+        ua.c_end = c0 + ncols;
+        CK(launch_update_simt(fmt, ua, s2));
         *launches += 1;
       }
     }
+    return MSIR_OK;
+  };
+
+  PanelArgs pa;
+  int C = 0;
+  msir_status r = panel_args(0, pa, C);
+  if (r != MSIR_OK) return r;
+  CK(launch_panel(fmt, pa, C, st));
+  *launches += 1;
+  for (int k = 0; k < n; k += nbo) {
+    const int W = pa.W;
+    const int knext = k + W;
+    if (!lookahead || knext >= n) {
+      r = block_columns(k, pa, true, knext, n, ctx->num_sms, st);
+      if (r != MSIR_OK) return r;
+      if (knext >= n) break;
+      r = panel_args(knext, pa, C);
+      if (r != MSIR_OK) return r;
+      CK(launch_panel(fmt, pa, C, st));
+      *launches += 1;
+      continue;
+    }
+    const int la_end = std::min(n, knext + nbo);
+    r = block_columns(k, pa, false, knext, la_end, ctx->num_sms, st);
+    if (r != MSIR_OK) return r;
+    CK(cudaEventRecord(ls.ready, st));
+    PanelArgs pn;
+    int Cn = 0;
+    r = panel_args(knext, pn, Cn);
+    if (r != MSIR_OK) return r;
+    CK(cudaStreamWaitEvent(ls.aux, ls.ready, 0));
+    CK(launch_panel(fmt, pn, Cn, ls.aux));
+    *launches += 1;
+    CK(cudaEventRecord(ls.panel, ls.aux));
+    r = block_columns(k, pa, true, la_end, n, std::max(1, ctx->num_sms - Cn), st);
+    if (r != MSIR_OK) return r;
+    CK(cudaStreamWaitEvent(st, ls.panel, 0));
+    pa = pn;
+    C = Cn;
   }
   CK(ipiv_to_perm(L.ipiv, n, L.perm, st));
   *launches += 1;
@@ -492,6 +576,7 @@ enum SlotStep { S_IDLE, S_FACTOR, S_REFINE, S_FINISH };
 
 struct Slot {
   cudaStream_t st = nullptr;
+  LuStreams lu;               // look-ahead stream and events of the LU
   Workspace w;
   int m_serial = -1;          // factorisation whose scaled blocks the workspace holds
   Job* job = nullptr;
@@ -525,6 +610,11 @@ static int level_index(int fmt) {
 static msir_status slot_init(Slot& s, int device) {
   CK(cudaSetDevice(device));
   CK(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
+  int lo_prio = 0, hi_prio = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio));
+  CK(cudaStreamCreateWithPriority(&s.lu.aux, cudaStreamNonBlocking, hi_prio));
+  CK(cudaEventCreateWithFlags(&s.lu.ready, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&s.lu.panel, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming));
   CK(cudaEventCreate(&s.e0));
   CK(cudaEventCreate(&s.e1));
@@ -541,6 +631,12 @@ static void slot_destroy(Slot& s) {
     cudaStreamSynchronize(s.st);
     cudaStreamDestroy(s.st);
   }
+  if (s.lu.aux) {
+    cudaStreamSynchronize(s.lu.aux);
+    cudaStreamDestroy(s.lu.aux);
+  }
+  if (s.lu.ready) cudaEventDestroy(s.lu.ready);
+  if (s.lu.panel) cudaEventDestroy(s.lu.panel);
   if (s.ev) cudaEventDestroy(s.ev);
   if (s.e0) cudaEventDestroy(s.e0);
   if (s.e1) cudaEventDestroy(s.e1);
@@ -695,7 +791,7 @@ static msir_status slot_enqueue_factor(msir_ctx* ctx, Slot& s, int fmt, bool squ
   s.nfact += squeeze ? 0 : 1;
   CK(cudaEventRecord(s.e0, s.st));
   msir_status r = enqueue_lu(ctx, s.w, j.n, s.u0, s.try_level, fmt, nb, nbo, squeeze, s.lv[s.try_level], s.st,
-                             &s.launches);
+                             s.lu, &s.launches);
   if (r != MSIR_OK) return r;
   CK(cudaMemcpyAsync(s.h_flags, s.w.iflags, 16 * sizeof(int), cudaMemcpyDeviceToHost, s.st));
   CK(cudaEventRecord(s.e1, s.st));

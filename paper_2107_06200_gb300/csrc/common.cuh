@@ -112,6 +112,46 @@ __device__ __forceinline__ dd_t two_prod(double a, double b) {
   double e = __fma_rn(a, b, -p);
   return {p, e};
 }
+// The same error-free transformations in fp32, for the compensated fp32
+// sums (Ogita, Rump and Oishi's Dot2): a running sum s and the sum c of the
+// exact rounding errors of every product and addition; fl(s + c) is the
+// accurately rounded sum except within about n u^2 of a rounding boundary.
+struct ff_t {
+  float s, c;
+};
+// FastTwoSum with the operands ordered by magnitude on their bit patterns
+// (exact sum and error, as Knuth's TwoSum gives them).
+__device__ __forceinline__ void two_sum_ord_f(float a, float b, float& s, float& e) {
+  const unsigned ia = __float_as_uint(a) & 0x7fffffffu, ib = __float_as_uint(b) & 0x7fffffffu;
+  const bool ab = ia >= ib;
+  const float x = ab ? a : b, y = ab ? b : a;
+  s = __fadd_rn(x, y);
+  e = __fsub_rn(y, __fsub_rn(s, x));
+}
+// acc + x*y with the product's and the sum's rounding errors kept in acc.c
+__device__ __forceinline__ ff_t ff_fma(float x, float y, ff_t acc) {
+  const float p = __fmul_rn(x, y);
+  const float pe = __fmaf_rn(x, y, -p);
+  float s, e;
+  two_sum_ord_f(acc.s, p, s, e);
+  return ff_t{s, __fadd_rn(acc.c, __fadd_rn(e, pe))};
+}
+__device__ __forceinline__ ff_t ff_merge(ff_t a, ff_t b) {
+  float s, e;
+  two_sum_ord_f(a.s, b.s, s, e);
+  return ff_t{s, __fadd_rn(__fadd_rn(a.c, b.c), e)};
+}
+__device__ __forceinline__ float ff_fin(ff_t a) { return __fadd_rn(a.s, a.c); }
+// fl(w - (a.s + a.c)): the difference w - a.s is formed exactly first
+__device__ __forceinline__ float ff_sub_from(float w, ff_t a) {
+  float s, e;
+  two_sum_ord_f(w, -a.s, s, e);
+  return __fadd_rn(s, __fsub_rn(e, a.c));
+}
+__device__ __forceinline__ ff_t ff_shfl_xor(ff_t a, int m) {
+  return ff_t{__shfl_xor_sync(0xffffffffu, a.s, m), __shfl_xor_sync(0xffffffffu, a.c, m)};
+}
+
 __device__ __forceinline__ dd_t dd_add(dd_t a, dd_t b) {
   dd_t s = two_sum(a.hi, b.hi);
   dd_t t = two_sum(a.lo, b.lo);

@@ -24,9 +24,12 @@ struct PanelArgs {
 
 // lu_outer_swap_trsm: interchanges of the outer block on the other columns,
 // U12 = L11^{-1} A12, and (if Ut) U12^T into Ut (ldut per output column).
+// Columns handled: [0, k) if do_left, and [c_begin, c_end) of the columns
+// right of the block (k + W <= c_begin).
 struct SwapTrsmArgs {
   void* A;
   int lda, n, k, W;
+  int do_left, c_begin, c_end;
   const int* map_pos;
   const int* map_val;
   const int* map_cnt;
@@ -35,10 +38,12 @@ struct SwapTrsmArgs {
   int* nonfinite;
 };
 
-// A22 <- fl(A22 - L21 U12) with K = W.
+// A22 <- fl(A22 - L21 U12) with K = W, for the trailing columns
+// [c_begin, c_end) (k + W <= c_begin) and every row below the block.
 struct UpdateArgs {
   void* A;
   int lda, n, k, W;
+  int c_begin, c_end;
 };
 
 size_t panel_smem_bytes(int fmt, int R_cap, int nb, int W);
@@ -50,15 +55,17 @@ cudaError_t launch_update_simt(int fmt, const UpdateArgs& a, cudaStream_t st);
 // tcgen05 trailing update for bf16/fp16 factors (lu_tc.cu).  tmA / tmB are
 // CUtensorMap objects (128-byte blobs) for the matrix and for U12^T.
 struct TcUpdateArgs {
-  void* C;        // &A[k+W][k+W]
+  void* C;        // &A[k+W][c_begin]
   int ldc;
-  int M, N;       // trailing size (rows, cols)
+  int M, N;       // rows, columns updated
   int a_row0, a_col0;  // TMA coordinates of L21 in the matrix map
+  int b_row0;     // row of U12^T (in its map) of the first updated column
   int K;          // W (multiple of 64)
   int* err;
 };
+// max_ctas: persistent grid limit (SMs left free for a concurrent panel).
 cudaError_t launch_update_tc(int fmt, const void* tmA, const void* tmB, const TcUpdateArgs& a,
-                             int num_sms, cudaStream_t st);
+                             int max_ctas, cudaStream_t st);
 
 // Inverses of the 64x64 diagonal blocks of L and U (inv.cu): outputs are
 // [2][ceil(n/64)][64][64] (triangle 0 = L, 1 = U).

@@ -478,9 +478,9 @@ __global__ void __launch_bounds__(256) lu_outer_swap_trsm(SwapTrsmArgs a) {
   F* A = (F*)a.A;
   const int lda = a.lda, n = a.n, k = a.k, W = a.W;
   const int cnt = *a.map_cnt;
-  const int nleft = k, nright = n - k - W;
+  const int nleft = a.do_left ? k : 0, nright = a.c_end - a.c_begin;
   const int tiles_left = (nleft + 31) / 32;
-  const int tiles_right = (nright + 31) / 32;
+  const int tiles_right = nright > 0 ? (nright + 31) / 32 : 0;
   const int tid = threadIdx.x;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -508,8 +508,8 @@ __global__ void __launch_bounds__(256) lu_outer_swap_trsm(SwapTrsmArgs a) {
 
   for (int t = blockIdx.x; t < tiles_left + tiles_right; t += gridDim.x) {
     const bool right = t >= tiles_left;
-    const int c0 = right ? k + W + (t - tiles_left) * 32 : t * 32;
-    const int cend = right ? n : k;
+    const int c0 = right ? a.c_begin + (t - tiles_left) * 32 : t * 32;
+    const int cend = right ? a.c_end : k;
     // gather sources
     for (int idx = tid; idx < cnt * 32; idx += blockDim.x) {
       const int s = idx / 32, cc = idx % 32, c = c0 + cc;
@@ -564,6 +564,7 @@ __global__ void __launch_bounds__(256) lu_update_simt(UpdateArgs a) {
   F* A = (F*)a.A;
   const int lda = a.lda, k = a.k, W = a.W;
   const int r0 = k + W, M = a.n - r0;
+  const int c0 = a.c_begin, NC = a.c_end - a.c_begin;
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN];
@@ -584,7 +585,7 @@ __global__ void __launch_bounds__(256) lu_update_simt(UpdateArgs a) {
     for (int idx = tid; idx < BK * BN; idx += 256) {
       const int kq = idx / BN, j = idx % BN;
       const int col = tn + j, kk = kc + kq;
-      Bs[kq][j] = (col < M && kk < W) ? (T)to_f(A[(size_t)(k + kk) * lda + r0 + col]) : (T)0;
+      Bs[kq][j] = (col < NC && kk < W) ? (T)to_f(A[(size_t)(k + kk) * lda + c0 + col]) : (T)0;
     }
     __syncthreads();
 #pragma unroll
@@ -608,8 +609,8 @@ __global__ void __launch_bounds__(256) lu_update_simt(UpdateArgs a) {
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int col = tn + tx * 4 + j;
-      if (col >= M) continue;
-      F* p = A + (size_t)(r0 + row) * lda + r0 + col;
+      if (col >= NC) continue;
+      F* p = A + (size_t)(r0 + row) * lda + c0 + col;
       *p = store_rn<F>(sub_rn((T)to_f(*p), acc[i][j]));
     }
   }
@@ -691,9 +692,9 @@ cudaError_t launch_swap_trsm(int fmt, const SwapTrsmArgs& a, int grid, cudaStrea
 }
 
 cudaError_t launch_update_simt(int fmt, const UpdateArgs& a, cudaStream_t st) {
-  const int M = a.n - a.k - a.W;
-  if (M <= 0) return cudaSuccess;
-  dim3 grid((M + 63) / 64, (M + 63) / 64);
+  const int M = a.n - a.k - a.W, NC = a.c_end - a.c_begin;
+  if (M <= 0 || NC <= 0) return cudaSuccess;
+  dim3 grid((NC + 63) / 64, (M + 63) / 64);
   switch (fmt) {
     case MSIR_FP16: lu_update_simt<__half><<<grid, 256, 0, st>>>(a); break;
     case MSIR_BF16: lu_update_simt<__nv_bfloat16><<<grid, 256, 0, st>>>(a); break;

@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         mbar_expect_tx(fb, TC_STAGE_BYTES);
         const uint32_t sa = base + s * TC_STAGE_BYTES;
         tma_load_2d(sa, &tmA, a.a_col0 + kc * TC_BK, a.a_row0 + tm * TC_BM, fb);
-        tma_load_2d(sa + TC_A_BYTES, &tmB, kc * TC_BK, tn * TC_BN, fb);
+        tma_load_2d(sa + TC_A_BYTES, &tmB, kc * TC_BK, a.b_row0 + tn * TC_BN, fb);
         if (++s == TC_STAGES) { s = 0; ph ^= 1u; }
       }
     }
@@ -303,11 +303,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 cudaError_t launch_update_tc(int fmt, const void* tmA, const void* tmB, const TcUpdateArgs& a,
-                             int num_sms, cudaStream_t st) {
+                             int max_ctas, cudaStream_t st) {
   if (a.M <= 0 || a.N <= 0) return cudaSuccess;
-  if (a.K % TC_BK) return cudaErrorInvalidValue;
+  if (a.K % TC_BK || max_ctas < 1) return cudaErrorInvalidValue;
   const int ntiles = ((a.M + TC_BM - 1) / TC_BM) * ((a.N + TC_BN - 1) / TC_BN);
-  const int grid = ntiles < num_sms ? ntiles : num_sms;
+  const int grid = ntiles < max_ctas ? ntiles : max_ctas;
   const size_t smem = (size_t)TC_STAGES * TC_STAGE_BYTES + 1024;
   CUtensorMap A, B;
   memcpy(&A, tmA, sizeof(CUtensorMap));

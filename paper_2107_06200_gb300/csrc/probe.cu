@@ -1,0 +1,80 @@
+// Throughput probe of the fp64 and fp32 fused multiply-add pipes.
+//
+// Measurement helper only (the paper has no counterpart): the refinement
+// kernel's residual, u^2 operator and double-double arithmetic run on the
+// fp64 pipe, and its roofline needs that pipe's peak as measured on this
+// device rather than a nominal figure.  Every thread runs kChains
+// independent dependent chains of a = fma(a, m, c) (kChains-way
+// instruction-level parallelism hides the pipe latency); the grid fills every
+// SM several times over.  Work per launch = 2 flops x threads x kChains x
+// iters; time = CUDA events around the launch on the caller's stream.
+#include <cuda_runtime.h>
+
+#include "../../include/msir.h"
+
+namespace {
+
+constexpr int kChains = 8;
+constexpr int kProbeThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kProbeThreads) fma_probe_kernel(T* sink, int iters, T m, T c) {
+  T a[kChains];
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) a[k] = (T)(threadIdx.x + k + 1) * (T)1e-3;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < kChains; ++k) a[k] = fma(a[k], m, c);
+  }
+  T s = 0;
+#pragma unroll
+  for (int k = 0; k < kChains; ++k) s += a[k];
+  // never true for the values used (keeps the chains live without a store)
+  if (s == (T)-1.2345) sink[blockIdx.x] = s;
+}
+
+template <typename T>
+msir_status run_probe(int device, int iters, double* tflops, double* seconds) {
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return MSIR_ERR_CUDA;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+    return MSIR_ERR_CUDA;
+  const int blocks = sms * 8;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return MSIR_ERR_CUDA;
+  msir_status out = MSIR_OK;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    out = MSIR_ERR_CUDA;
+  } else {
+    const T m = (T)0.999999, c = (T)1e-7;
+    fma_probe_kernel<T><<<blocks, kProbeThreads, 0, st>>>(nullptr, iters / 8 + 1, m, c);  // warm-up
+    cudaEventRecord(e0, st);
+    fma_probe_kernel<T><<<blocks, kProbeThreads, 0, st>>>(nullptr, iters, m, c);
+    cudaEventRecord(e1, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      out = MSIR_ERR_CUDA;
+    } else {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const double flops = 2.0 * (double)blocks * kProbeThreads * kChains * (double)iters;
+      *seconds = ms * 1e-3;
+      *tflops = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaStreamDestroy(st);
+  return out;
+}
+
+}  // namespace
+
+extern "C" msir_status msir_probe_fma_rate(int device, int fmt, int iters, double* tflops,
+                                           double* seconds) {
+  if (!tflops || !seconds || iters <= 0) return MSIR_ERR_INVALID;
+  if (fmt == MSIR_FP64) return run_probe<double>(device, iters, tflops, seconds);
+  if (fmt == MSIR_FP32) return run_probe<float>(device, iters, tflops, seconds);
+  return MSIR_ERR_INVALID;
+}

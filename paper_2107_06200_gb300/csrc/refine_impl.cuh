@@ -345,13 +345,18 @@ __device__ __forceinline__ void load_seg(const F* LU, int ldf, int n, int row, i
 
 // Accumulator policies.  V: value type of the solve; A: running sum of
 // products (fin() turns it into a V); L: factor element after widening;
-// I: inverse element; kW: 32-bit payload words per value.
+// I: inverse element; kW: 32-bit payload words per value.  wsub(w, acc) is
+// T(w - sum), the block's result before it is rounded to its storage format.
 // Vectors live in double arrays (fp32 solves store floats in them, so that
 // they never touch the scarce fp64 pipe; dd solves use a high and a low
 // array).
+// fp32 sums are compensated (ff_t, Dot2): their result is the accurately
+// rounded fp32 value of the sum, which is the model of an fp32 sum that the
+// solves follow (an accurate sum rounded once to the arithmetic precision),
+// at a few fp32 instructions per term instead of fp64 work.
 struct AccF {
   using V = float;
-  using A = float;
+  using A = ff_t;
   using L = float;
   using I = float;
   static constexpr int kW = 1;
@@ -366,12 +371,13 @@ struct AccF {
   static __device__ __forceinline__ double get(const double* hi, const double*, int i) {
     return (double)((const float*)hi)[i];
   }
-  static __device__ __forceinline__ A azero() { return 0.0f; }
-  static __device__ __forceinline__ A merge(A a, A b) { return __fadd_rn(a, b); }
-  static __device__ __forceinline__ A ax(A a, int m) { return __shfl_xor_sync(0xffffffffu, a, m); }
-  static __device__ __forceinline__ A fma(L l, V y, A acc) { return __fmaf_rn(l, y, acc); }
-  static __device__ __forceinline__ A ifma(I x, V z, A acc) { return __fmaf_rn(x, z, acc); }
-  static __device__ __forceinline__ V fin(A acc) { return acc; }
+  static __device__ __forceinline__ A azero() { return ff_t{0.0f, 0.0f}; }
+  static __device__ __forceinline__ A merge(A a, A b) { return ff_merge(a, b); }
+  static __device__ __forceinline__ A ax(A a, int m) { return ff_shfl_xor(a, m); }
+  static __device__ __forceinline__ A fma(L l, V y, A acc) { return ff_fma(l, y, acc); }
+  static __device__ __forceinline__ A ifma(I x, V z, A acc) { return ff_fma(x, z, acc); }
+  static __device__ __forceinline__ V fin(A acc) { return ff_fin(acc); }
+  static __device__ __forceinline__ V wsub(V w, A acc) { return ff_sub_from(w, acc); }
   static __device__ __forceinline__ V add(V a, V b) { return __fadd_rn(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return __fsub_rn(a, b); }
   static __device__ __forceinline__ V store(V v, int fmt) { return round_f(v, fmt); }
@@ -383,7 +389,7 @@ struct AccF {
   static __device__ __forceinline__ void tile(const RefineArgs& a, int n, int row, int col, Tm (&v)[N]) {
     load_seg<float, float, N>(a.M32, a.ldf, n, row, col, v);
   }
-  static __device__ __forceinline__ A tfma(Tm m, V y, A acc) { return __fmaf_rn(m, y, acc); }
+  static __device__ __forceinline__ A tfma(Tm m, V y, A acc) { return ff_fma(m, y, acc); }
   static __device__ __forceinline__ unsigned word(V v, int) { return __float_as_uint(v); }
   static __device__ __forceinline__ V unword(const unsigned* w) { return __uint_as_float(w[0]); }
 };
@@ -404,6 +410,7 @@ struct AccD {
   static __device__ __forceinline__ A fma(L l, V y, A acc) { return __fma_rn(l, y, acc); }
   static __device__ __forceinline__ A ifma(I x, V z, A acc) { return __fma_rn(x, z, acc); }
   static __device__ __forceinline__ V fin(A acc) { return acc; }
+  static __device__ __forceinline__ V wsub(V w, A acc) { return __dsub_rn(w, acc); }
   static __device__ __forceinline__ V add(V a, V b) { return __dadd_rn(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return __dsub_rn(a, b); }
   static __device__ __forceinline__ V store(V v, int) { return v; }
@@ -474,6 +481,7 @@ struct AccDD {
     return DDAcc{t.hi, __dadd_rn(acc.c, __dadd_rn(t.lo, pl))};
   }
   static __device__ __forceinline__ V fin(A acc) { return two_sum(acc.s, acc.c); }
+  static __device__ __forceinline__ V wsub(V w, A acc) { return dd_sub(w, fin(acc)); }
   static __device__ __forceinline__ V add(V a, V b) { return dd_add(a, b); }
   static __device__ __forceinline__ V sub(V a, V b) { return dd_sub(a, b); }
   static __device__ __forceinline__ V store(V v, int) { return v; }
@@ -806,7 +814,7 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
       // the TPR segments of the row: s_r, then y_r = S(T(w_r - s_r))
 #pragma unroll
       for (int m = 1; m < TPR; m <<= 1) acc = ACC::merge(acc, ACC::ax(acc, m));
-      V y = ACC::store(ACC::sub(wr, ACC::fin(acc)), store_fmt);
+      V y = ACC::store(ACC::wsub(wr, acc), store_fmt);
       if (rr >= nr) y = ACC::zero();
       // publish: segment k writes payload word k of the row (rows past n as 0)
       if (seg < W)
@@ -897,11 +905,15 @@ __device__ __forceinline__ double get_z(const RefineArgs& a, int arith, int i) {
   for (int _b = (cx).cta; _b < (cx).nblk; _b += (cx).G)                               \
     for (int i = _b * kBlk + (cx).tid; i < min((_b + 1) * kBlk, (cx).n); i += kRefThreads)
 
+// Squeezed factors of B = mu R A S (Sec. 2.1.2's cited scaling): A x = c is
+// solved as B y = mu R c, x = S y; mu scales the right-hand side before it
+// is rounded to the solve's storage format, which keeps it (and y) inside
+// the bf16 / fp16 range when A's entries are far from 1.
 static __device__ __forceinline__ double rscale(const RefineArgs& a, int row) {
-  return a.Rsc ? a.Rsc[row] : 1.0;
+  return a.Rsc ? a.Rsc[row] * a.mu : 1.0;
 }
 static __device__ __forceinline__ double cscale(const RefineArgs& a, int col) {
-  return a.Ssc ? a.Ssc[col] * a.mu : 1.0;
+  return a.Ssc ? a.Ssc[col] : 1.0;
 }
 
 // ------------------------------------------------------------ residual
@@ -984,9 +996,10 @@ template <> struct UA<double> {
 };
 
 // Operator t = A v (rows perm[i]) in the operator precision, scaled by R,
-// placed in c.  op = FP32: fp32 accumulation, rows of my blocks (no barrier
-// needed before the substitution); FP64 / DD: rows over every warp of the
-// grid, followed by a grid barrier.
+// placed in c.  op = FP32: compensated fp32 sums (the accurately rounded
+// fp32 value of each row's sum), rows of my blocks (no barrier needed before
+// the substitution); FP64 / DD: rows over every warp of the grid, followed
+// by a grid barrier.
 template <typename A0, typename U>
 __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
   PhaseTimer pt(cx, 4);
@@ -998,12 +1011,12 @@ __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
       const int i0 = b * kBlk + cx.warp * 8;
       if (i0 >= cx.n) continue;
       const A0* rows[8];
-      float acc[8];
+      ff_t acc[8];
 #pragma unroll
       for (int rr = 0; rr < 8; ++rr) {
         const int i = min(i0 + rr, cx.n - 1);  // rows past n repeat the last one, never stored
         rows[rr] = A + (size_t)a.perm[i] * a.lda;
-        acc[rr] = 0.0f;
+        acc[rr] = ff_t{0.0f, 0.0f};
       }
       // four consecutive columns per lane and step, 16-byte loads
       const int n4 = ((reinterpret_cast<uintptr_t>(v) & 15) == 0) ? (cx.n & ~3) : 0;
@@ -1016,23 +1029,25 @@ __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
           float av[4];
           ld4f_row<A0>(rows[rr] + j, av);
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[rr] = __fmaf_rn(av[q], vv[q], acc[rr]);
+          for (int q = 0; q < 4; ++q) acc[rr] = ff_fma(av[q], vv[q], acc[rr]);
         }
       }
       for (int j = n4 + cx.lane; j < cx.n; j += 32) {
         const float vj = (float)__ldcg(v + j);
 #pragma unroll
-        for (int rr = 0; rr < 8; ++rr) acc[rr] = __fmaf_rn((float)__ldg(rows[rr] + j), vj, acc[rr]);
+        for (int rr = 0; rr < 8; ++rr) acc[rr] = ff_fma((float)__ldg(rows[rr] + j), vj, acc[rr]);
       }
 #pragma unroll
-      for (int rr = 0; rr < 8; ++rr) acc[rr] = warp_sum_f(acc[rr]);
+      for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+        for (int m = 16; m > 0; m >>= 1) acc[rr] = ff_merge(acc[rr], ff_shfl_xor(acc[rr], m));
       if (cx.lane < 8 && i0 + cx.lane < cx.n) {
-        float mine = acc[0];
+        float mine = ff_fin(acc[0]);
 #pragma unroll
         for (int rr = 1; rr < 8; ++rr)
-          if (cx.lane == rr) mine = acc[rr];
+          if (cx.lane == rr) mine = ff_fin(acc[rr]);
         const int ar = a.perm[i0 + cx.lane];
-        const float R = a.Rsc ? (float)a.Rsc[ar] : 1.0f;
+        const float R = (float)rscale(a, ar);
         ((float*)a.c_hi)[i0 + cx.lane] = __fmul_rn(mine, R);
       }
     }

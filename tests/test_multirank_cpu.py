@@ -54,3 +54,53 @@ def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(12.5, 1) == 12.5
     assert bench.whole_job_rate(1e12, 1, 1000.0) == pytest.approx(1.0)
+
+
+def _lpt_rank(rank, world, port, costs, q):
+    import torch.distributed as dist
+    import bench
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        mine = bench.lpt_partition(costs, world)[rank]   # computed locally, no exchange
+        got = [None] * world
+        dist.all_gather_object(got, mine)                # the test's check only
+        q.put((rank, mine, got))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_lpt_partition_two_gloo_ranks_solve_every_system_once():
+    """The batched workload's systems (n uniform in [32, 512]) sharded by LPT
+    on n^3 over two ranks: each rank derives its share alone, the shares are
+    disjoint and cover every system, and the loads differ by at most the
+    largest single system."""
+    from synth import batched_systems
+    systems = batched_systems(512, seed=0)
+    costs = [float(n) ** 3 for (n, _, _) in systems]
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_lpt_rank, args=(r, 2, port, costs, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    shares = [r[1] for r in res]
+    assert res[0][2] == res[1][2] == shares            # both ranks agree on the partition
+    flat = sorted(i for sh in shares for i in sh)
+    assert flat == list(range(len(systems)))           # every system exactly once
+    loads = [sum(costs[i] for i in sh) for sh in shares]
+    assert abs(loads[0] - loads[1]) <= max(costs)
+
+
+def test_lpt_partition_properties():
+    import bench
+    assert bench.lpt_partition([5.0, 1.0, 4.0, 3.0, 3.0], 2) == [[0, 4], [1, 2, 3]]
+    assert bench.lpt_partition([1.0, 2.0], 1) == [[0, 1]]
+    assert bench.lpt_partition([], 3) == [[], [], []]
+    parts = bench.lpt_partition([7.0] * 9, 4)
+    assert sorted(len(p) for p in parts) == [2, 2, 2, 3]

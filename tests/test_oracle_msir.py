@@ -186,3 +186,52 @@ def test_zero_rhs_and_exact_start():
     assert res.cged and np.all(res.x == 0)
     res = M.msir(A, np.ones(5), HSD)  # x0 = 0.5 exactly: residual 0
     assert res.cged and np.all(res.x == 0.5)
+
+
+def test_factor_check_retries_with_squeezing():
+    """Sec. 2.1.2: a half-precision LU whose factors overflow is retried once
+    on the two-sided scaled matrix B = mu R A S.  A = 1e6 * (randsvd) has
+    entries beyond fp16's 65504, so the first LU holds Inf; the retry's
+    factors are finite, factor B within the LU model's backward-error bound,
+    and (applied as mu S U^-1 L^-1 P R) solve A to within kappa u_f."""
+    from oracle import lu as OL, squeeze as OS
+    n = 60
+    A0, _, _ = randsvd_system(n, 1e2, 3)
+    A = (1e6 * A0).astype(np.float32).astype(np.float64)
+    F1, _, _ = OL.lu_factor(A.astype(np.float32), F.FP16)
+    assert not np.all(np.isfinite(F1))
+    fac, scaled = M.factorize(A.astype(np.float32), F.FP16)
+    assert scaled and fac is not None and fac.scaled
+    assert np.all(np.isfinite(fac.F))
+    B = OS.scaled_matrix(A, fac.R, fac.S, fac.mu)
+    assert 0.1 * 65504 / 4 <= np.max(np.abs(B)) <= 0.1 * 65504 * 2
+    L, U = OL.unpack(fac.F)
+    Bf = F.fl(B.astype(np.float32), F.FP16).astype(np.float64)
+    nb, _ = OL.default_blocking(F.FP16, n)
+    E = np.abs(Bf[fac.perm] - L @ U)
+    assert np.all(E <= 2.0 * (np.ceil(n / nb) + 2) * F.u_of(F.FP16) * (np.abs(L) @ np.abs(U)))
+    c = np.random.default_rng(4).standard_normal(n)
+    y = np.linalg.solve(U, np.linalg.solve(L, (fac.R * c)[fac.perm]))
+    x = fac.mu * fac.S * y
+    xt = np.linalg.solve(A, c)
+    assert np.max(np.abs(x - xt)) / np.max(np.abs(xt)) <= 1e2 * 10 * F.u_of(F.FP16)
+    # no retry when the first factors are fine; a retry that still fails gives None
+    fac2, scaled2 = M.factorize(A0.astype(np.float32), F.FP16)
+    assert fac2 is not None and not scaled2 and not fac2.scaled
+    Z = A.copy()
+    Z[:, 5] = 0.0
+    fac3, scaled3 = M.factorize(Z.astype(np.float32), F.FP16)
+    assert fac3 is None and scaled3
+
+
+def test_squeezed_run_converges_and_records_scaling():
+    n = 80
+    A0, B0, _ = randsvd_system(n, 1e2, 5)
+    A = 1e6 * A0
+    b = 1e6 * B0[:, 0]
+    res = M.msir(A, b, (F.FP16, F.FP32, F.FP64))
+    assert res.cged and res.scaled[0] is True
+    Au = F.fl(A, F.FP32).astype(np.float64)
+    bu = F.fl(b, F.FP32).astype(np.float64)
+    from oracle import metrics as X
+    assert X.nbe(Au, bu, res.x) <= 2 * 2.0 ** -24
