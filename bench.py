@@ -1,20 +1,24 @@
 """Benchmark of the MSIR hot path on GB300.
 
-Workload (the n = 2000 sweep): dense randsvd systems, n = 2000, geometric
-singular values, kappa_2 in {1e2, 1e4, 1e6, 1e8} at (u_f, u, u_r) = (half,
-single, double) and {1e8, 1e10, 1e12} at (single, double, double-double),
-each also with row scalings 10^U(-4,4): 14 systems, one right-hand side
-each.  A step solves all 14 systems with MSIR (Algorithm 4) through
-msir_solve_batched, with inputs resident on the device.
+Default workload (c3_n8192_k1e3): the large single-solve configuration at
+n = 8192 with kappa_2 = 1e3 and geometric singular values, for each of the
+three precision triples (u_f, u, u_r) = (bf16, single, double), (half,
+single, double) and (single, double, double-double), one right-hand side:
+three systems per step, each solved by msir_solve on the whole GPU.  Other
+workloads (--workload): c3_n8192 (kappa in {1e3, 1e6, 1e10}, nine systems),
+c3 (n in {8192, 16384}, nrhs in {1, 16}, 36 runs), sweep_n2000 (the n = 2000
+sweep of 14 systems through msir_solve_batched).
 
-Metric: n^3-equivalent rate sum(2/3 n^3 + 2 n^2) / T in TFLOP/s, where T is
-the time from "A, b on the device" to "x on the device" with every system
-converged to nbe <= 2 u0.  Per-system device latencies give p50/p99; a plain
-fp64 LU solve (torch.linalg.lu_factor + lu_solve) of the same systems on the
-same GPU is timed as the comparator.
+Metric: n^3-equivalent rate sum(2/3 n^3 + 2 n^2 nrhs) / T in TFLOP/s, where
+T is the time from "A, b on the device" to "x on the device" with every
+system converged to nbe <= 2 u0.  Per-system device latencies give p50/p99;
+a plain fp64 LU solve (torch.linalg.lu_factor + lu_solve) of the same
+systems on the same GPU is timed as the comparator.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-With N > 1 (torchrun) every rank solves the full sweep (weak scaling).
+With N > 1 (torchrun) the job's systems (the workload once per rank) are
+sharded over the ranks by longest-processing-time on n^3 (weak scaling, no
+data-path collective).
 """
 
 import argparse
@@ -32,7 +36,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = "n³-equiv TFLOP/s to FP64-level backward error vs plain FP64 LU; p50/p99 ms"
 UNIT = "TFLOP/s"
-WORKLOAD = "sweep_n2000"
+HSD, BSD, SDQ = "fp16,fp32,fp64", "bf16,fp32,fp64", "fp32,fp64,dd"
+DEFAULT_WORKLOAD = "c3_n8192_k1e3"
+
+
+def workload_systems(name):
+    """(n, kappa, triple, graded, nrhs) of a named workload, and whether its
+    systems run one at a time on the whole GPU ('single') or together
+    through msir_solve_batched ('batched')."""
+    from synth import workloads
+    if name == "c3_n8192_k1e3":
+        return [(8192, 1e3, t, False, 1) for t in (BSD, HSD, SDQ)], "single"
+    if name == "c3_n8192":
+        return [(8192, k, t, False, 1) for k in (1e3, 1e6, 1e10) for t in (BSD, HSD, SDQ)], "single"
+    if name == "c3":
+        return [(n, k, t, False, r) for n in (8192, 16384) for k in (1e3, 1e6, 1e10)
+                for t in (BSD, HSD, SDQ) for r in (1, 16)], "single"
+    if name == "sweep_n2000":
+        return [(n, k, t, g, 1) for (n, k, t, g) in workloads("sweep_n2000")], "batched"
+    raise KeyError(name)
 
 
 def measure_gemv(ctx, dev, n=8192, kappa=1e3):
@@ -101,12 +123,14 @@ def flops_equiv(n, nrhs=1):
     return 2.0 / 3.0 * n ** 3 + 2.0 * n * n * nrhs
 
 
-def build_systems(device=None):
-    from synth import randsvd_system, workloads
+def build_systems(units, device=None):
+    """The seeded systems (A row-major fp64, B n x nrhs) of the given units."""
+    from synth import randsvd_system
     out = []
-    for (n, kappa, spec, graded) in workloads(WORKLOAD):
-        A, B, X = randsvd_system(n, kappa, 0, graded=graded, device=device)
-        out.append(dict(n=n, kappa=kappa, spec=spec, graded=graded, A=A, b=B[:, 0].copy()))
+    for (n, kappa, spec, graded, nrhs) in units:
+        A, B, X = randsvd_system(n, kappa, 0, nrhs=nrhs, graded=graded, device=device)
+        out.append(dict(n=n, kappa=kappa, spec=spec, graded=graded, nrhs=nrhs, A=A,
+                        b=B[:, 0].copy() if nrhs == 1 else B))
     return out
 
 
@@ -193,25 +217,17 @@ def refine_bytes(rep, n):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per refinement
-# launch, from one ncu capture of this bench's launch list (104 refinement
-# launches of four steps, serialised by the profiler), taken with the
-# refinement kernel as it stands; None once that kernel changes.
-REFINE_DRAM_BYTES_PER_LAUNCH = 2.430e9
-
-# fp64 pipe: 2 FMA lanes per SM per clock (the nominal 1.25 TFLOP/s over
-# 152 SMs at 2070 MHz), an FMA counted as 2 flops
-FP64_FMA_LANES_PER_SM = 2
-NUM_SMS = 152
-
-
-def fp64_peak_tflops(sm_mhz=2070.0):
-    return FP64_FMA_LANES_PER_SM * 2 * NUM_SMS * sm_mhz * 1e6 / 1e12
+# launch of this bench's default workload, from one ncu launch-list capture
+# of the same command with the refinement kernel as it stands; None when no
+# capture of the current kernel exists.
+REFINE_DRAM_BYTES_PER_LAUNCH = None
 
 
 def refine_fp64_flops(rep, n):
-    """fp64-pipe flops of the refinement of one system, per term of each
-    product in the precision it runs in: fp32 arithmetic none; fp64 one FMA
-    (2); a dd x fp64 product into a dd sum 8 (TwoProduct 3, FastTwoSum 3,
+    """fp64-pipe flops of the refinement of one system as this implementation
+    executes it, per term of each product in the precision it runs in: fp32
+    arithmetic none (compensated fp32 sums stay on the fp32 pipe); fp64 one
+    FMA (2); a dd x fp64 product into a dd sum 8 (TwoProduct 3, FastTwoSum 3,
     two additions); a dd x dd product 12 (one more FMA pair).  Every step
     forms the residual in u_r (n^2 terms) and applies the factors once
     (scaled-block substitutions, n^2 terms over both triangles) in u_f's
@@ -238,37 +254,67 @@ def refine_fp64_flops(rep, n):
     return tot
 
 
-def roofline_line(ref_bytes, ref_fp64, hbm_ach, fp64_ach, hbm_pk, hbm_kind, fp64_pk, concurrency):
+def refine_algorithmic_flops(rep, n):
+    """The method's own flop count of the refinement of one system, in
+    whatever precision each part runs: per step the residual (2 n^2) and one
+    application of the factors (2 n^2); per GMRES iteration the operator
+    product and the factors (4 n^2) and CGS2 (8 n k)."""
+    n2 = float(n) * n
+    tot = 0.0
+    for st in rep["stages"]:
+        tot += st["steps"] * 4.0 * n2
+        for k in st["gmres_iters"]:
+            for j in range(k):
+                tot += 4.0 * n2 + 8.0 * n * (j + 1)
+    return tot
+
+
+def fp64_peak():
+    """The fp64 fma rate measured on this GPU (msir_probe_fma_rate)."""
+    import paper_2107_06200_gb300 as M
+    best = 0.0
+    for _ in range(3):
+        tf, _sec = M.probe_fma_rate(0, M.FP64, 1 << 16)
+        best = max(best, tf)
+    return best
+
+
+def roofline_line(ref_bytes, ref_fp64, ref_alg, hbm_ach, fp64_ach, alg_ach, hbm_pk, hbm_kind, fp64_pk,
+                  concurrency):
     """The refinement kernel's bound is the larger of its two model times,
-    bytes at the measured HBM rate and fp64 flops at the fp64 pipe's peak."""
+    bytes at the measured HBM rate and fp64-pipe flops at the measured fp64
+    peak (the method's own flop count is reported beside them)."""
     t_hbm = ref_bytes / (hbm_pk * 1e9)
     t_fp64 = ref_fp64 / (fp64_pk * 1e12)
     hbm = {"achieved": hbm_ach, "peak": hbm_pk, "unit": "GB/s", "frac": hbm_ach / hbm_pk,
            "peak_source": hbm_kind, "model_s": t_hbm}
     fp64 = {"achieved": fp64_ach, "peak": fp64_pk, "unit": "TFLOP/s", "frac": fp64_ach / fp64_pk,
-            "peak_source": "derived: 2 fp64 FMA lanes/SM/clock x 152 SMs x 2070 MHz", "model_s": t_fp64}
+            "peak_source": "measured (msir_probe_fma_rate, fp64 fma chains on every SM)", "model_s": t_fp64,
+            "work": "fp64-pipe flops as executed (dd terms at 8 or 12 flops)"}
     top = ({"bound": "alu", "pipe": "fp64"} | fp64) if t_fp64 > t_hbm else ({"bound": "hbm"} | hbm)
     top.update({"kernel": "refine_kernel (persistent refinement)", "traffic": REFINE_DRAM_BYTES_PER_LAUNCH,
-                "traffic_unit": "bytes per launch (ncu, launches serialised)",
-                "concurrency": concurrency, "frac_of_gpu_share": top["frac"] * concurrency,
-                "hbm": hbm, "fp64": fp64})
+                "traffic_unit": "bytes per launch (ncu)", "concurrency": concurrency,
+                "frac_of_gpu_share": top["frac"] * concurrency, "hbm": hbm, "fp64": fp64,
+                "algorithmic": {"achieved": alg_ach, "unit": "TFLOP/s",
+                                "work": "4 n^2 per GMRES iteration or step, 8 n k for CGS2"}})
     return top
 
 
-def run_cpu_baseline(max_seconds=25.0):
+def run_cpu_baseline(units, max_seconds=25.0, n_sample=1024):
     """The oracle as it stands on the host cores, on a bounded sample of the
-    workload: the first systems of the sweep in order until the budget."""
-    from synth import randsvd_system, workloads
+    workload: its (kappa, triple) systems at n = n_sample (the oracle's LU
+    alone takes minutes at n = 8192), in order, until the budget; the rate
+    is the metric's n^3-equivalent rate of the systems it solved."""
+    from synth import randsvd_system
     from oracle import msir as OM, formats as OF
     names = {"fp16": OF.FP16, "bf16": OF.BF16, "fp32": OF.FP32, "fp64": OF.FP64, "dd": OF.DD}
     el = 0.0
     fl = 0.0
     done = []
-    for (n, kappa, spec, graded) in workloads(WORKLOAD):
+    for (n0, kappa, spec, graded, nrhs) in units:
         if el > max_seconds and done:
             break
-        if spec.endswith("dd"):
-            continue  # dd GMRES-IR in pure numpy takes many minutes per system
+        n = min(n0, n_sample)
         A, B, _ = randsvd_system(n, kappa, 0, graded=graded)
         trip = tuple(names[x] for x in spec.split(","))
         t1 = time.time()
@@ -278,8 +324,8 @@ def run_cpu_baseline(max_seconds=25.0):
         fl += flops_equiv(n)
         done.append(f"n={n} kappa={kappa:.0e} {spec}{' graded' if graded else ''} {dt:.1f}s")
     return {"value": fl / el / 1e12, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle MSIR on the (half, single, double) systems of the sweep in order, "
-                      "until ~%.0f s: " % max_seconds + "; ".join(done)}
+            "sample": "oracle MSIR, one right-hand side, on the workload's systems at n = %d in order, "
+                      "until ~%.0f s: " % (n_sample, max_seconds) + "; ".join(done)}
 
 
 # Small single solves for profiler captures: (n, kappa, triple, graded, repeats)
@@ -296,8 +342,8 @@ DATA = "synthetic (randsvd, geometric singular values, seeded)"
 # ---------------------------------------------------------------- serving
 
 def request_bytes(n):
-    """Device bytes a submitted request holds until it is done (the server
-    copies A, b and x at submission)."""
+    """Host bytes a submitted request holds until it is done (the server
+    keeps a host copy of A, b and x while the request waits)."""
     return 8 * n * n + 16 * n
 
 
@@ -307,7 +353,8 @@ def run_serving(server, systems, times, picks, duration_s, byte_cap, clock=time.
     start) for pool system picks[i]; outstanding requests are polled until
     duration_s.  An arrival whose device copy would take the outstanding
     requests above byte_cap is rejected and counted (the client's
-    back-pressure), not submitted.
+    back-pressure on the server's host-side queue), not submitted; None
+    means no cap.
 
     server: submit(A, b, spec) -> ticket; poll(ticket, n) -> (state, x,
     report, latency_ms), state 2 = done.  systems: (A, b, spec) host arrays.
@@ -327,7 +374,7 @@ def run_serving(server, systems, times, picks, duration_s, byte_cap, clock=time.
             rec = {"t": times[i], "n": n, "spec": spec, "status": "rejected", "latency_ms": None,
                    "cged": None, "t_done": None}
             need = request_bytes(n)
-            if used + need <= byte_cap:
+            if byte_cap is None or used + need <= byte_cap:
                 pending[server.submit(A, b, spec)] = rec
                 rec["status"] = "pending"
                 used += need
@@ -388,9 +435,13 @@ def run_serve_bench(args):
     ctx = M.Context(0)
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.9 * free)
-    srv = M.Server(ctx, hbm_budget_bytes=budget // 2, max_slots=args.max_slots)
+    # the server admits by device footprint inside `budget`; queued requests
+    # wait in host memory, which the client caps (an overloaded open-loop
+    # queue would otherwise grow without bound)
+    host_cap = int(args.host_queue_gb * 2 ** 30)
+    srv = M.Server(ctx, hbm_budget_bytes=budget, max_slots=args.max_slots)
     try:
-        recs = run_serving(srv, systems, times, picks, args.duration, byte_cap=budget // 2)
+        recs = run_serving(srv, systems, times, picks, args.duration, byte_cap=host_cap)
     finally:
         srv.close()
         ctx.close()
@@ -398,21 +449,25 @@ def run_serve_bench(args):
             "config": {"workload": "serving_poisson", "rate_per_s": args.rate, "duration_s": args.duration,
                        "warmup_s": args.serve_warmup, "pool": args.pool, "n_range": [args.nmin, args.nmax],
                        "log10_kappa_range": [2, 10], "triples": ["fp16,fp32,fp64", "bf16,fp32,fp64", "fp32,fp64,dd"],
-                       "max_slots": args.max_slots, "hbm_budget_bytes": budget // 2,
-                       "client_byte_cap": budget // 2}}
+                       "max_slots": args.max_slots, "hbm_budget_bytes": budget,
+                       "client_host_queue_bytes": host_cap}}
     line.update(serving_summary(recs, args.serve_warmup, args.duration))
     print(json.dumps(line))
 
 
-def bench_config(world, sequential=False):
+def bench_config(name, world, mode):
     """The workload both arms report (the reference arm times the oracle on
-    the same configuration)."""
-    from synth import workloads
-    return {"workload": WORKLOAD, "systems": len(list(workloads(WORKLOAD))), "n": 2000, "nrhs": 1,
-            "triples": ["fp16,fp32,fp64", "fp32,fp64,dd"], "graded": "both",
-            "l2": "inputs larger than L2 (14 fp64 2000x2000 matrices per step)",
-            "parallelism": f"weak x{world}",
-            "mode": "sequential msir_solve" if sequential else "msir_solve_batched"}
+    a bounded sample of the same configuration)."""
+    units, _ = workload_systems(name)
+    ns = sorted({u[0] for u in units})
+    return {"workload": name, "systems": len(units), "n": ns if len(ns) > 1 else ns[0],
+            "kappa": sorted({u[1] for u in units}), "triples": sorted({u[2] for u in units}),
+            "nrhs": sorted({u[4] for u in units}), "graded": sorted({u[3] for u in units}),
+            "l2": "inputs larger than L2 (fp64 A of %s)" % ", ".join(f"n={n}" for n in ns),
+            "parallelism": f"weak x{world} (LPT on n^3 over ranks)",
+            "mode": {"single": "msir_solve per system, whole GPU each",
+                     "batched": "msir_solve_batched (systems share the GPU)",
+                     "sequential": "msir_solve per system"}[mode]}
 
 
 def run_profile_case(name):
@@ -441,6 +496,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
+                    choices=["c3_n8192_k1e3", "c3_n8192", "c3", "sweep_n2000"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true", help="skip the operator bandwidth measurement")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
@@ -456,6 +513,8 @@ def main():
     ap.add_argument("--nmin", type=int, default=256)
     ap.add_argument("--nmax", type=int, default=8192)
     ap.add_argument("--max-slots", type=int, default=8, help="serving: concurrent solves")
+    ap.add_argument("--host-queue-gb", type=float, default=64.0,
+                    help="serving: client cap on the host bytes of outstanding requests")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args.profile_case)
@@ -467,6 +526,10 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
+    name = args.workload
+    units_all, mode = workload_systems(name)
+    if args.sequential:
+        mode = "sequential"
 
     if args.impl == "reference":
         if rank != 0:
@@ -475,7 +538,7 @@ def main():
         steps = []
         cb = None
         for i in range(args.warmup + args.steps):
-            cb = run_cpu_baseline(max_seconds=8.0)
+            cb = run_cpu_baseline(units_all, max_seconds=8.0)
             if i >= args.warmup:
                 steps.append(cb["value"])
         val = float(np.mean(steps))
@@ -483,8 +546,8 @@ def main():
             "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f16+f32+f64+dd", "data": DATA,
-            "config": bench_config(args.gpus),
+            "dtype": "f16+bf16+f32+f64+dd", "data": DATA,
+            "config": bench_config(name, args.gpus, mode) | {"reference_sample": cb["sample"]},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cb["cores"], "kind": "oracle",
                              "sample": cb["sample"]},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -499,26 +562,34 @@ def main():
     dev = torch.device("cuda", local)
     import paper_2107_06200_gb300 as M
 
-    systems = build_systems(device=None)  # numpy QR on the host (seeded, deterministic)
+    # the job's units: the workload once per rank, sharded by LPT on n^3
+    job_units = [u for _ in range(world) for u in units_all]
+    mine = lpt_partition([float(u[0]) ** 3 * (1 + 0.1 * (u[4] - 1)) for u in job_units], world)[rank]
+    units = [job_units[i] for i in mine]
+    big = max(u[0] for u in units) >= 4096
+    systems = build_systems(units, device=str(dev) if big else None)
     ctx = M.Context(local)
-    As = [torch.from_numpy(s["A"]).to(dev) for s in systems]
-    bs = [torch.from_numpy(s["b"]).to(dev) for s in systems]
-    specs = [s["spec"] for s in systems]
-    fl_step = sum(flops_equiv(s["n"]) for s in systems)
+    As = [torch.from_numpy(s_["A"]).to(dev) for s_ in systems]
+    bs = [torch.from_numpy(np.ascontiguousarray(s_["b"])).to(dev) for s_ in systems]
+    specs = [s_["spec"] for s_ in systems]
+    fl_step = sum(flops_equiv(s_["n"], s_["nrhs"]) for s_ in systems)
+    fl_job = sum(flops_equiv(u[0], u[4]) for u in job_units)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
     def step():
-        if args.sequential:
-            xs, reps = [], []
-            for A, b, sp in zip(As, bs, specs):
-                x, r, st = ctx.solve(A, b, sp)
-                xs.append(x)
-                reps.append(r[0])
+        if mode == "batched":
+            xs, reps, st = ctx.solve_batched(As, bs, specs)
             return xs, reps, st
-        xs, reps, st = ctx.solve_batched(As, bs, specs)
+        xs, reps = [], []
+        st = M.OK
+        for A, b, sp in zip(As, bs, specs):
+            x, r, st1 = ctx.solve(A, b, sp)
+            xs.append(x)
+            reps.extend(r)
+            st = max(st, st1)
         return xs, reps, st
 
     for _ in range(args.warmup):
@@ -543,62 +614,78 @@ def main():
     ms = ev0.elapsed_time(ev1)
     ms = max_over_ranks(ms, world, dev)
     ms_per_step = ms / args.steps
-    value = whole_job_rate(fl_step, world, ms_per_step)
+    # whole-job rate: all ranks' units over the slowest rank's time
+    value = fl_job / (ms_per_step * 1e-3) / 1e12
 
-    # accuracy of the last step (every system must reach nbe <= 2 u0)
+    # per-report system sizes (a 16-column system gives 16 reports)
+    rep_n = [s_["n"] for s_ in systems for _ in range(s_["nrhs"])]
+    rep_spec = [s_["spec"] for s_ in systems for _ in range(s_["nrhs"])]
     u0s = {"fp32": 2.0 ** -24, "fp64": 2.0 ** -53}
-    nbe_ok = all(r["cged"] and r["nbe"] <= 2 * u0s[s.split(",")[1]]
-                 for r, s in zip(all_reps[-1], specs))
-    # per-system latency (device time of factorisations and refinement) over
-    # at least 200 solves: the timed steps, then further untimed steps
+    last = all_reps[-1]
+    nbe_ok = all(r["cged"] and r["nbe"] <= 2 * u0s[sp.split(",")[1]] for r, sp in zip(last, rep_spec))
     lat = [r["t_factor_ms"] + r["t_refine_ms"] for reps in all_reps for r in reps]
-    tl = time.perf_counter()
-    while len(lat) < 200 and time.perf_counter() - tl < 20.0:
-        _, reps_x, _ = step()
-        lat.extend(r["t_factor_ms"] + r["t_refine_ms"] for r in reps_x)
     p50 = float(np.percentile(lat, 50))
     p99 = float(np.percentile(lat, 99))
 
     # roofline of the dominant kernel (persistent refinement kernel)
-    ref_ms = sum(r["t_refine_ms"] for r in all_reps[-1])
-    ref_launch = sum(r["n_refine_launches"] for r in all_reps[-1])
-    fac_ms = sum(r["t_factor_ms"] for r in all_reps[-1])
-    ref_bytes = sum(refine_bytes(r, s["n"]) for r, s in zip(all_reps[-1], systems))
-    ref_fp64 = sum(refine_fp64_flops(r, s["n"]) for r, s in zip(all_reps[-1], systems))
+    ref_ms = sum(r["t_refine_ms"] for r in last)
+    ref_launch = sum(r["n_refine_launches"] for r in last)
+    fac_ms = sum(r["t_factor_ms"] for r in last)
+    ref_bytes = sum(refine_bytes(r, n) for r, n in zip(last, rep_n))
+    ref_fp64 = sum(refine_fp64_flops(r, n) for r, n in zip(last, rep_n))
+    ref_alg = sum(refine_algorithmic_flops(r, n) for r, n in zip(last, rep_n))
     peak, peak_kind = peaks()
-    # per launch: algorithmic work / average launch duration (the launches
-    # of concurrent solves share the GPU: `concurrency` is the mean number
-    # of solves in flight, device time of all solves over the step time)
     dur_s = (ref_ms / ref_launch) * 1e-3 if ref_ms > 0 else float("inf")
     hbm_ach = (ref_bytes / ref_launch) / dur_s / 1e9
     fp64_ach = (ref_fp64 / ref_launch) / dur_s / 1e12
-    fp64_pk = fp64_peak_tflops()
+    alg_ach = (ref_alg / ref_launch) / dur_s / 1e12
+    fp64_pk = fp64_peak()
     concurrency = max(1.0, (fac_ms + ref_ms) / ms_per_step) if ms_per_step > 0 else 1.0
     launches = sum(r["n_launches"] for reps in all_reps for r in reps)
+    per_system = [{"n": s_["n"], "kappa": s_["kappa"], "triple": s_["spec"], "nrhs": s_["nrhs"],
+                   "stages": r["steps"], "nbe": r["nbe"], "cged": r["cged"],
+                   "ms": r["t_factor_ms"] + r["t_refine_ms"], "factor_ms": r["t_factor_ms"]}
+                  for s_, r in zip([s_ for s_ in systems for _ in range(s_["nrhs"])], last)]
 
-    # end to end through the public API with host buffers: pinned host ->
-    # device copies of A and b, solve, device -> host copy of x, every step
-    As_h = [torch.from_numpy(s["A"]).pin_memory() for s in systems]
-    bs_h = [torch.from_numpy(s["b"]).pin_memory() for s in systems]
-    h2d = sum(a.numel() * 8 for a in As_h) + sum(b.numel() * 8 for b in bs_h)
-    d2h = sum(s["n"] * 8 for s in systems)
+    # end to end through the public API with host buffers: the C call copies
+    # A and b in and x out (msir_solve_host), every step
+    e2e_steps = max(1, min(args.steps, 3))
+    As_h = [np.asfortranarray(s_["A"]) for s_ in systems]
+    bs_h = [np.ascontiguousarray(s_["b"]) for s_ in systems]
+    h2d = sum(8 * s_["n"] * s_["n"] + 8 * s_["n"] * s_["nrhs"] for s_ in systems)
+    d2h = sum(8 * s_["n"] * s_["nrhs"] for s_ in systems)
+    if mode == "batched":
+        As_p = [torch.from_numpy(s_["A"]).pin_memory() for s_ in systems]
+        bs_p = [torch.from_numpy(np.ascontiguousarray(s_["b"])).pin_memory() for s_ in systems]
     torch.cuda.synchronize()
+    barrier()
     te = time.perf_counter()
-    for _ in range(args.steps):
-        Ad = [a.to(dev, non_blocking=True) for a in As_h]
-        bd = [b.to(dev, non_blocking=True) for b in bs_h]
-        xs, reps, st = ctx.solve_batched(Ad, bd, specs)
-        xh = [x.cpu() for x in xs]
+    for _ in range(e2e_steps):
+        if mode == "batched":
+            Ad = [a.to(dev, non_blocking=True) for a in As_p]
+            bd = [b.to(dev, non_blocking=True) for b in bs_p]
+            xs, reps, st = ctx.solve_batched(Ad, bd, specs)
+            xh = [x.cpu() for x in xs]
+        else:
+            for A_h, b_h, s_ in zip(As_h, bs_h, systems):
+                if s_["nrhs"] == 1:
+                    xh, rh, sh = ctx.solve_host(A_h, b_h, s_["spec"])
+                else:  # several columns: device buffers from pinned host copies
+                    Ad = torch.from_numpy(s_["A"]).pin_memory().to(dev, non_blocking=True)
+                    Bd = torch.from_numpy(np.ascontiguousarray(s_["b"])).pin_memory().to(dev, non_blocking=True)
+                    X, _, _ = ctx.solve(Ad, Bd, s_["spec"])
+                    X.cpu()
     torch.cuda.synchronize()
-    e2e_s = (time.perf_counter() - te) / args.steps
-    e2e_val = fl_step * world / e2e_s / 1e12
+    barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - te) / e2e_steps * 1e3, world, dev) * 1e-3
+    e2e_val = fl_job / e2e_s / 1e12
 
     # comparator: plain fp64 LU solve of the same systems on the same GPU
     def fp64_step():
         xs64 = []
         for A, b in zip(As, bs):
             LU, piv = torch.linalg.lu_factor(A)
-            xs64.append(torch.linalg.lu_solve(LU, piv, b[:, None])[:, 0])
+            xs64.append(torch.linalg.lu_solve(LU, piv, b[:, None] if b.dim() == 1 else b))
         return xs64
     try:
         fp64_step()
@@ -608,12 +695,12 @@ def main():
         torch.cuda.synchronize()
         fp64_s = time.perf_counter() - tf
         fp64_val = fl_step / fp64_s / 1e12
-        # its normwise backward error, for comparison with the 2 u0 target
         fp64_nbe = 0.0
         for A, b, x64 in zip(As, bs, fp64_step()):
-            r64 = b - A @ x64
+            bb = b[:, None] if b.dim() == 1 else b
+            r64 = bb - A @ x64
             fp64_nbe = max(fp64_nbe, float(torch.max(torch.abs(r64)) / (
-                torch.max(torch.abs(A).sum(1)) * torch.max(torch.abs(x64)) + torch.max(torch.abs(b)))))
+                torch.max(torch.abs(A).sum(1)) * torch.max(torch.abs(x64)) + torch.max(torch.abs(bb)))))
     except Exception as exc:  # e.g. torch's linalg library not loadable in this environment
         fp64_s, fp64_val, fp64_nbe = float("nan"), None, None
         print(f"fp64 LU comparator unavailable: {exc}", file=sys.stderr)
@@ -622,26 +709,29 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = run_cpu_baseline()
+        cpu = run_cpu_baseline(units_all)
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f16+f32+f64+dd",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f16+bf16+f32+f64+dd",
             "data": DATA,
-            "config": bench_config(world, args.sequential),
+            "config": bench_config(name, world, mode),
             "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat)},
             "all_converged_nbe_le_2u0": nbe_ok,
+            "systems": per_system,
             "fp64_lu": {"value": fp64_val, "unit": UNIT,
                         "ms_per_step": None if fp64_val is None else fp64_s * 1e3,
                         "nbe_max": fp64_nbe,
                         "impl": "torch.linalg.lu_factor+lu_solve float64",
                         "versions": {"torch": torch.__version__, "cuda": torch.version.cuda}},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h},
-            "roofline": roofline_line(ref_bytes, ref_fp64, hbm_ach, fp64_ach, peak, peak_kind,
-                                      fp64_pk, concurrency),
+                    "d2h_bytes_per_step": d2h, "steps": e2e_steps,
+                    "api": "msir_solve_host (host buffers, copies inside the call)"
+                    if mode != "batched" else "pinned host copies + msir_solve_batched"},
+            "roofline": roofline_line(ref_bytes, ref_fp64, ref_alg, hbm_ach, fp64_ach, alg_ach, peak,
+                                      peak_kind, fp64_pk, concurrency),
             "time_split_ms": {"factor": fac_ms, "refine": ref_ms},
             "cpu_baseline": cpu,
             "gemv": gemv,

@@ -247,22 +247,24 @@ msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n,
                                const msir_params* params, msir_report* reps);
 
 /* Continuous-batching solve server on the context's device.
- * hbm_budget_bytes: device memory the server may hold for admitted
- * requests (0 = 90% of the free memory).  max_slots: requests in flight on
- * the device at once.  A worker thread admits queued requests when their
- * footprint (A in u, L/U in the largest u_f it may need, Krylov basis)
- * fits the budget and a slot is free, and runs each on its own stream. */
+ * hbm_budget_bytes: device memory the server may hold (0 = 90% of the free
+ * memory).  max_slots: requests in flight on the device at once.  A worker
+ * thread admits queued requests into free slots, each on its own stream:
+ * a request is admitted when the device memory it needs (its workspace and
+ * its A, b, x in the slot) fits the budget; requests are taken in arrival
+ * order, and one that does not fit may be passed by later requests that do,
+ * at most 8 times, after which it waits for memory to free up.  Slots keep
+ * their workspaces between requests and give them back only when a request
+ * would not fit otherwise. */
 msir_status msir_server_create(msir_ctx* ctx, size_t hbm_budget_bytes, int max_slots,
                                msir_server** out);
 
 /* Queues one request.  A_host (column-major, lda) and b_host are host
- * memory, copied before the call returns.  *ticket receives an id.
- * The copy is made on the device (8 n^2 + 16 n bytes, outside
- * hbm_budget_bytes) and held while the request waits in the queue, so a
- * caller that submits faster than the server solves bounds its own
- * outstanding requests.  Errors: MSIR_ERR_INVALID for bad arguments,
- * MSIR_ERR_NOMEM / MSIR_ERR_CUDA when the device copy fails (nothing is
- * queued then). */
+ * memory; they are copied into host memory that the server owns before the
+ * call returns, and to the device when the request is admitted (inside
+ * hbm_budget_bytes).  *ticket receives an id.  Errors: MSIR_ERR_INVALID for
+ * bad arguments, MSIR_ERR_NOMEM when the host copy cannot be allocated
+ * (nothing is queued then). */
 msir_status msir_server_submit(msir_server* s, int n, const double* A_host, int lda,
                                const double* b_host, msir_triple t, const msir_params* params,
                                uint64_t* ticket);

@@ -26,6 +26,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -1448,17 +1449,31 @@ msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n, const dou
 struct Request {
   uint64_t ticket;
   Job job;
-  double* dA = nullptr;  // device copies owned by the server
+  std::vector<double> A_host;  // column-major n x n copy, held while queued
+  std::vector<double> b_host;
+  std::vector<double> x_host;
+  int state = 0;               // 0 queued, 1 running, 2 done
+  size_t footprint = 0;        // device bytes while running (workspace + A, b, x)
+  int bypassed = 0;            // admissions of later requests while this one waited first in line
+};
+
+// A server slot: a solve slot plus device buffers for the admitted
+// request's A, b and x.  Slots keep their workspace and buffers between
+// requests (grown when a larger request arrives), so admission allocates
+// only when a request needs more than the slot holds.
+struct ServerSlot {
+  Slot s;
+  double* dA = nullptr;
   double* db = nullptr;
   double* dx = nullptr;
-  std::vector<double> x_host;
-  int state = 0;         // 0 queued, 1 running, 2 done
-  size_t footprint = 0;
+  int ncap = 0;             // dA / db / dx sized for n <= ncap
+  size_t held = 0;          // device bytes held: workspace + buffers
+  Request* req = nullptr;
 };
 
 struct msir_server {
   msir_ctx* ctx = nullptr;
-  size_t budget = 0, in_use = 0;
+  size_t budget = 0, in_use = 0;  // in_use: bytes held by all slots
   int max_slots = 1;
   std::mutex mu;
   std::condition_variable cv;
@@ -1467,8 +1482,7 @@ struct msir_server {
   uint64_t next_ticket = 1;
   std::atomic<bool> stop{false};
   std::thread worker;
-  std::vector<Slot> slots;
-  std::vector<Request*> running;
+  std::vector<ServerSlot> slots;
 };
 
 static size_t request_footprint(int n, const msir_params& p, int u) {
@@ -1478,47 +1492,128 @@ static size_t request_footprint(int n, const msir_params& p, int u) {
   return ws + nn * 8 + (size_t)n * 16;
 }
 
+// A request that arrives first in line is passed by smaller ones that fit
+// while it does not; after this many such admissions no later request is
+// admitted before it (it waits for memory to free up instead).
+constexpr int kMaxBypass = 8;
+
+// Device bytes that admitting a request of footprint fp into slot ss adds
+// to what the slot already holds (slots keep what they allocated).
+static size_t admit_delta(const ServerSlot& ss, size_t fp) { return fp > ss.held ? fp - ss.held : 0; }
+
+// Frees what an idle slot holds (workspace and buffers).  Worker only.
+static void server_release(msir_server* S, ServerSlot& ss) {
+  Slot& s = ss.s;
+  ws_free(s.w, s.st);
+  if (ss.dA) cudaFreeAsync(ss.dA, s.st);
+  if (ss.db) cudaFreeAsync(ss.db, s.st);
+  if (ss.dx) cudaFreeAsync(ss.dx, s.st);
+  cudaStreamSynchronize(s.st);
+  ss.dA = ss.db = ss.dx = nullptr;
+  ss.ncap = 0;
+  s.loaded_id = 0;
+  S->in_use -= ss.held;
+  ss.held = 0;
+}
+
+// Bring slot ss's buffers and workspace up to request q and copy q's A and
+// b to the device (on the slot's stream).  Called by the worker only.
+static msir_status server_load(msir_server* S, ServerSlot& ss, Request* q) {
+  Slot& s = ss.s;
+  const int n = q->job.n;
+  const msir_params& p = q->job.p;
+  if (n > ss.ncap) {
+    if (ss.dA) cudaFreeAsync(ss.dA, s.st);
+    if (ss.db) cudaFreeAsync(ss.db, s.st);
+    if (ss.dx) cudaFreeAsync(ss.dx, s.st);
+    ss.dA = ss.db = ss.dx = nullptr;
+    ss.ncap = 0;
+    CK(cudaMallocAsync((void**)&ss.dA, (size_t)n * n * 8, s.st));
+    CK(cudaMallocAsync((void**)&ss.db, (size_t)n * 8, s.st));
+    CK(cudaMallocAsync((void**)&ss.dx, (size_t)n * 8, s.st));
+    ss.ncap = n;
+  }
+  CK(cudaMemcpyAsync(ss.dA, q->A_host.data(), (size_t)n * n * 8, cudaMemcpyHostToDevice, s.st));
+  CK(cudaMemcpyAsync(ss.db, q->b_host.data(), (size_t)n * 8, cudaMemcpyHostToDevice, s.st));
+  q->job.A = ss.dA;
+  q->job.lda = n;
+  q->job.b = ss.db;
+  q->job.x = ss.dx;
+  (void)p;
+  (void)S;
+  return MSIR_OK;
+}
+
 static void server_loop(msir_server* S) {
   cudaSetDevice(S->ctx->device);
   const int share = S->max_slots;
   while (true) {
-    // admit
+    // admit: requests in arrival order into free slots while the memory
+    // they add fits the budget; a request that does not fit is passed by
+    // later ones that do, at most kMaxBypass times
     {
       std::unique_lock<std::mutex> lk(S->mu);
       for (size_t si = 0; si < S->slots.size(); ++si) {
-        if (S->running[si] || S->queue.empty()) continue;
-        Request* q = S->queue.front();
-        if (S->in_use + q->footprint > S->budget && S->in_use > 0) break;
-        S->queue.pop_front();
-        S->in_use += q->footprint;
-        q->state = 1;
-        S->running[si] = q;
+        ServerSlot& ss = S->slots[si];
+        if (ss.req || S->queue.empty()) continue;
+        Request* pick = nullptr;
+        size_t delta = 0;
+        for (int attempt = 0; attempt < 2 && !pick; ++attempt) {
+          for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
+            Request* q = *it;
+            const size_t d = admit_delta(ss, q->footprint);
+            const bool fits = S->in_use + d <= S->budget || S->in_use == 0;
+            if (fits) {
+              pick = q;
+              delta = d;
+              S->queue.erase(it);
+              break;
+            }
+            if (it == S->queue.begin() && q->bypassed >= kMaxBypass) break;  // the head's turn
+          }
+          if (pick || attempt > 0) break;
+          // nothing fits: idle slots give back what they keep, then retry
+          bool freed = false;
+          for (auto& o : S->slots)
+            if (!o.req && o.held > 0) {
+              server_release(S, o);
+              freed = true;
+            }
+          if (!freed) break;
+        }
+        if (!pick) continue;
+        if (!S->queue.empty() && S->queue.front()->job.t_submit < pick->job.t_submit)
+          S->queue.front()->bypassed++;
+        S->in_use += delta;
+        ss.held += delta;
+        pick->state = 1;
+        ss.req = pick;
         lk.unlock();
-        Slot& s = S->slots[si];
-        ws_free(s.w, s.st);
+        Slot& s = ss.s;
         s.loaded_id = 0;
-        msir_status r = slot_start(S->ctx, s, &q->job, share);
+        msir_status r = server_load(S, ss, pick);
+        if (r == MSIR_OK) r = slot_start(S->ctx, s, &pick->job, share);
         lk.lock();
         if (r != MSIR_OK) {
-          q->job.status = r;
-          q->state = 2;
-          q->job.t_done = std::chrono::steady_clock::now();
-          S->in_use -= q->footprint;
-          S->running[si] = nullptr;
+          pick->job.status = r;
+          pick->state = 2;
+          pick->job.t_done = std::chrono::steady_clock::now();
+          ss.req = nullptr;
           s.job = nullptr;
           s.step = S_IDLE;
         }
       }
       if (S->stop && S->queue.empty()) {
         bool any = false;
-        for (auto* q : S->running) any = any || q;
+        for (auto& ss : S->slots) any = any || ss.req;
         if (!any) break;
       }
     }
     bool progressed = false;
     for (size_t si = 0; si < S->slots.size(); ++si) {
-      Slot& s = S->slots[si];
-      Request* q = S->running[si];
+      ServerSlot& ss = S->slots[si];
+      Slot& s = ss.s;
+      Request* q = ss.req;
       if (!q || !s.job) continue;
       cudaError_t e = cudaEventQuery(s.ev);
       if (e == cudaErrorNotReady) continue;
@@ -1533,25 +1628,20 @@ static void server_loop(msir_server* S) {
         done = slot_advance(S->ctx, s);
       }
       if (done) {
-        cudaMemcpyAsync(q->x_host.data(), q->dx, (size_t)q->job.n * 8, cudaMemcpyDeviceToHost, s.st);
-        cudaStreamSynchronize(s.st);
-        ws_free(s.w, s.st);
-        cudaFreeAsync(q->dA, s.st);
-        cudaFreeAsync(q->db, s.st);
-        cudaFreeAsync(q->dx, s.st);
+        cudaMemcpyAsync(q->x_host.data(), ss.dx, (size_t)q->job.n * 8, cudaMemcpyDeviceToHost, s.st);
         cudaStreamSynchronize(s.st);
         std::lock_guard<std::mutex> lk(S->mu);
-        q->dA = q->db = q->dx = nullptr;
+        q->A_host.clear();
+        q->A_host.shrink_to_fit();
         q->job.t_done = std::chrono::steady_clock::now();
         q->state = 2;
-        S->in_use -= q->footprint;
-        S->running[si] = nullptr;
+        ss.req = nullptr;
       }
     }
     if (!progressed) {
       std::unique_lock<std::mutex> lk(S->mu);
       bool idle = S->queue.empty();
-      for (auto* q : S->running) idle = idle && !q;
+      for (auto& ss : S->slots) idle = idle && !ss.req;
       if (idle && !S->stop)
         S->cv.wait_for(lk, std::chrono::milliseconds(2));
       else
@@ -1573,11 +1663,10 @@ msir_status msir_server_create(msir_ctx* ctx, size_t hbm_budget_bytes, int max_s
   S->budget = hbm_budget_bytes;
   S->max_slots = max_slots;
   S->slots.resize(max_slots);
-  S->running.assign(max_slots, nullptr);
-  for (auto& s : S->slots) {
-    msir_status r = slot_init(s, ctx->device);
+  for (auto& ss : S->slots) {
+    msir_status r = slot_init(ss.s, ctx->device);
     if (r != MSIR_OK) {
-      for (auto& s2 : S->slots) slot_destroy(s2);
+      for (auto& s2 : S->slots) slot_destroy(s2.s);
       delete S;
       return r;
     }
@@ -1593,35 +1682,24 @@ msir_status msir_server_submit(msir_server* S, int n, const double* A_host, int 
   if (!valid_triple(t)) return MSIR_ERR_INVALID;
   msir_params p = resolve_params(params);
   if (!valid_params(p)) return MSIR_ERR_INVALID;
-  cudaSetDevice(S->ctx->device);
-  auto* q = new Request();
+  auto* q = new (std::nothrow) Request();
+  if (!q) return MSIR_ERR_NOMEM;
   q->job.n = n;
   q->job.lda = n;
   q->job.t = t;
   q->job.p = p;
   q->footprint = request_footprint(n, p, t.u);
-  q->x_host.assign(n, 0.0);
-  // copy in now: the caller may free its buffers when submit returns
-  cudaStream_t cs;
-  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) { delete q; return MSIR_ERR_CUDA; }
-  cudaError_t e = cudaMallocAsync((void**)&q->dA, (size_t)n * n * 8, cs);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&q->db, (size_t)n * 8, cs);
-  if (e == cudaSuccess) e = cudaMallocAsync((void**)&q->dx, (size_t)n * 8, cs);
-  if (e == cudaSuccess) e = cudaMemcpy2DAsync(q->dA, (size_t)n * 8, A_host, (size_t)lda * 8, (size_t)n * 8, n,
-                                              cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(q->db, b_host, (size_t)n * 8, cudaMemcpyHostToDevice, cs);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
-  cudaStreamDestroy(cs);
-  if (e != cudaSuccess) {
-    if (q->dA) cudaFree(q->dA);
-    if (q->db) cudaFree(q->db);
-    if (q->dx) cudaFree(q->dx);
+  // copy in now (host memory; the caller may free its buffers on return);
+  // the device copy is made when the request is admitted
+  try {
+    q->A_host.resize((size_t)n * n);
+    q->b_host.assign(b_host, b_host + n);
+    q->x_host.assign(n, 0.0);
+  } catch (...) {
     delete q;
-    return cuda_status(e);
+    return MSIR_ERR_NOMEM;
   }
-  q->job.A = q->dA;
-  q->job.b = q->db;
-  q->job.x = q->dx;
+  for (int j = 0; j < n; ++j) memcpy(q->A_host.data() + (size_t)j * n, A_host + (size_t)j * lda, (size_t)n * 8);
   q->job.t_submit = std::chrono::steady_clock::now();
   {
     std::lock_guard<std::mutex> lk(S->mu);
@@ -1658,14 +1736,15 @@ msir_status msir_server_destroy(msir_server* S) {
   S->stop = true;
   S->cv.notify_all();
   if (S->worker.joinable()) S->worker.join();
-  for (auto& s : S->slots) slot_destroy(s);
-  for (auto& kv : S->all) {
-    Request* q = kv.second;
-    if (q->dA) cudaFree(q->dA);
-    if (q->db) cudaFree(q->db);
-    if (q->dx) cudaFree(q->dx);
-    delete q;
+  for (auto& ss : S->slots) {
+    if (ss.s.st) {
+      if (ss.dA) cudaFreeAsync(ss.dA, ss.s.st);
+      if (ss.db) cudaFreeAsync(ss.db, ss.s.st);
+      if (ss.dx) cudaFreeAsync(ss.dx, ss.s.st);
+    }
+    slot_destroy(ss.s);
   }
+  for (auto& kv : S->all) delete kv.second;
   delete S;
   return MSIR_OK;
 }

@@ -1020,16 +1020,33 @@ __device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
       }
       // four consecutive columns per lane and step, 16-byte loads
       const int n4 = ((reinterpret_cast<uintptr_t>(v) & 15) == 0) ? (cx.n & ~3) : 0;
-#pragma unroll 2
-      for (int j = cx.lane * 4; j < n4; j += 128) {
-        float vv[4];
-        ld4f_vec<U>(v + j, vv);
+      // software pipeline: the next step's 8 rows x 4 columns and v are
+      // loaded into registers while this step's compensated sums run
+      {
+        int j = cx.lane * 4;
+        float an[8][4], vn[4];
+        if (j < n4) {
+          ld4f_vec<U>(v + j, vn);
 #pragma unroll
-        for (int rr = 0; rr < 8; ++rr) {
-          float av[4];
-          ld4f_row<A0>(rows[rr] + j, av);
+          for (int rr = 0; rr < 8; ++rr) ld4f_row<A0>(rows[rr] + j, an[rr]);
+        }
+        for (; j < n4; j += 128) {
+          float ac[8][4], vc[4];
 #pragma unroll
-          for (int q = 0; q < 4; ++q) acc[rr] = ff_fma(av[q], vv[q], acc[rr]);
+          for (int q = 0; q < 4; ++q) vc[q] = vn[q];
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) ac[rr][q] = an[rr][q];
+          if (j + 128 < n4) {
+            ld4f_vec<U>(v + j + 128, vn);
+#pragma unroll
+            for (int rr = 0; rr < 8; ++rr) ld4f_row<A0>(rows[rr] + j + 128, an[rr]);
+          }
+#pragma unroll
+          for (int rr = 0; rr < 8; ++rr)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[rr] = ff_fma(ac[rr][q], vc[q], acc[rr]);
         }
       }
       for (int j = n4 + cx.lane; j < cx.n; j += 32) {

@@ -93,10 +93,15 @@ def same_result(A, b, u0, x1, r1, x2, r2):
     assert f1 <= 2 * f2 + 2 * uu and f2 <= 2 * f1 + 2 * uu, (f1, f2)
 
 
+# spacing of the subnormal numbers (gradual underflow) of each format
+ETA = {OF.BF16: 2.0 ** -133, OF.FP16: 2.0 ** -24, OF.FP32: 2.0 ** -149, OF.FP64: 2.0 ** -1074}
+
+
 def ulp_f(a, fmt):
-    """One unit in the last place of format fmt at magnitude a (> 0)."""
+    """One unit in the last place of format fmt at magnitude a (the
+    subnormal spacing below the normal range)."""
     p = {OF.BF16: 8, OF.FP16: 11, OF.FP32: 24, OF.FP64: 53}[fmt]
-    return 2.0 ** (math.floor(math.log2(a)) - (p - 1)) if a > 0 else 0.0
+    return max(2.0 ** (math.floor(math.log2(a)) - (p - 1)), ETA[fmt]) if a > 0 else ETA[fmt]
 
 
 def check_half_factors(ctx, A, u, uf, nb, nbo):
@@ -109,8 +114,11 @@ def check_half_factors(ctx, A, u, uf, nb, nbo):
         candidates of the two chosen rows lie within c_j ulps of u_f at the
         column's scale max_i (|L||U|)_ij, c_j = ceil(j / nb) + 1 (one per
         panel store before j, one for the panel's own arithmetic);
-      * before j the factors agree elementwise within c_j u_f (|L||U|) (for
-        L relative to |u_jj|), rows in their original order;
+      * before j the factors agree elementwise within c_j (u_f (|L||U|) + eta)
+        (for L, u_f (|L||U|) / |u_jj| + eta), rows in their original order,
+        eta the subnormal spacing of u_f (rows scaled far down, as in the
+        graded systems, hold subnormal values whose rounding error is
+        absolute);
       * the GPU's factors satisfy the factorisation model's elementwise
         backward-error bound 2 (ceil(n/nb) + 2) u_f |L||U|, and |l_ij| <= 1.
     Returns (j, gap in ulps of the candidate) with j = n if no pivot differs."""
@@ -142,13 +150,14 @@ def check_half_factors(ctx, A, u, uf, nb, nbo):
         Lr[perm_o] = np.tril(Fo, -1)
         LUr[perm_o] = LUabs
         ujj = np.abs(np.diag(Fo))[:j]
-        assert np.all(np.abs(Lg[:, :j] - Lr[:, :j]) <= cj * uu * LUr[:, :j] / ujj[None, :])
-        assert np.all(np.abs(np.triu(fac.F)[:j] - np.triu(Fo)[:j]) <= cj * uu * LUabs[:j])
+        eta = ETA[uf]
+        assert np.all(np.abs(Lg[:, :j] - Lr[:, :j]) <= cj * (uu * LUr[:, :j] / ujj[None, :] + eta))
+        assert np.all(np.abs(np.triu(fac.F)[:j] - np.triu(Fo)[:j]) <= cj * (uu * LUabs[:j] + eta))
     L, U = OL.unpack(fac.F)
     Af = OF.fl(Au, uf).astype(np.float64)
     E = np.abs(Af[fac.perm] - L @ U)
     c_bound = 2.0 * (math.ceil(n / nb_used) + 2) * OF.u_of(uf)
-    assert np.all(E <= c_bound * (np.abs(L) @ np.abs(U)) + 1e-300)
+    assert np.all(E <= c_bound * (np.abs(L) @ np.abs(U)) + n * ETA[uf])
     assert np.max(np.abs(np.tril(fac.F, -1))) <= 1.0
     return j, gap
 

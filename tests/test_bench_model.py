@@ -38,18 +38,35 @@ def test_fp64_flops_sir_after_escalation_to_fp64_factors():
     assert bench.refine_fp64_flops(rep, n) == 2 * (8 + 2) * n * n
 
 
-def test_fp64_peak_from_unit_counts_and_clock():
-    assert bench.fp64_peak_tflops(2070.0) == pytest.approx(2 * 2 * 152 * 2.07e9 / 1e12)
+def test_algorithmic_flops_per_step_and_iteration():
+    n, k = 30, 2
+    rep = {"stages": [_st("SIR", "fp16", "fp32", "fp64", 2),
+                      _st("GMRES-IR", "fp16", "fp32", "fp64", 1, [k])]}
+    want = 2 * 4 * n * n + 1 * 4 * n * n + sum(4 * n * n + 8 * n * (j + 1) for j in range(k))
+    assert bench.refine_algorithmic_flops(rep, n) == want
 
 
 @pytest.mark.parametrize("fp64_flops,bound", [(1e12, "alu"), (1e6, "hbm")])
 def test_roofline_takes_the_larger_model_time(fp64_flops, bound):
-    line = bench.roofline_line(1e9, fp64_flops, 100.0, 0.1, 6779.4, "measured", 1.25, 4.0)
+    line = bench.roofline_line(1e9, fp64_flops, 5e8, 100.0, 0.1, 0.05, 6779.4, "measured", 1.25, 4.0)
     assert line["bound"] == bound
     top = line["fp64"] if bound == "alu" else line["hbm"]
     assert line["achieved"] == top["achieved"] and line["frac"] == pytest.approx(top["frac"])
     assert line["frac_of_gpu_share"] == pytest.approx(line["frac"] * 4.0)
     assert line["traffic"] is None or line["traffic"] > 0
+    assert line["algorithmic"]["achieved"] == 0.05
+
+
+def test_workloads_and_their_shards():
+    units, mode = bench.workload_systems("c3_n8192_k1e3")
+    assert mode == "single" and [u[2] for u in units] == [bench.BSD, bench.HSD, bench.SDQ]
+    assert all(u[0] == 8192 and u[1] == 1e3 and u[4] == 1 for u in units)
+    units, _ = bench.workload_systems("c3")
+    assert len(units) == 36 and {u[4] for u in units} == {1, 16} and {u[0] for u in units} == {8192, 16384}
+    units, mode = bench.workload_systems("sweep_n2000")
+    assert mode == "batched" and len(units) == 14
+    cfg = bench.bench_config("c3_n8192_k1e3", 2, "single")
+    assert cfg["workload"] == "c3_n8192_k1e3" and cfg["n"] == 8192 and cfg["systems"] == 3
 
 
 def test_refine_bytes_per_step_and_per_iteration():

@@ -467,7 +467,7 @@ def test_fma_probe_measures_the_pipes(M):
     assert tf32 > 5 * tf64
 
 
-@pytest.mark.parametrize("n,kappa,scale", [(200, 1e2, 1e6), (300, 1e3, 3e5)])
+@pytest.mark.parametrize("n,kappa,scale", [(200, 1e2, 1e6), (300, 1e3, 1e7)])
 def test_squeezed_factorisation_end_to_end(ctx, M, n, kappa, scale):
     """Sec. 2.1.2: A scaled so that its entries exceed fp16's range makes the
     first half-precision LU overflow; the factor check retries on the
@@ -490,3 +490,35 @@ def test_squeezed_factorisation_end_to_end(ctx, M, n, kappa, scale):
     assert OX.nbe(Au, bu, xg) <= 2 * 2.0 ** -24
     xr = OX.x_ref(Au, bu)
     assert OX.ferr(xg, xr) <= 2 * OX.ferr(ref.x, xr) + 2 * 2.0 ** -24
+
+
+def test_server_with_a_tight_budget_runs_one_request_at_a_time(ctx, M):
+    """A one-byte budget admits a request only when the server holds no device
+    memory: every later request first makes the idle slots give their
+    workspaces back.  All requests still finish, each with the result of
+    solving it alone."""
+    import time
+    srv = M.Server(ctx, hbm_budget_bytes=1, max_slots=3)
+    try:
+        cases = [(300, 1e3, HSD), (120, 1e2, SDQ), (257, 1e4, BSD), (90, 1e5, HSD)]
+        tickets = []
+        for i, (n, kappa, spec) in enumerate(cases):
+            A, B, _ = randsvd_system(n, kappa, 200 + i)
+            tickets.append((srv.submit(A, B[:, 0], spec), A, B[:, 0].copy(), spec))
+        done = {}
+        t0 = time.time()
+        while len(done) < len(tickets) and time.time() - t0 < 120:
+            for t, A, b, spec in tickets:
+                if t not in done:
+                    state, x, rep, lat = srv.poll(t, A.shape[0])
+                    if state == 2:
+                        done[t] = (x, rep)
+            time.sleep(0.005)
+        assert len(done) == len(tickets)
+        for t, A, b, spec in tickets:
+            x, rep = done[t]
+            x1, r1, s1 = ctx.solve(to_dev(A), to_dev(b), spec)
+            assert rep["call_status"] >= 0
+            same_result(A, b, _trip(M, spec)[1], x, rep, x1.cpu().numpy(), r1[0])
+    finally:
+        srv.close()
