@@ -70,7 +70,11 @@ typedef enum {
   /* 0 <= phi <= gamma*u0 and nbe(x_{i+1}) <= 2*u0 (default) */
   MSIR_CONV_COMBINED = 0,
   /* 0 <= phi <= gamma*u0 only (Eq. (1) estimate, Algorithm 4 literally) */
-  MSIR_CONV_EST = 1
+  MSIR_CONV_EST = 1,
+  /* ferr(x_{i+1}) <= u0 and nbe(x_{i+1}) <= u0 against a given exact
+   * solution (the stopping rule of the paper's experiments, Sec. 3); needs
+   * msir_params.x_ref_dev; msir_solve only */
+  MSIR_CONV_TRUE = 2
 } msir_conv;
 
 typedef enum {
@@ -91,13 +95,22 @@ typedef enum {
 typedef struct {
   int i_max;            /* maximum steps of each variant (Sec. 2.1)          */
   double rho_thresh;    /* ratio threshold of successive corrections          */
-  double kmax_frac;     /* k_max = kmax_frac * n GMRES iterations per step    */
+  double kmax_frac;     /* k_max = kmax_frac * n GMRES iterations per step;
+                           < 0: cost-aware k_max, at most |kmax_frac| * n: a
+                           GMRES stage stops once its iterations have cost
+                           about as much as the next factorisation (from the
+                           measured LU and iteration times)                   */
   double tau;           /* GMRES tolerance; <= 0 picks 1e-6 / 1e-10 by u      */
   double gamma;         /* convergence factor; <= 0 picks sqrt(n)             */
   int conv;             /* msir_conv                                          */
   int nb;               /* panel width of the LU (numeric parameter); 0: default */
   int nbo;              /* outer block width of the LU (multiple of nb); 0: default */
   int allow_escalation; /* 0: stop after GMRES-IR instead of raising u_f      */
+  const double* x_ref_dev; /* MSIR_CONV_TRUE: device pointer to the exact
+                              solution of (fl_u0(A), fl_u0(B)), n x nrhs
+                              column-major with leading dimension n; ferr is
+                              ||x - x_ref||_inf / ||x_ref||_inf; otherwise
+                              ignored (NULL) */
 } msir_params;
 
 #define MSIR_MAX_STAGES 24
@@ -240,7 +253,8 @@ msir_status msir_solve_host(msir_ctx* ctx, int n, const double* A_host, int lda,
  * (n[i] doubles) and t[i] are host arrays of device pointers / values;
  * reps: count reports (may be NULL).  Systems are grouped and their
  * refinement runs as persistent launches over groups of SMs.  Returns
- * MSIR_OK if all converged, MSIR_NOT_CONVERGED if some did not. */
+ * MSIR_OK if all converged, MSIR_NOT_CONVERGED if some did not.
+ * MSIR_CONV_TRUE is not accepted here (MSIR_ERR_INVALID). */
 msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n,
                                const double* const* A_dev, const double* const* b_dev,
                                double* const* x_dev, const msir_triple* t,
@@ -287,6 +301,14 @@ msir_status msir_server_destroy(msir_server* s);
  * kernel's fp64 work is compared with.  Blocks until the launch is done;
  * allocates nothing on the device. */
 msir_status msir_probe_fma_rate(int device, int fmt, int iters, double* tflops, double* seconds);
+
+/* Failure-handling check; the paper has no counterpart.  Runs one block
+ * into the library's bounded grid-barrier wait for a grid of two blocks, so
+ * that the wait can only run out: after limit_s seconds (0 < limit_s <= 10)
+ * it records MSIR_ERR_TIMEOUT and the kernel returns, leaving the context
+ * usable.  *status receives the recorded code (MSIR_ERR_TIMEOUT expected).
+ * Blocks until done; allocates and frees a few bytes of device memory. */
+msir_status msir_probe_wait_timeout(int device, double limit_s, int* status);
 
 /* Short text for a status code (static storage). */
 const char* msir_status_string(int status);

@@ -12,13 +12,13 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (BF16, FP16, FP32, FP64, DD, CONV_COMBINED, CONV_EST, ALG_NAMES, PREC_NAMES,
+from ._lib import (BF16, FP16, FP32, FP64, DD, CONV_COMBINED, CONV_EST, CONV_TRUE, ALG_NAMES, PREC_NAMES,
                    PREC_CODES, OK, NOT_CONVERGED, Triple, Params, Report)
 
 _L = _lib.load()
 
 __all__ = ["Context", "Server", "MsirError", "triple", "params_default", "report_to_dict",
-           "stage_string", "probe_fma_rate", "BF16", "FP16", "FP32", "FP64", "DD", "lib_path"]
+           "stage_string", "probe_fma_rate", "probe_wait_timeout", "BF16", "FP16", "FP32", "FP64", "DD", "lib_path"]
 
 
 def lib_path():
@@ -64,6 +64,14 @@ def probe_fma_rate(device=0, fmt=FP64, iters=1 << 16):
     _check(_L.msir_probe_fma_rate(device, fmt, iters, ctypes.byref(tf), ctypes.byref(sec)),
            "probe_fma_rate")
     return tf.value, sec.value
+
+
+def probe_wait_timeout(device=0, limit_s=0.2):
+    """Runs one bounded device wait that can only run out
+    (msir_probe_wait_timeout); returns the status code it recorded."""
+    st = ctypes.c_int(0)
+    _check(_L.msir_probe_wait_timeout(device, float(limit_s), ctypes.byref(st)), "probe_wait_timeout")
+    return st.value
 
 
 def stage_string(stages):

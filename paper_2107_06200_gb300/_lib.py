@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libmsir.so")
 BF16, FP16, FP32, FP64, DD = 1, 2, 3, 4, 5
 PREC_NAMES = {BF16: "bf16", FP16: "fp16", FP32: "fp32", FP64: "fp64", DD: "dd"}
 PREC_CODES = {v: k for k, v in PREC_NAMES.items()}
-CONV_COMBINED, CONV_EST = 0, 1
+CONV_COMBINED, CONV_EST, CONV_TRUE = 0, 1, 2
 ALG_SIR, ALG_SGMRES, ALG_GMRES = 0, 1, 2
 ALG_NAMES = {ALG_SIR: "SIR", ALG_SGMRES: "SGMRES-IR", ALG_GMRES: "GMRES-IR"}
 OK, NOT_CONVERGED = 0, 1
@@ -25,6 +25,7 @@ EXPORTED = [
     "msir_factors_export", "msir_factors_apply", "msir_residual", "msir_solve", "msir_solve_host",
     "msir_solve_batched", "msir_server_create", "msir_server_submit", "msir_server_poll",
     "msir_server_destroy", "msir_status_string", "msir_residual_noalloc", "msir_probe_fma_rate",
+    "msir_probe_wait_timeout",
 ]
 
 
@@ -36,7 +37,8 @@ class Params(ctypes.Structure):
     _fields_ = [("i_max", ctypes.c_int), ("rho_thresh", ctypes.c_double),
                 ("kmax_frac", ctypes.c_double), ("tau", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("conv", ctypes.c_int), ("nb", ctypes.c_int),
-                ("nbo", ctypes.c_int), ("allow_escalation", ctypes.c_int)]
+                ("nbo", ctypes.c_int), ("allow_escalation", ctypes.c_int),
+                ("x_ref_dev", ctypes.c_void_p)]
 
 
 class Stage(ctypes.Structure):
@@ -89,6 +91,7 @@ def load(path=LIB_PATH):
         "msir_status_string": [I],
         "msir_residual_noalloc": [I, P, I, I, P, P, I, P, P, P],
         "msir_probe_fma_rate": [I, I, I, pD, pD],
+        "msir_probe_wait_timeout": [I, D, pI],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

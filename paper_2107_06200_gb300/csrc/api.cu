@@ -170,6 +170,7 @@ struct Level {  // one factorisation of the current matrix
   double* inv_hi = nullptr;
   double* inv_lo = nullptr;
   int serial = 0;            // identifies this factorisation (scaled blocks follow it)
+  float t_ms = 0;            // device time of this factorisation
 };
 
 // Device workspace of one slot, sized for systems up to nmax.
@@ -277,7 +278,7 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
 }
 
 static int kcap_of(int n, double kmax_frac) {
-  int k = (int)std::ceil(kmax_frac * n);
+  int k = (int)std::ceil(std::fabs(kmax_frac) * n);
   return std::max(1, std::min(k, kMaxKcap));
 }
 
@@ -558,6 +559,8 @@ static msir_status enqueue_lu(msir_ctx* ctx, Workspace& w, int n, int u0, int l,
 
 // ------------------------------------------------------------ jobs/slots
 
+struct MatrixShare;
+
 struct Job {
   int n = 0;
   const double* A = nullptr;  // device, column-major
@@ -567,13 +570,15 @@ struct Job {
   msir_triple t{};
   msir_params p{};
   uint64_t matrix_id = 0;     // jobs with equal ids share the ingest and factors
+  const double* xref = nullptr;  // MSIR_CONV_TRUE: exact solution (device)
+  MatrixShare* share = nullptr;  // columns of one solve running on several slots
   msir_report rep{};
   int status = MSIR_OK;
   bool done = false;
   std::chrono::steady_clock::time_point t_submit, t_done;
 };
 
-enum SlotStep { S_IDLE, S_FACTOR, S_REFINE, S_FINISH };
+enum SlotStep { S_IDLE, S_FACTOR, S_REFINE, S_FINISH, S_WAIT };
 
 struct Slot {
   cudaStream_t st = nullptr;
@@ -599,7 +604,26 @@ struct Slot {
   bool factoring_initial = true;
   int nfact = 0;
   int launches = 0, refine_launches = 0;
+  double iter_ms = 0;         // measured device time per GMRES iteration (cost-aware k_max)
+  int wait_fmt = 0;           // S_WAIT: the shared level this slot waits for
   RefState state{};
+};
+
+// The columns of one multi-right-hand-side solve run on several slots at
+// once and share the matrix: A_u and the factor levels live in the
+// workspace of the slot that started first (the owner); the other slots
+// point their workspaces at those buffers and keep their own vectors,
+// Krylov basis, scaled blocks and controller.  Each level is factored once,
+// by the first slot that needs it; a slot that needs a level being factored
+// waits (S_WAIT).  Levels are factored one after another (a level is only
+// needed after the previous one), so the factorisation scratch (Ut, maps,
+// flags) stays with the factoring slot.
+struct MatrixShare {
+  Slot* owner = nullptr;
+  bool ready_to_attach = false;  // owner's ingest done (normA known)
+  double normA = 0;
+  Level lv[3];
+  int state[3] = {0, 0, 0};      // 0 none, 1 being factored, 2 ready, 3 failed
 };
 
 static int level_index(int fmt) {
@@ -662,6 +686,30 @@ static msir_status pooled_slots(msir_ctx* ctx, int k, std::vector<Slot*>& out) {
   return MSIR_OK;
 }
 
+// Cost-aware k_max (kmax_frac < 0; the paper leaves the thresholds to the
+// costs of the machine, Sec. 2.1.1): a GMRES stage stops once its iterations
+// have cost about as much as factoring at the next precision, where the
+// stages would go after GMRES-IR.  Next factorisation: the current level's
+// measured time times 1.15 (16-bit -> fp32; both LUs are bound by the same
+// panel kernel on GB300) or 10 (fp32 -> fp64, the fp64 pipe); none after fp64.
+// Per-iteration time: the previous refinement launch's measured time per
+// GMRES iteration, else a model of one iteration (two substitution chains
+// of ceil(n/64) blocks at 1.5 us, plus A_u and the factors at 6.8 TB/s).
+// The cap is never above the paper's k_max and never below 8.
+static double cost_aware_kmax(const Slot& s, int n, double kmax_paper) {
+  const Level& L = s.lv[s.cur];
+  double t_next;
+  if (L.fmt == MSIR_FP64) return kmax_paper;
+  t_next = L.t_ms * (L.fmt == MSIR_FP32 ? 10.0 : 1.15);
+  double t_it = s.iter_ms;
+  if (t_it <= 0) {
+    const double nb = std::ceil(n / 64.0);
+    t_it = 2.0 * nb * 1.5e-3 + (double)n * n * 8.0 / 6.8e9;
+  }
+  const double k = std::ceil(t_next / t_it);
+  return std::max(8.0, std::min(kmax_paper, k));
+}
+
 static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   Job& j = *s.job;
   Workspace& w = s.w;
@@ -692,8 +740,13 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   a.tsv = trsv_timers_enabled() ? w.tsv : nullptr;
   a.i_max = j.p.i_max;
   a.rho_thresh = j.p.rho_thresh;
-  a.kmax = j.p.kmax_frac * j.n;
-  a.kcap = kcap_of(j.n, j.p.kmax_frac);
+  a.kmax = std::fabs(j.p.kmax_frac) * j.n;
+  a.kcap = kcap_of(j.n, std::fabs(j.p.kmax_frac));
+  if (j.p.kmax_frac < 0) {
+    const double k = cost_aware_kmax(s, j.n, a.kmax);
+    a.kmax = k;
+    a.kcap = std::min(a.kcap, std::max(1, (int)std::ceil(k)));
+  }
   // MSIR_TEAM_K (1, 2, 4 or 8) fixes the fp64/dd substitution team size
   // (tuning only; the default rule is in team_size)
   static const int team_k = [] {
@@ -704,6 +757,7 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   a.tau = j.p.tau;
   a.gamma = j.p.gamma;
   a.conv = j.p.conv;
+  a.xref = j.p.conv == MSIR_CONV_TRUE ? j.xref : nullptr;
   a.allow_escalation = j.p.allow_escalation;
   a.u0 = j.t.u;
   (void)ctx;
@@ -832,6 +886,78 @@ static void slot_finish(Slot& s, int status) {
   cudaEventRecord(s.ev, s.st);
 }
 
+// ---------------------------------------------- shared matrix (columns)
+
+// Point slot workspace w at the owner's A_u and factor levels.
+static void ws_alias(Workspace& w, const Workspace& o) {
+  w.Au = o.Au;
+  w.ident = o.ident;
+  for (int l = 0; l < 3; ++l) {
+    w.Fbuf[l] = o.Fbuf[l];
+    w.ipiv[l] = o.ipiv[l];
+    w.perm[l] = o.perm[l];
+    w.R[l] = o.R[l];
+    w.S[l] = o.S[l];
+    w.inv32[l] = o.inv32[l];
+    w.inv_hi[l] = o.inv_hi[l];
+    w.inv_lo[l] = o.inv_lo[l];
+  }
+}
+
+// Give a workspace its own buffers back (after it pointed at an owner's).
+static void ws_restore(Workspace& w) {
+  if (w.base) ws_layout(w, w.nmax, w.kcapmax, w.G, true, w.base);
+}
+
+// Start refining with the shared level of format fmt (ready).
+static msir_status slot_use_shared_level(msir_ctx* ctx, Slot& s, int fmt) {
+  MatrixShare& sh = *s.job->share;
+  const int li = level_index(fmt);
+  s.lv[li] = sh.lv[li];
+  s.cur = li;
+  s.nfact += 1;
+  if (fmt != s.state.uf) {  // precision was raised
+    s.state.uf = fmt;
+    if (unit_roundoff_h(s.state.uf) < unit_roundoff_h(s.state.u)) s.state.u = s.state.uf;
+    if (unit_roundoff_h(s.state.ur) > unit_roundoff_h(s.state.u) * unit_roundoff_h(s.state.u))
+      s.state.ur = square_of_h(s.state.u);
+    if (!s.factoring_initial) s.state.phase = PH_ESCALATED;
+  }
+  return slot_enqueue_refine(ctx, s);
+}
+
+// Move a shared-matrix slot to the level of format fmt: use it if it is
+// ready, wait if another slot is factoring it, factor it if nobody has, or
+// go on to the next format if it failed.  With nothing left the job ends
+// (singular when even fp64 failed, else the best iterate).
+static msir_status slot_goto_shared_level(msir_ctx* ctx, Slot& s, int fmt) {
+  MatrixShare& sh = *s.job->share;
+  while (fmt) {
+    const int li = level_index(fmt);
+    if (sh.state[li] == 2 && sh.lv[li].fmt == fmt) return slot_use_shared_level(ctx, s, fmt);
+    if (sh.state[li] == 1) {
+      s.step = S_WAIT;
+      s.wait_fmt = fmt;
+      return MSIR_OK;
+    }
+    if (sh.state[li] == 0) {
+      sh.state[li] = 1;
+      return slot_enqueue_factor(ctx, s, fmt, false);
+    }
+    fmt = s.job->p.allow_escalation ? next_uf(fmt) : 0;
+  }
+  if (s.factoring_initial) {
+    slot_finish(s, MSIR_ERR_SINGULAR);
+  } else {
+    cudaMemcpyAsync(s.w.x, s.w.xbest, (size_t)s.job->n * 8, cudaMemcpyDeviceToDevice, s.st);
+    s.state.nbe = s.state.best_nbe;
+    *s.h_state = s.state;
+    slot_finish(s, MSIR_NOT_CONVERGED);
+  }
+  return MSIR_OK;
+}
+
+
 // Start a job in a slot: ingest (unless the matrix is already loaded) and
 // the first factorisation.
 static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
@@ -844,12 +970,19 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
                            std::max(s.G, s.w.G), s.st);
   if (r != MSIR_OK) return r;
   s.t_factor = s.t_refine = 0;
+  s.iter_ms = 0;
   s.nfact = 0;
   s.launches = 0;
   s.refine_launches = 0;
   memset(&j.rep, 0, sizeof(j.rep));
-  const bool same = j.matrix_id != 0 && j.matrix_id == s.loaded_id;
-  if (!same) {
+  MatrixShare* sh = j.share;
+  const bool attach = sh && sh->owner && sh->owner != &s;
+  if (attach) {
+    ws_alias(s.w, sh->owner->w);
+    s.loaded_id = 0;
+  }
+  const bool same = !attach && j.matrix_id != 0 && j.matrix_id == s.loaded_id;
+  if (!same && !attach) {
     for (auto& L : s.lv) L = Level();
     CK(ingest_matrix(j.A, j.lda, j.n, s.u0, s.w.Au, s.w.ldu, s.st));
     CK(row_stats(s.w.Au, s.w.ldu, j.n, s.u0, s.w.rowsum, nullptr, s.st));
@@ -864,8 +997,13 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
   double hs[2];
   CK(cudaMemcpyAsync(hs, s.w.scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s.st));
   CK(cudaStreamSynchronize(s.st));
-  s.normA = hs[0];
+  s.normA = attach ? sh->normA : hs[0];
   s.normb = hs[1];
+  if (sh && !sh->owner) {
+    sh->owner = &s;
+    sh->normA = s.normA;
+    sh->ready_to_attach = true;
+  }
   memset(&s.state, 0, sizeof(s.state));
   s.state.phase = PH_START;
   s.state.uf = j.t.uf;
@@ -876,6 +1014,7 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
   CK(cudaMemsetAsync(s.w.ll, 0, ll_bytes(j.n), s.st));
   s.factoring_initial = true;
   const int li = level_index(j.t.uf);
+  if (sh) return slot_goto_shared_level(ctx, s, j.t.uf);
   if (same && s.lv[li].valid && s.lv[li].fmt == j.t.uf) {
     s.cur = li;
     return slot_enqueue_refine(ctx, s);
@@ -913,11 +1052,18 @@ static void fill_report(Slot& s) {
 static bool slot_advance(msir_ctx* ctx, Slot& s) {
   Job& j = *s.job;
   float ms = 0;
+  if (s.step == S_WAIT) {  // a shared level another slot is factoring
+    if (j.share->state[level_index(s.wait_fmt)] == 1) return false;
+    msir_status r = slot_goto_shared_level(ctx, s, s.wait_fmt);
+    if (r != MSIR_OK) slot_finish(s, r);
+    return false;
+  }
   if (s.step == S_FACTOR) {
     cudaEventElapsedTime(&ms, s.e0, s.e1);
     s.t_factor += ms;
     print_lu_timers(s);
     Level& L = s.lv[s.try_level];
+    L.t_ms = ms;
     L.info = s.h_flags[0];
     L.nonfinite = s.h_flags[1];
     const int err = s.h_flags[2];
@@ -925,6 +1071,10 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
     const bool good = L.info == 0 && L.nonfinite == 0;
     if (good) {
       L.valid = true;
+      if (j.share) {
+        j.share->lv[s.try_level] = L;
+        j.share->state[s.try_level] = 2;
+      }
       s.cur = s.try_level;
       if (s.try_fmt != s.state.uf) {  // precision was raised
         s.state.uf = s.try_fmt;
@@ -947,11 +1097,12 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
       r = slot_enqueue_factor(ctx, s, s.try_fmt, true);
     } else {
       const int nx = next_uf(s.try_fmt);
+      if (j.share) j.share->state[s.try_level] = 3;  // slots waiting for it move on
       if (!nx || !j.p.allow_escalation) {
         slot_finish(s, s.try_fmt == MSIR_FP64 ? MSIR_ERR_SINGULAR : MSIR_NOT_CONVERGED);
         return false;
       }
-      r = slot_enqueue_factor(ctx, s, nx, false);
+      r = j.share ? slot_goto_shared_level(ctx, s, nx) : slot_enqueue_factor(ctx, s, nx, false);
     }
     if (r != MSIR_OK) slot_finish(s, r);
     return false;
@@ -960,6 +1111,10 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
     cudaEventElapsedTime(&ms, s.e0, s.e1);
     s.t_refine += ms;
     print_trsv_timers(s);
+    {
+      const int iters = s.h_state->total_gmres - s.state.total_gmres;
+      if (iters >= 8) s.iter_ms = ms / iters;  // the launch's time per GMRES iteration (an upper bound)
+    }
     s.state = *s.h_state;
     const int err = s.h_flags[2];
     if (err || s.state.phase == PH_ERROR) {
@@ -978,6 +1133,11 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
         return false;
       }
       s.factoring_initial = false;
+      if (j.share) {
+        msir_status r = slot_goto_shared_level(ctx, s, nx);
+        if (r != MSIR_OK) slot_finish(s, r);
+        return false;
+      }
       const int li = level_index(nx);
       if (s.lv[li].valid && s.lv[li].fmt == nx && j.matrix_id != 0) {
         s.cur = li;
@@ -1009,31 +1169,31 @@ static bool slot_advance(msir_ctx* ctx, Slot& s) {
 }
 
 // Run jobs over nslots slots until all are done (used by solve and batched).
+// A job of a shared matrix starts on a slot other than the owner's only once
+// the owner has loaded the matrix.
 static msir_status run_jobs(msir_ctx* ctx, std::vector<Job*>& jobs, std::vector<Slot*>& slots) {
   size_t next = 0, done = 0;
   const int share = (int)slots.size();
-  for (Slot* s : slots) {
-    s->loaded_id = 0;
-    if (next < jobs.size()) {
-      msir_status r = slot_start(ctx, *s, jobs[next++], share);
-      if (r != MSIR_OK) return r;
-    }
-  }
+  for (Slot* s : slots) s->loaded_id = 0;
+  auto can_start = [&](Slot* s, Job* j) {
+    return !j->share || !j->share->owner || j->share->owner == s || j->share->ready_to_attach;
+  };
   while (done < jobs.size()) {
     bool progressed = false;
     for (Slot* s : slots) {
-      if (!s->job) continue;
+      if (!s->job) {
+        if (next < jobs.size() && can_start(s, jobs[next])) {
+          msir_status r = slot_start(ctx, *s, jobs[next++], share);
+          if (r != MSIR_OK) return r;
+          progressed = true;
+        }
+        continue;
+      }
       cudaError_t q = cudaEventQuery(s->ev);
       if (q == cudaErrorNotReady) continue;
       if (q != cudaSuccess) return cuda_status(q);
-      progressed = true;
-      if (slot_advance(ctx, *s)) {
-        ++done;
-        if (next < jobs.size()) {
-          msir_status r = slot_start(ctx, *s, jobs[next++], share);
-          if (r != MSIR_OK) return r;
-        }
-      }
+      if (s->step != S_WAIT) progressed = true;
+      if (slot_advance(ctx, *s)) ++done;
     }
     if (!progressed) std::this_thread::yield();
   }
@@ -1079,8 +1239,10 @@ static msir_params resolve_params(const msir_params* p) {
 }
 
 static bool valid_params(const msir_params& p) {
-  return p.i_max >= 1 && p.rho_thresh > 0 && p.kmax_frac > 0 &&
-         (p.conv == MSIR_CONV_COMBINED || p.conv == MSIR_CONV_EST) && p.nb >= 0 && p.nbo >= 0;
+  return p.i_max >= 1 && p.rho_thresh > 0 && p.kmax_frac != 0 && std::fabs(p.kmax_frac) <= 1.0 &&
+         (p.conv == MSIR_CONV_COMBINED || p.conv == MSIR_CONV_EST ||
+          (p.conv == MSIR_CONV_TRUE && p.x_ref_dev != nullptr)) &&
+         p.nb >= 0 && p.nbo >= 0;
 }
 
 msir_status msir_create(msir_ctx** out, int device, void* stream) {
@@ -1335,6 +1497,7 @@ msir_status msir_solve(msir_ctx* ctx, int n, int nrhs, const double* A_dev, int 
   const uint64_t id = ids++;
   std::vector<Job> jobs(nrhs);
   std::vector<Job*> jp;
+  MatrixShare share;
   for (int c = 0; c < nrhs; ++c) {
     jobs[c].n = n;
     jobs[c].A = A_dev;
@@ -1344,17 +1507,29 @@ msir_status msir_solve(msir_ctx* ctx, int n, int nrhs, const double* A_dev, int 
     jobs[c].t = t;
     jobs[c].p = p;
     jobs[c].matrix_id = id;
+    jobs[c].xref = p.x_ref_dev ? p.x_ref_dev + (size_t)c * n : nullptr;
+    jobs[c].share = nrhs > 1 ? &share : nullptr;
     jp.push_back(&jobs[c]);
   }
+  // several right-hand sides: columns run on up to K slots at once, sharing
+  // the matrix and its factors (K = one per 16 SMs by default;
+  // MSIR_RHS_SLOTS overrides it for tuning)
+  const int K = nrhs > 1 ? std::min(nrhs, env_int("MSIR_RHS_SLOTS", std::max(1, ctx->num_sms / 16), 1, 64)) : 1;
   std::vector<Slot*> slots;
-  msir_status r = pooled_slots(ctx, 1, slots);
-  // order the slot's work after the caller's stream
+  msir_status r = pooled_slots(ctx, K, slots);
+  // order the slots' work after the caller's stream
   if (r == MSIR_OK) {
     cudaEventRecord(slots[0]->e0, ctx->stream);
-    cudaStreamWaitEvent(slots[0]->st, slots[0]->e0, 0);
+    for (Slot* sl : slots) cudaStreamWaitEvent(sl->st, slots[0]->e0, 0);
   }
   if (r == MSIR_OK) r = run_jobs(ctx, jp, slots);
-  if (r == MSIR_OK) cudaStreamSynchronize(slots[0]->st);
+  for (Slot* sl : slots) cudaStreamSynchronize(sl->st);
+  // slots that pointed at the owner's matrix get their own buffers back
+  for (Slot* sl : slots)
+    if (sl != share.owner) {
+      ws_restore(sl->w);
+      sl->loaded_id = 0;
+    }
   if (r != MSIR_OK) return r;
   msir_status agg = MSIR_OK;
   for (int c = 0; c < nrhs; ++c) {
@@ -1390,6 +1565,7 @@ msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n, const dou
   if (!ctx || count < 0 || (count > 0 && (!n || !A_dev || !b_dev || !x_dev || !t))) return MSIR_ERR_INVALID;
   msir_params p = resolve_params(params);
   if (!valid_params(p)) return MSIR_ERR_INVALID;
+  if (p.conv == MSIR_CONV_TRUE) return MSIR_ERR_INVALID;  // one exact solution per call only
   for (int i = 0; i < count; ++i)
     if (n[i] <= 0 || !valid_triple(t[i]) || !A_dev[i] || !b_dev[i] || !x_dev[i]) return MSIR_ERR_INVALID;
   if (count == 0) return MSIR_OK;
@@ -1682,6 +1858,7 @@ msir_status msir_server_submit(msir_server* S, int n, const double* A_host, int 
   if (!valid_triple(t)) return MSIR_ERR_INVALID;
   msir_params p = resolve_params(params);
   if (!valid_params(p)) return MSIR_ERR_INVALID;
+  if (p.conv == MSIR_CONV_TRUE) return MSIR_ERR_INVALID;  // the server does not keep device x_ref
   auto* q = new (std::nothrow) Request();
   if (!q) return MSIR_ERR_NOMEM;
   q->job.n = n;

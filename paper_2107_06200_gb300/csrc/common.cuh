@@ -230,7 +230,8 @@ __device__ __forceinline__ void record_timeout(int* err, int site, int v0, int v
 // Grid-wide barrier for a cooperative launch of G blocks.  `count` grows by
 // G per episode and is zeroed by the host before the launch.  Returns false
 // (after recording the error) on timeout or if another block failed.
-__device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned G) {
+__device__ __forceinline__ bool grid_barrier_for(unsigned* count, int* err, unsigned G,
+                                                 unsigned long long limit_ns) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -244,7 +245,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned
       __nanosleep(20);
       if ((++spins & 63u) == 0u) {
         if (ld_volatile_i32(err) != 0) { ok = 0; break; }
-        if (gtimer() - t0 > kWaitTimeoutNs) {
+        if (gtimer() - t0 > limit_ns) {
           record_timeout(err, 1, (int)ld_acquire_u32(count), (int)target, (int)G);
           ok = 0;
           break;
@@ -255,6 +256,9 @@ __device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned
   }
   __syncthreads();
   return s_ok != 0;
+}
+__device__ __forceinline__ bool grid_barrier(unsigned* count, int* err, unsigned G) {
+  return grid_barrier_for(count, err, G, kWaitTimeoutNs);
 }
 
 __device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {

@@ -24,6 +24,7 @@
 //                       factors (the bf16/fp16 update is in lu_tc.cu).
 #include <cooperative_groups.h>
 #include <climits>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -95,8 +96,6 @@ __device__ __forceinline__ void warp_argmax(float& v, int& i) {
 #define PT_BEGIN(id) unsigned long long _t##id = (a.tdbg && rank == 0 && tid == 0) ? gtimer() : 0
 #define PT_END(id) \
   if (a.tdbg && rank == 0 && tid == 0) s_tacc[id] += gtimer() - _t##id
-
-constexpr int kInnerRows = 8;   // rows per warp step of the inner update
 
 template <typename F>
 __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) {
@@ -420,7 +419,11 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
     PT_BEGIN(6);
 
     // inner update of my panel rows below the diagonal block:
-    // A[kk+gi][kk+w+c] <- fl(A - sum_mm L[gi][mm] U12[mm][c]), L from P
+    // A[kk+gi][kk+w+c] <- fl(A - sum_mm L[gi][mm] U12[mm][c]), L from P, the
+    // sum an ascending fused multiply-add chain from zero per element.
+    // Register tiles of 4 rows x CW columns per thread (CW = 4, or 2 for
+    // fp64; a warp covers 8 CW rows x 16 columns): 4 + CW shared-memory
+    // loads per 4 CW multiply-adds.
     if (nright > 0) {
       for (int idx = tid; idx < w * nright; idx += blockDim.x) {
         const int i = idx / nright, c = idx % nright;
@@ -428,28 +431,56 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
       }
       __syncthreads();
       const int lfirst = max(0, w - my0);  // first local row with gi >= w
-      for (int c0 = 0; c0 < nright; c0 += 32) {
-        const int c = c0 + lane;
-        for (int l0 = lfirst + warp * kInnerRows; l0 < nloc; l0 += NW * kInnerRows) {
-          T acc[kInnerRows];
+      const int nrow = nloc - lfirst;
+      constexpr int CW = sizeof(T) == 8 ? 2 : 4;
+      constexpr int CG = 16 / CW;              // column groups of a warp
+      constexpr int WR = 32 / CG * 4;          // rows of a warp tile
+      const int tiles_r = (nrow + WR - 1) / WR, tiles_c = (nright + 15) / 16;
+      const int ri = lane / CG, ci = lane % CG;
+      for (int t = warp; t < tiles_r * tiles_c; t += NW) {
+        const int r0 = lfirst + (t / tiles_c) * WR + ri * 4;
+        const int c0 = (t % tiles_c) * 16 + ci * CW;
+        int lr[4], uc[CW];
 #pragma unroll
-          for (int r = 0; r < kInnerRows; ++r) acc[r] = (T)0;
-          for (int mm = 0; mm < w; ++mm) {
-            const T u = c < nright ? U12[mm * W + c] : (T)0;
+        for (int r = 0; r < 4; ++r) lr[r] = min(r0 + r, nloc - 1) * ldp;  // rows past nloc: not stored
 #pragma unroll
-            for (int r = 0; r < kInnerRows; ++r) {
-              const T l = (l0 + r < nloc) ? P[(l0 + r) * ldp + mm] : (T)0;
-              acc[r] = fma_rn(l, u, acc[r]);
-            }
-          }
-          if (c < nright) {
+        for (int q = 0; q < CW; ++q) uc[q] = min(c0 + q, nright - 1);     // columns past nright: not stored
+        T acc[4][CW];
 #pragma unroll
-            for (int r = 0; r < kInnerRows; ++r) {
-              if (l0 + r < nloc) {
-                F* dst = A + (size_t)(kk + my0 + l0 + r) * lda + kk + w + c;
-                *dst = store_rn<F>(sub_rn((T)to_f(*dst), acc[r]));
-              }
-            }
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+          for (int q = 0; q < CW; ++q) acc[r][q] = (T)0;
+#pragma unroll 4
+        for (int mm = 0; mm < w; ++mm) {
+          T l[4], u[CW];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) l[r] = P[lr[r] + mm];
+#pragma unroll
+          for (int q = 0; q < CW; ++q) u[q] = U12[mm * W + uc[q]];
+#pragma unroll
+          for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < CW; ++q) acc[r][q] = fma_rn(l[r], u[q], acc[r][q]);
+        }
+        // C read and written as one CW-value vector per row (8 or 16 bytes)
+        // when kk + w is a multiple of CW (rows start on 128-byte boundaries
+        // and c0 is a multiple of CW, so the vector is then aligned)
+        using Vec = typename std::conditional<sizeof(F) * CW == 8, uint2, uint4>::type;
+        const bool vec_ok = ((kk + w) % CW) == 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+          if (r0 + r >= nloc) continue;
+          F* dst = A + (size_t)(kk + my0 + r0 + r) * lda + kk + w + c0;
+          if (vec_ok && c0 + CW <= nright) {
+            Vec raw = *reinterpret_cast<const Vec*>(dst);
+            F* e = reinterpret_cast<F*>(&raw);
+#pragma unroll
+            for (int q = 0; q < CW; ++q) e[q] = store_rn<F>(sub_rn((T)to_f(e[q]), acc[r][q]));
+            *reinterpret_cast<Vec*>(dst) = raw;
+          } else {
+#pragma unroll
+            for (int q = 0; q < CW; ++q)
+              if (c0 + q < nright) dst[q] = store_rn<F>(sub_rn((T)to_f(dst[q]), acc[r][q]));
           }
         }
       }

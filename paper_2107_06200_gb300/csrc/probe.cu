@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/msir.h"
+#include "common.cuh"
 
 namespace {
 
@@ -69,7 +70,44 @@ msir_status run_probe(int device, int iters, double* tflops, double* seconds) {
   return out;
 }
 
+// One block enters the library's grid barrier for a grid of two blocks, so
+// the second arrival never comes: the barrier's bounded wait runs out after
+// limit_ns, records MSIR_ERR_TIMEOUT in err and returns, and so does the
+// kernel.
+__global__ void wait_timeout_probe_kernel(unsigned* count, int* err, unsigned long long limit_ns) {
+  (void)msir::grid_barrier_for(count, err, 2u, limit_ns);
+}
+
 }  // namespace
+
+extern "C" msir_status msir_probe_wait_timeout(int device, double limit_s, int* status) {
+  if (!status || !(limit_s > 0.0) || limit_s > 10.0) return MSIR_ERR_INVALID;
+  if (cudaSetDevice(device) != cudaSuccess) return MSIR_ERR_CUDA;
+  unsigned* count = nullptr;
+  int* err = nullptr;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return MSIR_ERR_CUDA;
+  msir_status out = MSIR_OK;
+  if (cudaMallocAsync((void**)&count, 64, st) != cudaSuccess ||
+      cudaMallocAsync((void**)&err, 32 * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(count, 0, 64, st) != cudaSuccess ||
+      cudaMemsetAsync(err, 0, 32 * sizeof(int), st) != cudaSuccess) {
+    out = MSIR_ERR_CUDA;
+  } else {
+    wait_timeout_probe_kernel<<<1, 32, 0, st>>>(count, err, (unsigned long long)(limit_s * 1e9));
+    int h = 0;
+    if (cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      out = MSIR_ERR_CUDA;
+    else
+      *status = h;
+  }
+  if (count) cudaFreeAsync(count, st);
+  if (err) cudaFreeAsync(err, st);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  return out;
+}
 
 extern "C" msir_status msir_probe_fma_rate(int device, int fmt, int iters, double* tflops,
                                            double* seconds) {

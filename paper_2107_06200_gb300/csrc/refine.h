@@ -113,6 +113,7 @@ struct RefineArgs {
   double tau;              // <= 0: by u
   double gamma;
   int conv;
+  const double* xref;      // MSIR_CONV_TRUE: exact solution (natural order), else nullptr
   int allow_escalation;
   int u0;
   // MODE_APPLY: arith / store formats and input/output (natural order)

@@ -389,6 +389,7 @@ struct AccF {
   static __device__ __forceinline__ void tile(const RefineArgs& a, int n, int row, int col, Tm (&v)[N]) {
     load_seg<float, float, N>(a.M32, a.ldf, n, row, col, v);
   }
+  static __device__ __forceinline__ const Tm* mat(const RefineArgs& a) { return a.M32; }
   static __device__ __forceinline__ A tfma(Tm m, V y, A acc) { return ff_fma(m, y, acc); }
   static __device__ __forceinline__ unsigned word(V v, int) { return __float_as_uint(v); }
   static __device__ __forceinline__ V unword(const unsigned* w) { return __uint_as_float(w[0]); }
@@ -421,6 +422,7 @@ struct AccD {
   static __device__ __forceinline__ void tile(const RefineArgs& a, int n, int row, int col, Tm (&v)[N]) {
     load_seg<double, double, N>(a.M64, a.ldf, n, row, col, v);
   }
+  static __device__ __forceinline__ const Tm* mat(const RefineArgs& a) { return a.M64; }
   static __device__ __forceinline__ A tfma(Tm m, V y, A acc) { return __fma_rn(m, y, acc); }
   static __device__ __forceinline__ unsigned word(V v, int k) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(v);
@@ -681,6 +683,21 @@ __device__ __noinline__ bool build_scaled(Cx& cx, const RefineArgs& a, bool dd) 
   return grid_barrier(a.bar, a.err, cx.G);
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only) with zero fill past
+// `bytes` (0..16); groups of them are committed and waited for per thread.
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(sa), "l"(gsrc), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Depth of the ring of scaled-block tiles that fp32 / fp64 substitutions
+// stream through shared memory (the scaled-block staging area, idle during
+// the solves); a member's tile is R x 64 values.
+constexpr int kTileRing = 3;
+
 // One triangular solve (LOWER: L y = c, unit diagonal; else U z = y) over
 // all blocks of this CTA's team, with the block rows scaled beforehand:
 // y_b = w_b - sum_j M_bj y_j, w_b = inv(D_b) c_b (the backward solve the
@@ -772,41 +789,100 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
     // dependencies in the order they become available
     const int ndep = LOWER ? b : cx.nblk - 1 - b;
     typename ACC::A acc = ACC::azero();
+    // fp32/fp64 tiles of at most a sixth of the staging area stream through a
+    // ring in shared memory; wider ones (fp64 without teams) and dd tiles
+    // are loaded into registers
+    constexpr bool kRing = W <= 2 && (size_t)R * kBlk * sizeof(Tm) * kTileRing <= (size_t)kScaledSmem;
     if (ok && ndep > 0 && act) {
-      // fp32/fp64: tile and payload loads one dependency ahead (double
-      // buffer); dd: the next tile is loaded after the current one is used
-      // (its products, not the loads, bound the dd solve)
-      constexpr bool kDouble = W <= 2;
-      Tm tc[NC], tn[kDouble ? NC : 1];
-      LLRaw<W> pc, pn;
-      int jb = LOWER ? 0 : cx.nblk - 1;
-      ACC::template tile<NC>(a, n, row, jb * kBlk + seg * NC, tc);
-      ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
-      for (int t = 0; t < ndep; ++t) {
-        const int jn = LOWER ? jb + 1 : jb - 1;
-        const bool more = t + 1 < ndep;
-        if (kDouble && more) {
-          ACC::template tile<NC>(a, n, row, jn * kBlk + seg * NC, *(Tm(*)[NC])tn);
-          ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
-        }
-        if (!ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err,
-                              (tri << 24) | (b << 12) | jb)) {
-          ok = false;
-          break;
-        }
-        const V* ys = stage + seg * NC;
+      if constexpr (kRing) {
+        // fp32/fp64: the tiles stream through a ring in shared memory,
+        // kTileRing - 1 dependencies ahead (asynchronous copies; each thread
+        // copies and later reads only its own chunks, so no barrier), and the
+        // hand-off words are loaded one dependency ahead
+        constexpr int EPC = 16 / (int)sizeof(Tm);  // values per 16-byte chunk
+        constexpr int NCH = NC / EPC;              // chunks per thread and tile
+        Tm* ring = (Tm*)cx.ssm;                    // [kTileRing][NCH][NACT][EPC]
+        const Tm* Mat = ACC::mat(a);
+        auto issue = [&](int t) {
+          if (t < ndep) {
+            const int jt = LOWER ? t : cx.nblk - 1 - t;
+            Tm* slot = ring + (size_t)(t % kTileRing) * NCH * NACT * EPC;
 #pragma unroll
-        for (int k = 0; k < NC; ++k) acc = ACC::tfma(tc[k], ys[k], acc);
-        if (!more) break;
-        if (kDouble) {
+            for (int c = 0; c < NCH; ++c) {
+              const int col = jt * kBlk + seg * NC + c * EPC;
+              const int valid = row < n ? max(0, min(EPC, n - col)) : 0;
+              const Tm* src = Mat + (valid > 0 ? (size_t)row * a.ldf + col : 0);
+              cp_async16(slot + ((size_t)c * NACT + cx.tid) * EPC, src, valid * (int)sizeof(Tm));
+            }
+          }
+          cp_async_commit();
+        };
 #pragma unroll
-          for (int k = 0; k < NC; ++k) tc[k] = tn[kDouble ? k : 0];
+        for (int t = 0; t < kTileRing - 1; ++t) issue(t);
+        LLRaw<W> pc, pn;
+        int jb = LOWER ? 0 : cx.nblk - 1;
+        ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
+        for (int t = 0; t < ndep; ++t) {
+          const int jn = LOWER ? jb + 1 : jb - 1;
+          const bool more = t + 1 < ndep;
+          issue(t + kTileRing - 1);
+          if (more) ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
+          cp_async_wait<kTileRing - 1>();  // this thread's copies of tile t are done
+          Tm tc[NC];
+          const Tm* slot = ring + (size_t)(t % kTileRing) * NCH * NACT * EPC;
+#pragma unroll
+          for (int c = 0; c < NCH; ++c)
+#pragma unroll
+            for (int e = 0; e < EPC; ++e) tc[c * EPC + e] = slot[((size_t)c * NACT + cx.tid) * EPC + e];
+          if (!ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err,
+                                (tri << 24) | (b << 12) | jb)) {
+            ok = false;
+            break;
+          }
+          const V* ys = stage + seg * NC;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) acc = ACC::tfma(tc[k], ys[k], acc);
+          if (!more) break;
           pc = pn;
-        } else {
-          ACC::template tile<NC>(a, n, row, jn * kBlk + seg * NC, tc);
-          ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pc);
+          jb = jn;
         }
-        jb = jn;
+        cp_async_wait<0>();  // no copy outlives the solve (the ring is reused)
+      } else {
+        // fp64 without teams: tile and payload loads one dependency ahead
+        // (double buffer); dd: the next tile is loaded after the current
+        // one is used (its products, not the loads, bound the dd solve)
+        constexpr bool kDouble = W <= 2;
+        Tm tc[NC], tn[kDouble ? NC : 1];
+        LLRaw<W> pc, pn;
+        int jb = LOWER ? 0 : cx.nblk - 1;
+        ACC::template tile<NC>(a, n, row, jb * kBlk + seg * NC, tc);
+        ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
+        for (int t = 0; t < ndep; ++t) {
+          const int jn = LOWER ? jb + 1 : jb - 1;
+          const bool more = t + 1 < ndep;
+          if (kDouble && more) {
+            ACC::template tile<NC>(a, n, row, jn * kBlk + seg * NC, *(Tm(*)[NC])tn);
+            ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
+          }
+          if (!ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err,
+                                (tri << 24) | (b << 12) | jb)) {
+            ok = false;
+            break;
+          }
+          const V* ys = stage + seg * NC;
+#pragma unroll
+          for (int k = 0; k < NC; ++k) acc = ACC::tfma(tc[k], ys[k], acc);
+          if (!more) break;
+          if (kDouble) {
+#pragma unroll
+            for (int k = 0; k < NC; ++k) tc[k] = tn[kDouble ? k : 0];
+            pc = pn;
+          } else {
+            ACC::template tile<NC>(a, n, row, jn * kBlk + seg * NC, tc);
+            ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pc);
+          }
+          jb = jn;
+        }
       }
     }
     if (ts && cx.tid == 0 && member == 0) ts[1] = gtimer();
@@ -920,10 +996,12 @@ static __device__ __forceinline__ double cscale(const RefineArgs& a, int col) {
 
 // r_p[i] = b[perm[i]] - A[perm[i]] x in ur; rows are spread over every warp
 // of the grid (the fp64 work needs all SMs).  Returns (via grid reduction)
-// s = ||r||_inf and ||x||_inf.  The caller has made x complete (barrier).
+// s = ||r||_inf and ||x||_inf, and, with an exact solution given (MSIR_CONV_TRUE),
+// ferr = ||x - x_ref||_inf / ||x_ref||_inf.  The caller has made x complete
+// (barrier).
 template <typename A0>
 __device__ bool residual(Cx& cx, const RefineArgs& a, const double* x, int ur, double& s,
-                         double& xnorm) {
+                         double& xnorm, double* ferr = nullptr) {
   PhaseTimer pt(cx, 0);
   const A0* A = (const A0*)a.A;
   double mr = 0.0, mx = 0.0;
@@ -943,15 +1021,35 @@ __device__ bool residual(Cx& cx, const RefineArgs& a, const double* x, int ur, d
       mr = nanmax(mr, fabs(r));
     }
   }
-  for (int i = cx.cta * kRefThreads + cx.tid; i < cx.n; i += cx.G * kRefThreads)
-    mx = nanmax(mx, fabs(__ldcg(x + i)));
+  double mf = 0.0, mref = 0.0;
+  for (int i = cx.cta * kRefThreads + cx.tid; i < cx.n; i += cx.G * kRefThreads) {
+    const double xi = __ldcg(x + i);
+    mx = nanmax(mx, fabs(xi));
+    if (a.xref) {
+      const double ri = __ldg(a.xref + i);
+      mf = nanmax(mf, fabs(__dsub_rn(xi, ri)));
+      mref = nanmax(mref, fabs(ri));
+    }
+  }
   mr = cta_reduce(mr, 1, cx.tid);
   mx = cta_reduce(mx, 1, cx.tid);
+  if (a.xref) {
+    mf = cta_reduce(mf, 1, cx.tid);
+    mref = cta_reduce(mref, 1, cx.tid);
+    double v[4] = {mr, mx, mf, mref};
+    const int op[4] = {1, 1, 1, 1};
+    if (!grid_reduce<4>(cx, a, v, op)) return false;
+    s = v[0];
+    xnorm = v[1];
+    if (ferr) *ferr = v[3] > 0.0 ? v[2] / v[3] : v[2];
+    return true;
+  }
   double v[2] = {mr, mx};
   const int op[2] = {1, 1};
   if (!grid_reduce<2>(cx, a, v, op)) return false;
   s = v[0];
   xnorm = v[1];
+  if (ferr) *ferr = 0.0;
   return true;
 }
 
@@ -1400,7 +1498,7 @@ static __device__ void rep_new_stage(const RefineArgs& a, RefState& S) {
 // with the readings listed in the library documentation).  Thread 0 only.
 // Returns 0 continue, 1 converged, 2 switch (reset = phi > phi_0).
 static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, double dnorm, double xnorm,
-                               double nbe, int kg, int* reset) {
+                               double nbe, double ferr, int kg, int* reset) {
   const double delta = s * dnorm;
   const double z = xnorm > 0.0 ? delta / xnorm : __longlong_as_double(0x7ff0000000000000ll);
   const double v = isfinite(S.delta_prev) ? delta / S.delta_prev : 0.0;
@@ -1415,6 +1513,7 @@ static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, doubl
   const double thr = gamma * uu0;
   bool conv = phi >= 0.0 && phi <= thr;
   if (a.conv == MSIR_CONV_COMBINED) conv = conv && nbe <= 2.0 * uu0;
+  if (a.conv == MSIR_CONV_TRUE) conv = ferr <= uu0 && nbe <= uu0;
   *reset = 0;
   if (conv) return 1;
   const bool trig = z <= unit_roundoff(S.u) || v >= a.rho_thresh || S.it >= a.i_max ||
@@ -1613,7 +1712,8 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
       const double s_old = s, xnorm_old = mx;
       FOR_MY_ROWS(cx, i) a.x[i] = a.xn[i];
       if (!(ok = grid_barrier(a.bar, a.err, cx.G))) break;
-      if (!(ok = residual<A0>(cx, a, a.x, ur, s, xnorm))) break;
+      double ferr = 0.0;
+      if (!(ok = residual<A0>(cx, a, a.x, ur, s, xnorm, &ferr))) break;
       nbe = s / (a.normA * xnorm + a.normb);
       const bool better = nbe < S.best_nbe;
       // every thread has read S before thread 0 updates it (shared memory)
@@ -1630,7 +1730,7 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
           g.steps += 1;
         }
         int rs = 0;
-        s_act = ctl_step(S, a, s_old, md, xnorm_old, nbe, kg, &rs);
+        s_act = ctl_step(S, a, s_old, md, xnorm_old, nbe, ferr, kg, &rs);
         s_reset = rs;
         s_alg = S.alg;
         S.nbe = nbe;

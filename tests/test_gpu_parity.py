@@ -294,14 +294,41 @@ def test_msir_full_size_properties(ctx, M, n, kappa, spec, graded):
     assert rep["stages"][0]["alg"] == "SIR"
 
 
-def test_multi_rhs_columns_equal_single_solves(ctx, M):
-    n, nrhs = 300, 4
-    A, B, _ = randsvd_system(n, 1e4, 8, nrhs=nrhs)
-    X, reps, st = ctx.solve(to_dev(A), to_dev(B), HSD)
+@pytest.mark.parametrize("n,nrhs,kappa,spec", [(300, 4, 1e4, HSD), (2000, 16, 1e4, HSD), (700, 16, 1e9, SDQ),
+                                               (500, 16, 1e6, BSD)])
+def test_multi_rhs_columns_match_single_solves(ctx, M, n, nrhs, kappa, spec):
+    """Several right-hand sides run as concurrent columns that share the
+    matrix and its factor levels (each level factored once): every column
+    gives the result of solving it alone (same stages, steps and cged; nbe
+    <= 2 u0; forward errors within 2x of each other)."""
+    A, B, _ = randsvd_system(n, kappa, 8, nrhs=nrhs)
+    X, reps, st = ctx.solve(to_dev(A), to_dev(B), spec)
+    Xh = X.cpu().numpy()
+    u0 = _trip(M, spec)[1]
     for j in range(nrhs):
-        xj, rj, sj = ctx.solve(to_dev(A), to_dev(B[:, j].copy()), HSD)
-        assert np.array_equal(X[:, j].cpu().numpy(), xj.cpu().numpy())
-        assert reps[j]["steps"] == rj[0]["steps"]
+        xj, rj, sj = ctx.solve(to_dev(A), to_dev(B[:, j].copy()), spec)
+        same_result(A, B[:, j], u0, Xh[:, j], reps[j], xj.cpu().numpy(), rj[0])
+
+
+def test_multi_rhs_n8192_sixteen_columns(ctx, M):
+    """The large configuration with 16 right-hand sides (n = 8192, kappa =
+    1e3, (half, single, double)): every column converges to nbe <= 2 u0 (row
+    sums in fp64 on the host) with the stage sequence of its single solve."""
+    n, nrhs = 8192, 16
+    A, B, _ = randsvd_system(n, 1e3, 0, nrhs=nrhs, device="cuda:0")
+    Ad, Bd = to_dev(A), to_dev(B)
+    X, reps, st = ctx.solve(Ad, Bd, HSD)
+    assert st == M.OK
+    Au = OF.fl(A, OF.FP32).astype(np.float64)
+    normA = np.max(np.sum(np.abs(Au), 1))
+    Xh = X.cpu().numpy()
+    for j in (0, 5, 15):
+        bu = OF.fl(B[:, j], OF.FP32).astype(np.float64)
+        r = bu - Au @ Xh[:, j]
+        nbe = np.max(np.abs(r)) / (normA * np.max(np.abs(Xh[:, j])) + np.max(np.abs(bu)))
+        assert reps[j]["cged"] and nbe <= 2 * 2.0 ** -24
+        xj, rj, sj = ctx.solve(Ad, Bd[:, j].contiguous(), HSD)
+        assert [g[:5] for g in stages_of(reps[j])] == [g[:5] for g in stages_of(rj[0])]
 
 
 def test_batched_equals_single_solves(ctx, M):
@@ -522,3 +549,51 @@ def test_server_with_a_tight_budget_runs_one_request_at_a_time(ctx, M):
             same_result(A, b, _trip(M, spec)[1], x, rep, x1.cpu().numpy(), r1[0])
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("n,kappa,spec", [(100, 1e2, HSD), (100, 1e4, HSD), (150, 1e9, SDQ), (120, 1e6, HDQ)])
+def test_true_convergence_mode(ctx, M, n, kappa, spec):
+    """The stopping rule of the paper's experiments (Sec. 3): converged when
+    ferr(x_{i+1}) <= u0 and nbe(x_{i+1}) <= u0 against the exact solution of
+    (A_u, b_u), which both sides are given.  Same stage sequence as the
+    oracle in the same mode (on the GPU's factors), and the stopping
+    condition holds at the returned x."""
+    A, B, _ = randsvd_system(n, kappa, 0)
+    b = B[:, 0].copy()
+    trip = _trip(M, spec)
+    u0 = trip[1]
+    uu = OF.u_of(u0)
+    Au, bu = OF.fl(A, u0).astype(np.float64), OF.fl(b, u0).astype(np.float64)
+    xr = OX.x_ref(Au, bu)
+    xr_dev = to_dev(xr)
+    p = M.params_default(conv=M.CONV_TRUE, x_ref_dev=xr_dev.data_ptr())
+    x, reps, st = ctx.solve(to_dev(A), to_dev(b), spec, p)
+    rep = reps[0]
+    hook = _hook(ctx, A, u0, trip[0], rep["nb"], rep["nbo"])
+    ref = OM.msir(A, b, trip, OM.Params(conv=OM.CONV_TRUE, nb=rep["nb"], nbo=rep["nbo"]), x_ref=xr,
+                  factor_hook=hook)
+    print(f"TRUE n={n} kappa={kappa:g} {spec}: GPU '{rep['steps']}' oracle '{OM.stage_string(ref.stages)}'")
+    assert_stage_parity(stages_of(rep), stages_oracle(ref))
+    assert bool(rep["cged"]) == bool(ref.cged)
+    if rep["cged"]:
+        xg = x.cpu().numpy()
+        assert OX.ferr(xg, xr) <= uu and OX.nbe(Au, bu, xg) <= uu
+
+
+def test_true_mode_needs_an_exact_solution(ctx, M):
+    A, B, _ = randsvd_system(40, 10.0, 1)
+    with pytest.raises(M.MsirError):
+        ctx.solve(to_dev(A), to_dev(B[:, 0].copy()), HSD, M.params_default(conv=M.CONV_TRUE))
+
+
+def test_bounded_wait_runs_out_and_the_context_survives(ctx, M):
+    """A device wait that nothing completes (the library's grid barrier for a
+    grid of two, entered by one block) runs out after its limit and reports
+    MSIR_ERR_TIMEOUT; the GPU keeps working: a solve right after succeeds."""
+    import time
+    t0 = time.time()
+    assert M.probe_wait_timeout(0, 0.2) == -4
+    assert 0.15 <= time.time() - t0 < 30
+    A, B, _ = randsvd_system(64, 10.0, 3)
+    x, reps, st = ctx.solve(to_dev(A), to_dev(B[:, 0].copy()), HSD)
+    assert st == M.OK and reps[0]["cged"]

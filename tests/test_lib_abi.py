@@ -44,8 +44,8 @@ def test_library_exports_every_declared_symbol(lib):
 def test_struct_layouts_match_header():
     from paper_2107_06200_gb300._lib import Params, Report, Stage, Triple
     assert ctypes.sizeof(Triple) == 12
-    # int, pad, 4 doubles, 4 ints
-    assert ctypes.sizeof(Params) == 4 + 4 + 8 * 4 + 4 * 4
+    # int, pad, 4 doubles, 4 ints, a pointer
+    assert ctypes.sizeof(Params) == 4 + 4 + 8 * 4 + 4 * 4 + 8
     assert ctypes.sizeof(Stage) == 6 * 4 + 48 * 4
     assert ctypes.sizeof(Report) == 10 * 4 + 12 * 8 + 2 * 4 + 24 * ctypes.sizeof(Stage)
 

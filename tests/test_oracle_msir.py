@@ -235,3 +235,33 @@ def test_squeezed_run_converges_and_records_scaling():
     bu = F.fl(b, F.FP32).astype(np.float64)
     from oracle import metrics as X
     assert X.nbe(Au, bu, res.x) <= 2 * 2.0 ** -24
+
+
+def test_true_mode_uses_the_exact_errors_only():
+    """Sec. 3's stopping rule (ferr <= u0 and nbe <= u0 of x_{i+1}): a tiny
+    estimate phi does not converge while ferr is above u0, and a step with
+    both exact errors at u0 converges whatever phi says."""
+    u0 = 2.0 ** -24
+    c = _ctl(conv=M.CONV_TRUE)
+    a = c.step(1.0, 1e-12, 1.0, F.FP32, nbe_new=u0 / 2, ferr_new=4 * u0)[0]
+    assert a != "converged"
+    c = _ctl(conv=M.CONV_TRUE)
+    a = c.step(1.0, 0.3, 1.0, F.FP32, nbe_new=u0, ferr_new=u0)[0]
+    assert a == "converged"
+    a = _ctl(conv=M.CONV_TRUE).step(1.0, 0.3, 1.0, F.FP32, nbe_new=1.5 * u0, ferr_new=0.0)[0]
+    assert a != "converged"
+
+
+def test_true_mode_run_meets_its_criterion():
+    n = 100
+    A, B, _ = randsvd_system(n, 1e2, 0)
+    b = B[:, 0]
+    Au = F.fl(A, F.FP32).astype(np.float64)
+    bu = F.fl(b, F.FP32).astype(np.float64)
+    xr = X.x_ref(Au, bu)
+    res = M.msir(A, b, HSD, M.Params(conv=M.CONV_TRUE), x_ref=xr)
+    assert res.cged
+    assert X.ferr(res.x, xr) <= 2.0 ** -24 and X.nbe(Au, bu, res.x) <= 2.0 ** -24
+    comb = M.msir(A, b, HSD)
+    # the exact test can only stop later than (or with) the computable one here
+    assert sum(s.steps for s in res.stages) >= sum(s.steps for s in comb.stages) - 1
