@@ -328,11 +328,15 @@ def run_cpu_baseline(units, max_seconds=25.0, n_sample=1024):
                       "until ~%.0f s: " % (n_sample, max_seconds) + "; ".join(done)}
 
 
-# Small single solves for profiler captures: (n, kappa, triple, graded, repeats)
+# Small single solves for profiler captures: (n, kappa, triple, graded,
+# repeats, kmax_frac)
 PROFILE_CASES = {
-    "refine_n2000_k1e6_hsd": (2000, 1e6, "fp16,fp32,fp64", False, 2),
-    "refine_n2000_k1e10_sdq": (2000, 1e10, "fp32,fp64,dd", False, 2),
-    "lu_n8192_fp16": (8192, 1e3, "fp16,fp32,fp64", False, 2),
+    "refine_n2000_k1e6_hsd": (2000, 1e6, "fp16,fp32,fp64", False, 2, 0.1),
+    "refine_n2000_k1e10_sdq": (2000, 1e10, "fp32,fp64,dd", False, 2, 0.1),
+    "lu_n8192_fp16": (8192, 1e3, "fp16,fp32,fp64", False, 2, 0.1),
+    # the default workload's dominant system (bf16 factors, GMRES stages to
+    # the cap) at half the size and a fifth of the cap: a launch of ~0.1 s
+    "refine_n4096_k1e3_bsd": (4096, 1e3, "bf16,fp32,fp64", False, 2, 0.02),
 }
 
 
@@ -375,9 +379,16 @@ def run_serving(server, systems, times, picks, duration_s, byte_cap, clock=time.
                    "cged": None, "t_done": None}
             need = request_bytes(n)
             if byte_cap is None or used + need <= byte_cap:
-                pending[server.submit(A, b, spec)] = rec
-                rec["status"] = "pending"
-                used += need
+                try:
+                    tk = server.submit(A, b, spec)
+                except Exception as exc:  # the server's own back-pressure (MSIR_ERR_NOMEM)
+                    if getattr(exc, "code", None) != -2:
+                        raise
+                    tk = None
+                if tk is not None:
+                    pending[tk] = rec
+                    rec["status"] = "pending"
+                    used += need
             records.append(rec)
             i += 1
         for tk in list(pending):
@@ -436,9 +447,10 @@ def run_serve_bench(args):
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.9 * free)
     # the server admits by device footprint inside `budget`; queued requests
-    # wait in host memory, which the client caps (an overloaded open-loop
-    # queue would otherwise grow without bound)
-    host_cap = int(args.host_queue_gb * 2 ** 30)
+    # wait in host memory, which the server itself bounds (a submission
+    # beyond its limit is refused and counted as rejected); the client sets
+    # no cap unless asked to
+    host_cap = int(args.host_queue_gb * 2 ** 30) if args.host_queue_gb > 0 else None
     srv = M.Server(ctx, hbm_budget_bytes=budget, max_slots=args.max_slots)
     try:
         recs = run_serving(srv, systems, times, picks, args.duration, byte_cap=host_cap)
@@ -476,14 +488,14 @@ def run_profile_case(name):
     import torch
     import paper_2107_06200_gb300 as M
     from synth import randsvd_system
-    n, kappa, spec, graded, reps = PROFILE_CASES[name]
-    A, B, _ = randsvd_system(n, kappa, 0, graded=graded)
+    n, kappa, spec, graded, reps, kf = PROFILE_CASES[name]
+    A, B, _ = randsvd_system(n, kappa, 0, graded=graded, device="cuda:0" if n >= 4096 else None)
     dev = torch.device("cuda", 0)
     ctx = M.Context(0)
     At = torch.from_numpy(A).to(dev)
     bt = torch.from_numpy(B[:, 0].copy()).to(dev)
     for _ in range(reps):
-        x, r, st = ctx.solve(At, bt, spec)
+        x, r, st = ctx.solve(At, bt, spec, M.params_default(kmax_frac=kf))
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": name, "status": st, "cged": r[0]["cged"],
                       "stages": M.stage_string(r[0]["stages"]), "t_factor_ms": r[0]["t_factor_ms"],
@@ -500,6 +512,8 @@ def main():
                     choices=["c3_n8192_k1e3", "c3_n8192", "c3", "sweep_n2000"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true", help="skip the operator bandwidth measurement")
+    ap.add_argument("--no-cost-aware", action="store_true",
+                    help="skip the extra pass with the cost-aware k_max")
     ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
                     help="run one untimed solve of a named small case (for ncu captures) and exit")
     ap.add_argument("--sequential", action="store_true",
@@ -513,8 +527,8 @@ def main():
     ap.add_argument("--nmin", type=int, default=256)
     ap.add_argument("--nmax", type=int, default=8192)
     ap.add_argument("--max-slots", type=int, default=8, help="serving: concurrent solves")
-    ap.add_argument("--host-queue-gb", type=float, default=64.0,
-                    help="serving: client cap on the host bytes of outstanding requests")
+    ap.add_argument("--host-queue-gb", type=float, default=0.0,
+                    help="serving: optional client cap on the host bytes of outstanding requests (0: none)")
     args = ap.parse_args()
     if args.profile_case:
         run_profile_case(args.profile_case)
@@ -705,6 +719,31 @@ def main():
         fp64_s, fp64_val, fp64_nbe = float("nan"), None, None
         print(f"fp64 LU comparator unavailable: {exc}", file=sys.stderr)
 
+    # the same systems with the cost-aware k_max (an option of the library;
+    # the headline above uses the paper's k_max = 0.1 n)
+    cost_aware = None
+    if not args.no_cost_aware and mode != "batched":
+        pca = M.params_default(kmax_frac=-0.1)
+        for A, b, sp in zip(As, bs, specs):
+            ctx.solve(A, b, sp, pca)
+        torch.cuda.synchronize()
+        barrier()
+        tc0 = time.perf_counter()
+        ca_steps = max(1, min(args.steps, 3))
+        for _ in range(ca_steps):
+            ca_reps = []
+            for A, b, sp in zip(As, bs, specs):
+                x, r, st1 = ctx.solve(A, b, sp, pca)
+                ca_reps.extend(r)
+        torch.cuda.synchronize()
+        barrier()
+        ca_ms = max_over_ranks((time.perf_counter() - tc0) / ca_steps * 1e3, world, dev)
+        cost_aware = {"value": fl_job / (ca_ms * 1e-3) / 1e12, "unit": UNIT, "ms_per_step": ca_ms,
+                      "steps": ca_steps, "kmax_frac": -0.1,
+                      "all_converged_nbe_le_2u0": all(r["cged"] and r["nbe"] <= 2 * u0s[sp.split(",")[1]]
+                                                      for r, sp in zip(ca_reps, rep_spec)),
+                      "stages": [r["steps"] for r in ca_reps]}
+
     gemv = measure_gemv(ctx, dev) if (rank == 0 and not args.no_gemv) else None
 
     cpu = None
@@ -734,6 +773,7 @@ def main():
                                       peak_kind, fp64_pk, concurrency),
             "time_split_ms": {"factor": fac_ms, "refine": ref_ms},
             "cpu_baseline": cpu,
+            "cost_aware_kmax": cost_aware,
             "gemv": gemv,
             "clocks": clk.summary(),
             "gpu_launches": launches,

@@ -295,10 +295,15 @@ static int refine_grid(msir_ctx* ctx, int n, int share, int kcap) {
   return g;
 }
 
-static msir_status ws_alloc(Workspace& w, int nmax, int kcapmax, int G, cudaStream_t st) {
+// exact_n: the workspace must be laid out for exactly nmax (its leading
+// dimension then equals that of another workspace laid out for nmax).
+static msir_status ws_alloc(Workspace& w, int nmax, int kcapmax, int G, cudaStream_t st,
+                            bool exact_n = false) {
   Workspace probe;
   size_t bytes = ws_layout(probe, nmax, kcapmax, G, true, nullptr);
-  if (w.base && w.bytes >= bytes && w.nmax >= nmax && w.kcapmax >= kcapmax && w.G >= G) return MSIR_OK;
+  if (w.base && w.bytes >= bytes && (exact_n ? w.nmax == nmax : w.nmax >= nmax) && w.kcapmax >= kcapmax &&
+      w.G >= G)
+    return MSIR_OK;
   if (w.base) { cudaFreeAsync(w.base, st); w.base = nullptr; }
   char* base = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&base, bytes, st);
@@ -913,6 +918,8 @@ static void ws_restore(Workspace& w) {
 static msir_status slot_use_shared_level(msir_ctx* ctx, Slot& s, int fmt) {
   MatrixShare& sh = *s.job->share;
   const int li = level_index(fmt);
+  // this slot's status flags (the factoring slot's LU cleared its own)
+  CK(cudaMemsetAsync(s.w.iflags, 0, 32 * sizeof(int), s.st));
   s.lv[li] = sh.lv[li];
   s.cur = li;
   s.nfact += 1;
@@ -966,8 +973,15 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
   s.u0 = j.t.u;
   s.G = refine_grid(ctx, j.n, share, kcap_of(j.n, j.p.kmax_frac));
   const int kcap = kcap_of(j.n, j.p.kmax_frac);
-  msir_status r = ws_alloc(s.w, std::max(j.n, s.w.nmax), std::max(kcap, s.w.kcapmax),
-                           std::max(s.G, s.w.G), s.st);
+  MatrixShare* sh0 = j.share;
+  const bool attaching = sh0 && sh0->owner && sh0->owner != &s;
+  // a slot that uses the owner's matrix is laid out for the owner's size,
+  // so that both index A_u and the factors with the same leading dimension
+  msir_status r = attaching
+                      ? ws_alloc(s.w, sh0->owner->w.nmax, std::max(kcap, s.w.kcapmax), std::max(s.G, s.w.G),
+                                 s.st, true)
+                      : ws_alloc(s.w, std::max(j.n, s.w.nmax), std::max(kcap, s.w.kcapmax),
+                                 std::max(s.G, s.w.G), s.st);
   if (r != MSIR_OK) return r;
   s.t_factor = s.t_refine = 0;
   s.iter_ms = 0;
@@ -1512,9 +1526,11 @@ msir_status msir_solve(msir_ctx* ctx, int n, int nrhs, const double* A_dev, int 
     jp.push_back(&jobs[c]);
   }
   // several right-hand sides: columns run on up to K slots at once, sharing
-  // the matrix and its factors (K = one per 16 SMs by default;
-  // MSIR_RHS_SLOTS overrides it for tuning)
-  const int K = nrhs > 1 ? std::min(nrhs, env_int("MSIR_RHS_SLOTS", std::max(1, ctx->num_sms / 16), 1, 64)) : 1;
+  // the matrix and its factors.  K = 4 by default (at n = 8192 with 16
+  // columns, 1 / 4 / 9 / 16 slots measured 466 / 340 / 535 / 638 ms: each
+  // column's refinement needs a large share of the SMs for its substitution
+  // chains); MSIR_RHS_SLOTS overrides it for tuning
+  const int K = nrhs > 1 ? std::min(nrhs, env_int("MSIR_RHS_SLOTS", 4, 1, 64)) : 1;
   std::vector<Slot*> slots;
   msir_status r = pooled_slots(ctx, K, slots);
   // order the slots' work after the caller's stream
@@ -1647,9 +1663,16 @@ struct ServerSlot {
   Request* req = nullptr;
 };
 
+// Host bytes of request copies the server holds at most (queued and running
+// requests); a submission beyond it is refused with MSIR_ERR_NOMEM, so an
+// overloaded open-loop client gets back-pressure instead of exhausting the
+// host's memory.
+constexpr size_t kServerHostQueueBytes = (size_t)64 << 30;
+
 struct msir_server {
   msir_ctx* ctx = nullptr;
   size_t budget = 0, in_use = 0;  // in_use: bytes held by all slots
+  size_t host_held = 0;           // host bytes of the requests' copies
   int max_slots = 1;
   std::mutex mu;
   std::condition_variable cv;
@@ -1807,6 +1830,7 @@ static void server_loop(msir_server* S) {
         cudaMemcpyAsync(q->x_host.data(), ss.dx, (size_t)q->job.n * 8, cudaMemcpyDeviceToHost, s.st);
         cudaStreamSynchronize(s.st);
         std::lock_guard<std::mutex> lk(S->mu);
+        S->host_held -= (size_t)q->job.n * q->job.n * 8;
         q->A_host.clear();
         q->A_host.shrink_to_fit();
         q->job.t_done = std::chrono::steady_clock::now();
@@ -1868,12 +1892,23 @@ msir_status msir_server_submit(msir_server* S, int n, const double* A_host, int 
   q->footprint = request_footprint(n, p, t.u);
   // copy in now (host memory; the caller may free its buffers on return);
   // the device copy is made when the request is admitted
+  const size_t hb = ((size_t)n * n + 2 * (size_t)n) * 8;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->host_held + hb > kServerHostQueueBytes) {
+      delete q;
+      return MSIR_ERR_NOMEM;
+    }
+    S->host_held += hb;
+  }
   try {
     q->A_host.resize((size_t)n * n);
     q->b_host.assign(b_host, b_host + n);
     q->x_host.assign(n, 0.0);
   } catch (...) {
     delete q;
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->host_held -= hb;
     return MSIR_ERR_NOMEM;
   }
   for (int j = 0; j < n; ++j) memcpy(q->A_host.data() + (size_t)j * n, A_host + (size_t)j * lda, (size_t)n * 8);
@@ -1903,6 +1938,7 @@ msir_status msir_server_poll(msir_server* S, uint64_t ticket, int* state, double
   if (latency_ms)
     *latency_ms = std::chrono::duration<double, std::milli>(q->job.t_done - q->job.t_submit).count();
   const int st = q->job.status;
+  S->host_held -= 2 * (size_t)q->job.n * 8;
   S->all.erase(it);
   delete q;
   return st < 0 ? (msir_status)st : MSIR_OK;

@@ -114,11 +114,13 @@ def check_half_factors(ctx, A, u, uf, nb, nbo):
         candidates of the two chosen rows lie within c_j ulps of u_f at the
         column's scale max_i (|L||U|)_ij, c_j = ceil(j / nb) + 1 (one per
         panel store before j, one for the panel's own arithmetic);
-      * before j the factors agree elementwise within c_j (u_f (|L||U|) + eta)
-        (for L, u_f (|L||U|) / |u_jj| + eta), rows in their original order,
-        eta the subnormal spacing of u_f (rows scaled far down, as in the
-        graded systems, hold subnormal values whose rounding error is
-        absolute);
+      * before j the factors agree elementwise within
+        c_j (u_f (|L||U|)_ic + eta (1 + sum_{m<=i} |u_mc|)) for U and
+        c_j (u_f (|L||U|)_ic + eta (1 + sum_{m<=c} |u_mc|)) / |u_cc| for L,
+        rows in their original order; eta is the subnormal spacing of u_f:
+        rows scaled far down (the graded systems) hold subnormal values
+        with absolute errors up to eta, which reach later entries through
+        the pivot rows of U;
       * the GPU's factors satisfy the factorisation model's elementwise
         backward-error bound 2 (ceil(n/nb) + 2) u_f |L||U|, and |l_ij| <= 1.
     Returns (j, gap in ulps of the candidate) with j = n if no pivot differs."""
@@ -150,9 +152,12 @@ def check_half_factors(ctx, A, u, uf, nb, nbo):
         Lr[perm_o] = np.tril(Fo, -1)
         LUr[perm_o] = LUabs
         ujj = np.abs(np.diag(Fo))[:j]
-        eta = ETA[uf]
-        assert np.all(np.abs(Lg[:, :j] - Lr[:, :j]) <= cj * (uu * LUr[:, :j] / ujj[None, :] + eta))
-        assert np.all(np.abs(np.triu(fac.F)[:j] - np.triu(Fo)[:j]) <= cj * (uu * LUabs[:j] + eta))
+        # gradual underflow: a stored value carries an absolute error up to
+        # eta, which reaches later entries through U (eta (1 + sum_m |u_mc|))
+        eta_u = ETA[uf] * (1.0 + np.cumsum(np.abs(np.triu(Fo)), axis=0))  # [i, c]: sum over m <= i
+        colU = eta_u[np.minimum(np.arange(n), n - 1), np.arange(n)][:j]      # column c, rows m <= c
+        assert np.all(np.abs(Lg[:, :j] - Lr[:, :j]) <= cj * (uu * LUr[:, :j] + colU[None, :]) / ujj[None, :])
+        assert np.all(np.abs(np.triu(fac.F)[:j] - np.triu(Fo)[:j]) <= cj * (uu * LUabs[:j] + eta_u[:j]))
     L, U = OL.unpack(fac.F)
     Af = OF.fl(Au, uf).astype(np.float64)
     E = np.abs(Af[fac.perm] - L @ U)

@@ -108,3 +108,29 @@ def test_overloaded_server_queues_and_the_byte_cap_rejects():
     summ = bench.serving_summary(recs, warmup_s=0.0, duration_s=3.0)
     assert summ["unfinished"] == len(accepted) - len(done)
     assert summ["latency_ms"]["samples"] == len(done)
+
+
+def test_server_back_pressure_counts_as_rejected():
+    """A submission the server refuses with MSIR_ERR_NOMEM (its bound on held
+    host copies) is a rejected arrival, not an error of the harness."""
+    import bench
+
+    class Refusing:
+        def __init__(self):
+            self.calls = 0
+
+        def submit(self, A, b, spec):
+            self.calls += 1
+            err = RuntimeError("server_submit: out of device memory (-2)")
+            err.code = -2
+            raise err
+
+        def poll(self, t, n):
+            raise AssertionError("nothing was queued")
+
+    A = np.eye(4)
+    srv = Refusing()
+    clock = iter([0.0, 0.0, 0.5, 0.6, 1.5, 2.5, 3.0]).__next__
+    recs = bench.run_serving(srv, [(A, np.ones(4), "fp16,fp32,fp64")], [0.1, 0.4], [0, 0], 1.0, None,
+                             clock=clock, sleep=lambda s: None)
+    assert srv.calls == 2 and [r["status"] for r in recs] == ["rejected", "rejected"]
