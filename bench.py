@@ -218,9 +218,9 @@ def refine_bytes(rep, n):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per refinement
 # launch of this bench's default workload, from one ncu launch-list capture
-# of the same command with the refinement kernel as it stands; None when no
-# capture of the current kernel exists.
-REFINE_DRAM_BYTES_PER_LAUNCH = None
+# of the same command (3.54 TB over 12 refinement launches, four per step)
+# with the refinement kernel as it stands; None for other workloads.
+REFINE_DRAM_BYTES_PER_LAUNCH = {"c3_n8192_k1e3": 2.95e11}
 
 
 def refine_fp64_flops(rep, n):
@@ -280,7 +280,7 @@ def fp64_peak():
 
 
 def roofline_line(ref_bytes, ref_fp64, ref_alg, hbm_ach, fp64_ach, alg_ach, hbm_pk, hbm_kind, fp64_pk,
-                  concurrency):
+                  concurrency, workload=None):
     """The refinement kernel's bound is the larger of its two model times,
     bytes at the measured HBM rate and fp64-pipe flops at the measured fp64
     peak (the method's own flop count is reported beside them)."""
@@ -292,7 +292,8 @@ def roofline_line(ref_bytes, ref_fp64, ref_alg, hbm_ach, fp64_ach, alg_ach, hbm_
             "peak_source": "measured (msir_probe_fma_rate, fp64 fma chains on every SM)", "model_s": t_fp64,
             "work": "fp64-pipe flops as executed (dd terms at 8 or 12 flops)"}
     top = ({"bound": "alu", "pipe": "fp64"} | fp64) if t_fp64 > t_hbm else ({"bound": "hbm"} | hbm)
-    top.update({"kernel": "refine_kernel (persistent refinement)", "traffic": REFINE_DRAM_BYTES_PER_LAUNCH,
+    top.update({"kernel": "refine_kernel (persistent refinement)",
+                "traffic": REFINE_DRAM_BYTES_PER_LAUNCH.get(workload),
                 "traffic_unit": "bytes per launch (ncu)", "concurrency": concurrency,
                 "frac_of_gpu_share": top["frac"] * concurrency, "hbm": hbm, "fp64": fp64,
                 "algorithmic": {"achieved": alg_ach, "unit": "TFLOP/s",
@@ -770,7 +771,7 @@ def main():
                     "api": "msir_solve_host (host buffers, copies inside the call)"
                     if mode != "batched" else "pinned host copies + msir_solve_batched"},
             "roofline": roofline_line(ref_bytes, ref_fp64, ref_alg, hbm_ach, fp64_ach, alg_ach, peak,
-                                      peak_kind, fp64_pk, concurrency),
+                                      peak_kind, fp64_pk, concurrency, name),
             "time_split_ms": {"factor": fac_ms, "refine": ref_ms},
             "cpu_baseline": cpu,
             "cost_aware_kmax": cost_aware,

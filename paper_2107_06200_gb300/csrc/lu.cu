@@ -273,9 +273,12 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
       } else if (rank == 0 && tid == 0) {
         atomicCAS(a.info, 0, kk + j + 1);
       }
-      __syncthreads();
+      // no barrier here: the next column's scan reads only this thread's own
+      // rows, its pushes read rows after the next barrier, and the candidate
+      // buffers alternate, so a slower thread's update never meets them
       PT_END(3);
     }
+    __syncthreads();
     PT_END(0);
 
     // round the panel to F in place, store it, and record its pivots
@@ -344,7 +347,9 @@ __global__ void __launch_bounds__(kPanelThreads, 1) lu_outer_panel(PanelArgs a) 
         }
         __syncwarp();
       }
-      if (rank == 0) {
+    } else if (warp == 1 && rank == 0) {
+      // the outer block's map, built beside warp 0's inner map
+      {
         const int base = kk - k;
         for (int j = 0; j < w; ++j) {
           const int pa = base + j, pb = base + s_piv[j];
@@ -507,7 +512,7 @@ template <typename F>
 __global__ void __launch_bounds__(256) lu_outer_swap_trsm(SwapTrsmArgs a) {
   using T = typename Fmt<F>::T;
   F* A = (F*)a.A;
-  const int lda = a.lda, n = a.n, k = a.k, W = a.W;
+  const int lda = a.lda, k = a.k, W = a.W;
   const int cnt = *a.map_cnt;
   const int nleft = a.do_left ? k : 0, nright = a.c_end - a.c_begin;
   const int tiles_left = (nleft + 31) / 32;

@@ -72,9 +72,16 @@ def randsvd_system(n, kappa, seed, nrhs=1, graded=False, device=None, mode=3):
     X = rng.standard_normal((n, nrhs))
     g = rng.uniform(-4.0, 4.0, n) if graded else None
     sigma = singular_values(n, kappa, mode)
+    A_t = None
     if device is not None:
         import torch
-        A_t = _algebra_torch(G1, G2, sigma, device)
+        try:
+            A_t = _algebra_torch(G1, G2, sigma, device)
+        except RuntimeError:
+            # torch's linear-algebra library cannot be loaded (e.g. under a
+            # profiler): the same algebra with numpy on the host
+            A_t = None
+    if A_t is not None:
         if graded:
             A_t = torch.from_numpy(10.0 ** g).to(device)[:, None] * A_t
         B_t = A_t @ torch.from_numpy(X).to(device)
