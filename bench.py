@@ -54,6 +54,9 @@ def workload_systems(name):
                 for t in (BSD, HSD, SDQ) for r in (1, 16)], "single"
     if name == "sweep_n2000":
         return [(n, k, t, g, 1) for (n, k, t, g) in workloads("sweep_n2000")], "batched"
+    if name == "c4_batched":
+        from synth import batched_systems
+        return [(n, k, HSD, False, 1, seed) for (n, k, seed) in batched_systems(4096, seed=0)], "batched"
     raise KeyError(name)
 
 
@@ -127,8 +130,10 @@ def build_systems(units, device=None):
     """The seeded systems (A row-major fp64, B n x nrhs) of the given units."""
     from synth import randsvd_system
     out = []
-    for (n, kappa, spec, graded, nrhs) in units:
-        A, B, X = randsvd_system(n, kappa, 0, nrhs=nrhs, graded=graded, device=device)
+    for u in units:
+        n, kappa, spec, graded, nrhs = u[:5]
+        seed = u[5] if len(u) > 5 else 0
+        A, B, X = randsvd_system(n, kappa, seed, nrhs=nrhs, graded=graded, device=device)
         out.append(dict(n=n, kappa=kappa, spec=spec, graded=graded, nrhs=nrhs, A=A,
                         b=B[:, 0].copy() if nrhs == 1 else B))
     return out
@@ -312,11 +317,12 @@ def run_cpu_baseline(units, max_seconds=25.0, n_sample=1024):
     el = 0.0
     fl = 0.0
     done = []
-    for (n0, kappa, spec, graded, nrhs) in units:
+    for u in units:
+        n0, kappa, spec, graded, nrhs = u[:5]
         if el > max_seconds and done:
             break
         n = min(n0, n_sample)
-        A, B, _ = randsvd_system(n, kappa, 0, graded=graded)
+        A, B, _ = randsvd_system(n, kappa, u[5] if len(u) > 5 else 0, graded=graded)
         trip = tuple(names[x] for x in spec.split(","))
         t1 = time.time()
         OM.msir(A, B[:, 0], trip, OM.Params())
@@ -473,10 +479,14 @@ def bench_config(name, world, mode):
     a bounded sample of the same configuration)."""
     units, _ = workload_systems(name)
     ns = sorted({u[0] for u in units})
-    return {"workload": name, "systems": len(units), "n": ns if len(ns) > 1 else ns[0],
-            "kappa": sorted({u[1] for u in units}), "triples": sorted({u[2] for u in units}),
+    ks = sorted({u[1] for u in units})
+    many = len(ns) > 8
+    return {"workload": name, "systems": len(units),
+            "n": ([ns[0], ns[-1]] if many else ns) if len(ns) > 1 else ns[0],
+            "kappa": [ks[0], ks[-1]] if len(ks) > 8 else ks, "triples": sorted({u[2] for u in units}),
             "nrhs": sorted({u[4] for u in units}), "graded": sorted({u[3] for u in units}),
-            "l2": "inputs larger than L2 (fp64 A of %s)" % ", ".join(f"n={n}" for n in ns),
+            "l2": ("inputs larger than L2 (fp64 A of %s)" % ", ".join(f"n={n}" for n in ns)) if not many else
+                  "inputs larger than L2 (%.1f GB of fp64 matrices per step)" % (sum(8.0 * u[0] ** 2 for u in units) / 1e9),
             "parallelism": f"weak x{world} (LPT on n^3 over ranks)",
             "mode": {"single": "msir_solve per system, whole GPU each",
                      "batched": "msir_solve_batched (systems share the GPU)",
@@ -510,7 +520,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD,
-                    choices=["c3_n8192_k1e3", "c3_n8192", "c3", "sweep_n2000"])
+                    choices=["c3_n8192_k1e3", "c3_n8192", "c3", "sweep_n2000", "c4_batched"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gemv", action="store_true", help="skip the operator bandwidth measurement")
     ap.add_argument("--no-cost-aware", action="store_true",
@@ -760,7 +770,9 @@ def main():
             "config": bench_config(name, world, mode),
             "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat)},
             "all_converged_nbe_le_2u0": nbe_ok,
-            "systems": per_system,
+            "systems": per_system if len(per_system) <= 64 else
+            {"count": len(per_system), "stages_first_16": [p_["stages"] for p_ in per_system[:16]],
+             "max_nbe": max(p_["nbe"] for p_ in per_system)},
             "fp64_lu": {"value": fp64_val, "unit": UNIT,
                         "ms_per_step": None if fp64_val is None else fp64_s * 1e3,
                         "nbe_max": fp64_nbe,
