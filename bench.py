@@ -388,8 +388,8 @@ def run_serving(server, systems, times, picks, duration_s, byte_cap, clock=time.
             if byte_cap is None or used + need <= byte_cap:
                 try:
                     tk = server.submit(A, b, spec)
-                except Exception as exc:  # the server's own back-pressure (MSIR_ERR_NOMEM)
-                    if getattr(exc, "code", None) != -2:
+                except Exception as exc:  # the server's own back-pressure (MSIR_ERR_BUSY / NOMEM)
+                    if getattr(exc, "code", None) not in (-7, -2):
                         raise
                     tk = None
                 if tk is not None:
@@ -458,9 +458,21 @@ def run_serve_bench(args):
     # beyond its limit is refused and counted as rejected); the client sets
     # no cap unless asked to
     host_cap = int(args.host_queue_gb * 2 ** 30) if args.host_queue_gb > 0 else None
-    srv = M.Server(ctx, hbm_budget_bytes=budget, max_slots=args.max_slots)
+    srv = M.Server(ctx, hbm_budget_bytes=budget, max_slots=args.max_slots,
+                   max_backlog_ms=args.serve_backlog_ms)
+    params = M.params_default(kmax_frac=args.serve_kmax_frac)
+
+    class WithParams:
+        """The server with every request's Algorithm 4 parameters fixed."""
+
+        def submit(self, A, b, spec):
+            return srv.submit(A, b, spec, params)
+
+        def poll(self, t, n):
+            return srv.poll(t, n)
+
     try:
-        recs = run_serving(srv, systems, times, picks, args.duration, byte_cap=host_cap)
+        recs = run_serving(WithParams(), systems, times, picks, args.duration, byte_cap=host_cap)
     finally:
         srv.close()
         ctx.close()
@@ -469,6 +481,10 @@ def run_serve_bench(args):
                        "warmup_s": args.serve_warmup, "pool": args.pool, "n_range": [args.nmin, args.nmax],
                        "log10_kappa_range": [2, 10], "triples": ["fp16,fp32,fp64", "bf16,fp32,fp64", "fp32,fp64,dd"],
                        "max_slots": args.max_slots, "hbm_budget_bytes": budget,
+                       "max_backlog_ms": args.serve_backlog_ms,
+                       "kmax_frac": args.serve_kmax_frac,
+                       "kmax": "0.1 n (the paper's)" if args.serve_kmax_frac > 0 else
+                               "cost-aware, capped at %g n" % abs(args.serve_kmax_frac),
                        "client_host_queue_bytes": host_cap}}
     line.update(serving_summary(recs, args.serve_warmup, args.duration))
     print(json.dumps(line))
@@ -538,6 +554,12 @@ def main():
     ap.add_argument("--nmin", type=int, default=256)
     ap.add_argument("--nmax", type=int, default=8192)
     ap.add_argument("--max-slots", type=int, default=8, help="serving: concurrent solves")
+    ap.add_argument("--serve-backlog-ms", type=float, default=2000.0,
+                    help="serving: the server refuses arrivals while its queued work exceeds this many ms "
+                         "at its measured rate (0: only its host-memory bound)")
+    ap.add_argument("--serve-kmax-frac", type=float, default=0.1,
+                    help="serving: msir_params.kmax_frac of every request (0.1: the paper's k_max = 0.1 n; "
+                         "negative: cost-aware)")
     ap.add_argument("--host-queue-gb", type=float, default=0.0,
                     help="serving: optional client cap on the host bytes of outstanding requests (0: none)")
     args = ap.parse_args()

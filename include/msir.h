@@ -85,7 +85,9 @@ typedef enum {
   MSIR_ERR_SINGULAR = -3,   /* exact zero pivot with u_f = fp64 */
   MSIR_ERR_TIMEOUT = -4,    /* a device-side wait hit its deadline */
   MSIR_ERR_CUDA = -5,       /* a CUDA runtime call failed */
-  MSIR_ERR_UNSUPPORTED = -6 /* device is not sm_103 or lacks a feature */
+  MSIR_ERR_UNSUPPORTED = -6, /* device is not sm_103 or lacks a feature */
+  MSIR_ERR_BUSY = -7         /* msir_server_submit: the server's queue is at its
+                                host-memory or backlog limit; nothing was queued */
 } msir_status;
 
 /* Parameters of Algorithm 4.  msir_params_default() fills the paper's
@@ -277,11 +279,23 @@ msir_status msir_server_create(msir_ctx* ctx, size_t hbm_budget_bytes, int max_s
  * memory; they are copied into host memory that the server owns before the
  * call returns, and to the device when the request is admitted (inside
  * hbm_budget_bytes).  *ticket receives an id.  Errors: MSIR_ERR_INVALID for
- * bad arguments, MSIR_ERR_NOMEM when the host copy cannot be allocated
- * (nothing is queued then). */
+ * bad arguments; MSIR_ERR_BUSY when the requests the server holds already
+ * take 64 GiB of host memory, or when a backlog limit is set
+ * (msir_server_set_backlog_limit) and the queued work would exceed it;
+ * MSIR_ERR_NOMEM when the host copy cannot be allocated.  Nothing is queued
+ * on an error. */
 msir_status msir_server_submit(msir_server* s, int n, const double* A_host, int lda,
                                const double* b_host, msir_triple t, const msir_params* params,
                                uint64_t* ticket);
+
+/* Admission by expected waiting time (the paper has no counterpart; a
+ * serving policy).  With max_backlog_ms > 0, a submission is refused with
+ * MSIR_ERR_BUSY when the queued requests' work, sum of n^3, divided by the
+ * server's recent completion rate (n^3 per ms over its last 32 completed
+ * requests) exceeds max_backlog_ms.  Until 4 requests have completed there
+ * is no rate and only the host-memory limit applies.  0 (the default)
+ * removes the limit.  MSIR_ERR_INVALID for a negative or non-finite value. */
+msir_status msir_server_set_backlog_limit(msir_server* s, double max_backlog_ms);
 
 /* Non-blocking poll.  *state: 0 queued, 1 running, 2 done.  When done, x_host
  * (n doubles, may be NULL) and *rep (may be NULL) are filled and the ticket
@@ -301,6 +315,16 @@ msir_status msir_server_destroy(msir_server* s);
  * kernel's fp64 work is compared with.  Blocks until the launch is done;
  * allocates nothing on the device. */
 msir_status msir_probe_fma_rate(int device, int fmt, int iters, double* tflops, double* seconds);
+
+/* Arithmetic check; the paper has no counterpart.  The fp64 operator on
+ * fp32 data widens operands with integer instructions (the IEEE binary32 ->
+ * binary64 field mapping) instead of the hardware conversion.  This runs
+ * that widening on all 2^32 fp32 bit patterns on device `device`:
+ * *mismatches counts patterns where it differs from the hardware conversion
+ * or where its test for subnormal / infinite / NaN input is wrong (0
+ * expected); *checked counts the patterns it converted itself.  Blocks; a
+ * few milliseconds. */
+msir_status msir_probe_widen_check(int device, unsigned long long* mismatches, unsigned long long* checked);
 
 /* Failure-handling check; the paper has no counterpart.  Runs one block
  * into the library's bounded grid-barrier wait for a grid of two blocks, so

@@ -18,7 +18,7 @@ from ._lib import (BF16, FP16, FP32, FP64, DD, CONV_COMBINED, CONV_EST, CONV_TRU
 _L = _lib.load()
 
 __all__ = ["Context", "Server", "MsirError", "triple", "params_default", "report_to_dict",
-           "stage_string", "probe_fma_rate", "probe_wait_timeout", "BF16", "FP16", "FP32", "FP64", "DD", "lib_path"]
+           "stage_string", "probe_fma_rate", "probe_wait_timeout", "probe_widen_check", "BF16", "FP16", "FP32", "FP64", "DD", "lib_path"]
 
 
 def lib_path():
@@ -72,6 +72,14 @@ def probe_wait_timeout(device=0, limit_s=0.2):
     st = ctypes.c_int(0)
     _check(_L.msir_probe_wait_timeout(device, float(limit_s), ctypes.byref(st)), "probe_wait_timeout")
     return st.value
+
+
+def probe_widen_check(device=0):
+    """Runs the integer fp32 -> fp64 widening on every fp32 bit pattern
+    (msir_probe_widen_check); returns (mismatches, patterns checked)."""
+    bad, chk = ctypes.c_ulonglong(0), ctypes.c_ulonglong(0)
+    _check(_L.msir_probe_widen_check(device, ctypes.byref(bad), ctypes.byref(chk)), "probe_widen_check")
+    return bad.value, chk.value
 
 
 def stage_string(stages):
@@ -277,12 +285,14 @@ class Context:
 class Server:
     """Continuous-batching solve server (msir_server_*)."""
 
-    def __init__(self, ctx, hbm_budget_bytes=0, max_slots=8):
+    def __init__(self, ctx, hbm_budget_bytes=0, max_slots=8, max_backlog_ms=0.0):
         self.ctx = ctx
         h = ctypes.c_void_p()
         _check(_L.msir_server_create(ctx.h, hbm_budget_bytes, max_slots, ctypes.byref(h)),
                "server_create")
         self.h = h
+        if max_backlog_ms:
+            _check(_L.msir_server_set_backlog_limit(h, float(max_backlog_ms)), "server_set_backlog_limit")
 
     def submit(self, A, b, spec, params=None):
         A = np.asfortranarray(np.asarray(A, dtype=np.float64))

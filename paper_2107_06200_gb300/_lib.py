@@ -18,14 +18,15 @@ ALG_SIR, ALG_SGMRES, ALG_GMRES = 0, 1, 2
 ALG_NAMES = {ALG_SIR: "SIR", ALG_SGMRES: "SGMRES-IR", ALG_GMRES: "GMRES-IR"}
 OK, NOT_CONVERGED = 0, 1
 ERR_INVALID, ERR_NOMEM, ERR_SINGULAR, ERR_TIMEOUT, ERR_CUDA, ERR_UNSUPPORTED = -1, -2, -3, -4, -5, -6
+ERR_BUSY = -7
 MAX_STAGES, MAX_STEPS = 24, 48
 
 EXPORTED = [
     "msir_params_default", "msir_create", "msir_destroy", "msir_factor", "msir_factors_destroy",
     "msir_factors_export", "msir_factors_apply", "msir_residual", "msir_solve", "msir_solve_host",
     "msir_solve_batched", "msir_server_create", "msir_server_submit", "msir_server_poll",
-    "msir_server_destroy", "msir_status_string", "msir_residual_noalloc", "msir_probe_fma_rate",
-    "msir_probe_wait_timeout",
+    "msir_server_destroy", "msir_server_set_backlog_limit", "msir_status_string", "msir_residual_noalloc", "msir_probe_fma_rate",
+    "msir_probe_wait_timeout", "msir_probe_widen_check",
 ]
 
 
@@ -88,10 +89,12 @@ def load(path=LIB_PATH):
                                ctypes.POINTER(ctypes.c_uint64)],
         "msir_server_poll": [P, ctypes.c_uint64, pI, P, ctypes.POINTER(Report), pD],
         "msir_server_destroy": [P],
+        "msir_server_set_backlog_limit": [P, D],
         "msir_status_string": [I],
         "msir_residual_noalloc": [I, P, I, I, P, P, I, P, P, P],
         "msir_probe_fma_rate": [I, I, I, pD, pD],
         "msir_probe_wait_timeout": [I, D, pI],
+        "msir_probe_widen_check": [I, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

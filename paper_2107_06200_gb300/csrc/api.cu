@@ -273,7 +273,7 @@ static size_t ws_layout(Workspace& w, int n, int kcap, int G, bool alloc_f64_lev
   w.st = (RefState*)take(sizeof(RefState));
   w.rep = (msir_report*)take(sizeof(msir_report));
   w.ident = (int*)take(n * 4);
-  w.tsv = (unsigned long long*)take(((size_t)(n + kBlk - 1) / kBlk) * 6 * 8);
+  w.tsv = (unsigned long long*)take(((size_t)(n + kBlk - 1) / kBlk) * 8 * 8);
   return off + 256;
 }
 
@@ -293,6 +293,25 @@ static int refine_grid(msir_ctx* ctx, int n, int share, int kcap) {
   (void)kcap;
   if (share > 1) g = std::max(1, std::min(g, ctx->num_sms / share));  // systems running together split the SMs
   return g;
+}
+
+// Cluster size of a solve's refinement launch.  Clusters are opt-in
+// (MSIR_CLUSTER = 2, 4 or 8), for a solve that runs alone on the GPU with at
+// least 16 blocks of rows (a cooperative launch of clusters needs whole
+// free GPCs, which concurrent solves would fragment).  Measured on one
+// GB300 (n = 8192, (bf16, single, double), 328 GMRES iterations): with 8-CTA
+// clusters the fp32 substitution hand-off falls from 1.27 to 1.0 us per
+// block, but the launch then has 144 instead of 152 CTAs and the whole
+// refinement takes 328 instead of 288 ms (the other phases ran 25-40 %
+// slower); 2- and 4-CTA clusters gave 288 and 294 ms.  Default: no clusters.
+static int env_int(const char* name, int dflt, int lo, int hi);
+static int refine_cluster_size(int n, int share) {
+  static const int env = [] {
+    const int v = env_int("MSIR_CLUSTER", 0, 1, kMaxCluster);
+    return (v == 2 || v == 4 || v == 8) ? v : 1;
+  }();
+  if (share > 1 || (n + kBlk - 1) / kBlk < 16) return 1;
+  return env;
 }
 
 // exact_n: the workspace must be laid out for exactly nmax (its leading
@@ -604,6 +623,7 @@ struct Slot {
   bool try_squeeze = false;
   int try_level = 0;
   int G = 1;
+  int C = 1;                  // CTAs per thread-block cluster of the refinement launch
   double normA = 0, normb = 0;
   float t_factor = 0, t_refine = 0;
   bool factoring_initial = true;
@@ -759,6 +779,7 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
     return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
   }();
   a.team_k = team_k;
+  a.cluster = (mode == MODE_SOLVE && s.C > 1 && s.G % s.C == 0) ? s.C : 1;
   a.tau = j.p.tau;
   a.gamma = j.p.gamma;
   a.conv = j.p.conv;
@@ -799,15 +820,15 @@ static void print_wait_site(Slot& s) {
 static void print_trsv_timers(Slot& s) {
   if (!trsv_timers_enabled() || !s.job) return;
   const int nblk = (s.job->n + kBlk - 1) / kBlk;
-  std::vector<unsigned long long> t((size_t)nblk * 6);
+  std::vector<unsigned long long> t((size_t)nblk * 8);
   cudaStreamSynchronize(s.st);
   cudaMemcpy(t.data(), s.w.tsv, t.size() * 8, cudaMemcpyDeviceToHost);
   for (int dir = 0; dir < 2; ++dir) {
     unsigned long long t0 = ~0ull, t1 = 0;
-    double off = 0, diag = 0, offmax = 0, diagmax = 0, gap = 0;
+    double off = 0, diag = 0, offmax = 0, diagmax = 0, gap = 0, seen = 0, last = 0;
     int ngap = 0;
     for (int b = 0; b < nblk; ++b) {
-      const unsigned long long* q = &t[((size_t)dir * nblk + b) * 3];
+      const unsigned long long* q = &t[((size_t)dir * nblk + b) * 4];
       t0 = std::min(t0, q[0]);
       t1 = std::max(t1, q[2]);
       off += (double)(q[1] - q[0]);
@@ -816,13 +837,20 @@ static void print_trsv_timers(Slot& s) {
       diagmax = std::max(diagmax, (double)(q[2] - q[1]));
       const int pb = dir ? b + 1 : b - 1;  // the block this one waits for last
       if (pb >= 0 && pb < nblk) {
-        const unsigned long long* pq = &t[((size_t)dir * nblk + pb) * 3];
-        if (q[1] > pq[2]) { gap += (double)(q[1] - pq[2]); ++ngap; }
+        const unsigned long long* pq = &t[((size_t)dir * nblk + pb) * 4];
+        if (q[1] > pq[2] && q[3] >= pq[2] && q[1] >= q[3]) {
+          gap += (double)(q[1] - pq[2]);
+          seen += (double)(q[3] - pq[2]);
+          last += (double)(q[1] - q[3]);
+          ++ngap;
+        }
       }
     }
-    fprintf(stderr, "[msir trsv %s] blocks %d span %.1f us, per block: offdiag avg %.2f max %.2f us, diag avg %.2f max %.2f us, publish->next offdiag done %.2f us\n",
+    const double g = ngap ? 1e-3 / ngap : 0.0;
+    fprintf(stderr, "[msir trsv %s] blocks %d span %.1f us, per block: offdiag avg %.2f max %.2f us, diag avg %.2f max %.2f us, "
+            "publish->next offdiag done %.2f us (publish->seen %.2f, last tile %.2f)\n",
             dir ? "upper" : "lower", nblk, (t1 - t0) * 1e-3, off / nblk * 1e-3, offmax * 1e-3,
-            diag / nblk * 1e-3, diagmax * 1e-3, ngap ? gap / ngap * 1e-3 : 0.0);
+            diag / nblk * 1e-3, diagmax * 1e-3, gap * g, seen * g, last * g);
   }
 }
 
@@ -973,6 +1001,18 @@ static msir_status slot_start(msir_ctx* ctx, Slot& s, Job* job, int share) {
   s.u0 = j.t.u;
   s.G = refine_grid(ctx, j.n, share, kcap_of(j.n, j.p.kmax_frac));
   const int kcap = kcap_of(j.n, j.p.kmax_frac);
+  // a solve that has the GPU to itself runs its refinement in clusters, so
+  // that most substitution hand-offs go through distributed shared memory
+  s.C = 1;
+  const int C = refine_cluster_size(j.n, share);
+  if (C > 1) {
+    const int gc = refine_max_cluster_grid(s.u0, kcap, C);
+    const int g = std::min(s.G, gc) / C * C;
+    if (g >= C) {
+      s.G = g;
+      s.C = C;
+    }
+  }
   MatrixShare* sh0 = j.share;
   const bool attaching = sh0 && sh0->owner && sh0->owner != &s;
   // a slot that uses the owner's matrix is laid out for the owner's size,
@@ -1228,6 +1268,7 @@ const char* msir_status_string(int s) {
     case MSIR_ERR_TIMEOUT: return "device wait timed out";
     case MSIR_ERR_CUDA: return "CUDA error";
     case MSIR_ERR_UNSUPPORTED: return "unsupported device or size";
+    case MSIR_ERR_BUSY: return "server queue full";
   }
   return "unknown";
 }
@@ -1682,7 +1723,31 @@ struct msir_server {
   std::atomic<bool> stop{false};
   std::thread worker;
   std::vector<ServerSlot> slots;
+  // admission by expected waiting time (msir_server_set_backlog_limit)
+  double max_backlog_ms = 0.0;
+  double queued_work = 0.0;  // sum of n^3 over queued requests
+  std::deque<std::pair<double, double>> done_log;  // (completion time in ms, n^3), last kRateWindow
 };
+
+// Completions over which the server's work rate is measured.
+constexpr size_t kRateWindow = 32;
+
+static double request_work(int n) { return (double)n * (double)n * (double)n; }
+
+static double steady_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Expected waiting time of the queue in ms (work over the measured rate), or
+// -1 while fewer than 4 requests have completed.  Caller holds S->mu.
+static double server_backlog_ms(const msir_server* S) {
+  if (S->done_log.size() < 4) return -1.0;
+  double w = 0.0;
+  for (size_t i = 1; i < S->done_log.size(); ++i) w += S->done_log[i].second;
+  const double span = S->done_log.back().first - S->done_log.front().first;
+  if (!(span > 0.0) || !(w > 0.0)) return -1.0;
+  return S->queued_work / (w / span);
+}
 
 static size_t request_footprint(int n, const msir_params& p, int u) {
   const size_t nn = (size_t)n * n;
@@ -1766,6 +1831,7 @@ static void server_loop(msir_server* S) {
               pick = q;
               delta = d;
               S->queue.erase(it);
+              S->queued_work -= request_work(q->job.n);
               break;
             }
             if (it == S->queue.begin() && q->bypassed >= kMaxBypass) break;  // the head's turn
@@ -1836,6 +1902,8 @@ static void server_loop(msir_server* S) {
         q->job.t_done = std::chrono::steady_clock::now();
         q->state = 2;
         ss.req = nullptr;
+        S->done_log.emplace_back(steady_ms(), request_work(q->job.n));
+        if (S->done_log.size() > kRateWindow) S->done_log.pop_front();
       }
     }
     if (!progressed) {
@@ -1895,9 +1963,10 @@ msir_status msir_server_submit(msir_server* S, int n, const double* A_host, int 
   const size_t hb = ((size_t)n * n + 2 * (size_t)n) * 8;
   {
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->host_held + hb > kServerHostQueueBytes) {
+    const double bl = S->max_backlog_ms > 0.0 ? server_backlog_ms(S) : -1.0;
+    if (S->host_held + hb > kServerHostQueueBytes || (bl >= 0.0 && bl > S->max_backlog_ms)) {
       delete q;
-      return MSIR_ERR_NOMEM;
+      return MSIR_ERR_BUSY;
     }
     S->host_held += hb;
   }
@@ -1918,9 +1987,17 @@ msir_status msir_server_submit(msir_server* S, int n, const double* A_host, int 
     q->ticket = S->next_ticket++;
     S->all[q->ticket] = q;
     S->queue.push_back(q);
+    S->queued_work += request_work(n);
   }
   S->cv.notify_all();
   *ticket = q->ticket;
+  return MSIR_OK;
+}
+
+msir_status msir_server_set_backlog_limit(msir_server* S, double max_backlog_ms) {
+  if (!S || !(max_backlog_ms >= 0.0) || !std::isfinite(max_backlog_ms)) return MSIR_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->max_backlog_ms = max_backlog_ms;
   return MSIR_OK;
 }
 

@@ -185,6 +185,31 @@ __device__ __forceinline__ dd_t dd_shfl_xor(dd_t a, int m) {
   return {__shfl_xor_sync(0xffffffffu, a.hi, m), __shfl_xor_sync(0xffffffffu, a.lo, m)};
 }
 
+// ------------------------------------------------------------ widening
+
+// fp32 -> fp64 from the IEEE 754 binary32 and binary64 layouts: the sign
+// bit stays, the 8-bit exponent is rebiased from 127 to 1023 (+896) into the
+// 11-bit field, and the 23 fraction bits become the top of the 52-bit
+// fraction.  Integer instructions only; exact for zeros and normal numbers.
+// Subnormals, infinities and NaNs need the hardware conversion: callers test
+// widen_special() first (one warp vote for a group of values).  On GB300 the
+// hardware conversion runs on the narrow fp64 pipe, where it costs as much
+// as the fused multiply-add it feeds.
+__device__ __forceinline__ double widen_normal(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned mag = b & 0x7fffffffu;
+  const unsigned hi = mag == 0u ? (b & 0x80000000u) : ((b & 0x80000000u) | ((mag >> 3) + 0x38000000u));
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+// subnormal (magnitude bits 1 .. 2^23 - 1), infinity or NaN (exponent 255)
+__device__ __forceinline__ bool widen_special(float f) {
+  const unsigned mag = __float_as_uint(f) & 0x7fffffffu;
+  return mag - 1u < 0x007fffffu || mag >= 0x7f800000u;
+}
+__device__ __forceinline__ bool widen_special4(const float4& f) {
+  return widen_special(f.x) | widen_special(f.y) | widen_special(f.z) | widen_special(f.w);
+}
+
 // ------------------------------------------------------------ waits
 
 __device__ __forceinline__ unsigned long long gtimer() {

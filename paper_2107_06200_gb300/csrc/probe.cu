@@ -78,7 +78,56 @@ __global__ void wait_timeout_probe_kernel(unsigned* count, int* err, unsigned lo
   (void)msir::grid_barrier_for(count, err, 2u, limit_ns);
 }
 
+// Every fp32 bit pattern: widen_special() must flag exactly the
+// subnormals, infinities and NaNs, and widen_normal() must equal the
+// hardware conversion, bit for bit, on every other pattern.
+__global__ void widen_check_kernel(unsigned long long* out) {
+  unsigned long long bad = 0, checked = 0;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < (1ull << 32);
+       i += stride) {
+    const float f = __uint_as_float((unsigned)i);
+    const float a = fabsf(f);
+    const bool expect = isnan(f) || isinf(f) || (a != 0.0f && a < 1.17549435e-38f);
+    const bool sp = msir::widen_special(f);
+    if (sp != expect) ++bad;
+    if (!sp) {
+      ++checked;
+      if (__double_as_longlong(msir::widen_normal(f)) != __double_as_longlong((double)f)) ++bad;
+    }
+  }
+  atomicAdd(out, bad);
+  atomicAdd(out + 1, checked);
+}
+
 }  // namespace
+
+extern "C" msir_status msir_probe_widen_check(int device, unsigned long long* mismatches,
+                                              unsigned long long* checked) {
+  if (!mismatches || !checked) return MSIR_ERR_INVALID;
+  if (cudaSetDevice(device) != cudaSuccess) return MSIR_ERR_CUDA;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return MSIR_ERR_CUDA;
+  unsigned long long* d = nullptr;
+  msir_status out = MSIR_OK;
+  unsigned long long h[2] = {0, 0};
+  if (cudaMallocAsync((void**)&d, 16, st) != cudaSuccess || cudaMemsetAsync(d, 0, 16, st) != cudaSuccess) {
+    out = MSIR_ERR_CUDA;
+  } else {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    widen_check_kernel<<<sms * 8, 256, 0, st>>>(d);
+    if (cudaMemcpyAsync(h, d, 16, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+      out = MSIR_ERR_CUDA;
+  }
+  if (d) cudaFreeAsync(d, st);
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(st);
+  *mismatches = h[0];
+  *checked = h[1];
+  return out;
+}
 
 extern "C" msir_status msir_probe_wait_timeout(int device, double limit_s, int* status) {
   if (!status || !(limit_s > 0.0) || limit_s > 10.0) return MSIR_ERR_INVALID;

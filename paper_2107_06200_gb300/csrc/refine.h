@@ -24,6 +24,13 @@ constexpr int kTrsvSmem = (kRefThreads / 32 + 1) * kBlk * 16;
 // doubles each; factor rows, 32 x 65 doubles).
 constexpr int kScLd = kBlk + 1;
 constexpr int kScaledSmem = (2 * kBlk * (kBlk / 2 + 1) + (kBlk / 2) * kScLd) * 8;
+// Thread-block clusters of the refinement launch: at most kMaxCluster CTAs.
+// Each CTA keeps an inbox in shared memory where the CTAs of its cluster
+// that solve the blocks just before it (forward) or after it (backward)
+// write their solved values: one slot of kBlk values of kLLWords words per
+// team position in the cluster.
+constexpr int kMaxCluster = 8;
+constexpr int kInboxSmem = kMaxCluster * kBlk * kLLWords * 8;
 
 enum RefMode { MODE_SOLVE = 0, MODE_APPLY = 1, MODE_RESIDUAL = 2 };
 enum RefPhase {
@@ -123,14 +130,21 @@ struct RefineArgs {
   // MODE_RESIDUAL: output s
   double* res_s;
   // optional wavefront timestamps of the last substitution pair (ns):
-  // [direction][block][start, off-diagonal done, published]
+  // [direction][block][start, off-diagonal done, published, last dependency seen]
   unsigned long long* tsv;
+  // CTAs per thread-block cluster of this launch (1: no clusters); the
+  // substitutions hand solved blocks to the CTAs of their cluster through
+  // distributed shared memory
+  int cluster;
 };
 
 constexpr int kRedW = 4;
 
 cudaError_t launch_refine(int a_fmt, int f_fmt, const RefineArgs& a, int grid, cudaStream_t st);
 int refine_max_grid(int a_fmt, int f_fmt, int kcap);
+// Largest cooperative grid of `cluster`-CTA clusters that fits on the
+// device for every u_f instantiation with A_u in a_fmt (0 if none).
+int refine_max_cluster_grid(int a_fmt, int kcap, int cluster);
 size_t refine_smem_bytes(int kcap);
 
 }  // namespace msir

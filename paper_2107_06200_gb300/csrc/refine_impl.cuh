@@ -21,6 +21,8 @@
 #pragma once
 
 #include "common.cuh"
+#include <type_traits>
+
 #include "refine.h"
 
 namespace msir {
@@ -36,6 +38,8 @@ struct Cx {
   unsigned char* tsm;        // shared scratch of the substitutions (kTrsvSmem bytes)
   unsigned char* ssm;        // shared staging of the scaled-block construction (kScaledSmem)
   unsigned mready;           // RefState::mready of this launch (uniform)
+  int C;                     // CTAs per cluster (1: no clusters)
+  unsigned long long* inbox; // [kMaxCluster][kBlk][kLLWords] words written by cluster peers
 };
 
 // Phase timer: CTA 0 / thread 0 accumulates %globaltimer deltas.
@@ -164,16 +168,64 @@ __device__ void rows_dot_d(const A0* const (&row)[NR], const X* x, int n, int la
 #pragma unroll
   for (int r = 0; r < NR; ++r) acc[r] = 0.0;
   const int n4 = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) ? (n & ~3) : 0;
+  if constexpr (sizeof(A0) == 4 && sizeof(X) == 4) {
+    // fp32 matrix and vector: widened by integer instructions (the fp64
+    // pipe then only does the fused multiply-adds); a step with a subnormal,
+    // infinite or NaN operand on any lane takes the hardware conversion.
+    // The step loop is warp-uniform (the vote needs every lane): lanes past
+    // n4 in the last step load nothing and add zeros.  Two accumulators per
+    // row (columns 0, 2 and 1, 3 of each step) keep four independent fp64
+    // chains per warp in flight.
+    double acc2[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc2[r] = 0.0;
 #pragma unroll 2
-  for (int j = lane * 4; j < n4; j += 128) {
-    double xv[4];
-    Ld4<X>::vec(x + j, xv);
+    for (int j0 = 0; j0 < n4; j0 += 128) {
+      const int j = j0 + lane * 4;
+      const bool in = j < n4;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 xf = in ? __ldcg((const float4*)(x + j)) : z4;
+      float4 af[NR];
+      bool sp = widen_special4(xf);
 #pragma unroll
-    for (int r = 0; r < NR; ++r) {
-      double av[4];
-      Ld4<A0>::row(row[r] + j, av);
+      for (int r = 0; r < NR; ++r) {
+        af[r] = in ? __ldg((const float4*)(row[r] + j)) : z4;
+        sp |= widen_special4(af[r]);
+      }
+      if (__any_sync(0xffffffffu, sp)) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) acc[r] = __fma_rn(av[q], xv[q], acc[r]);
+        for (int r = 0; r < NR; ++r) {
+          acc[r] = __fma_rn((double)af[r].x, (double)xf.x, acc[r]);
+          acc2[r] = __fma_rn((double)af[r].y, (double)xf.y, acc2[r]);
+          acc[r] = __fma_rn((double)af[r].z, (double)xf.z, acc[r]);
+          acc2[r] = __fma_rn((double)af[r].w, (double)xf.w, acc2[r]);
+        }
+      } else {
+        const double x0 = widen_normal(xf.x), x1 = widen_normal(xf.y), x2 = widen_normal(xf.z),
+                     x3 = widen_normal(xf.w);
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+          acc[r] = __fma_rn(widen_normal(af[r].x), x0, acc[r]);
+          acc2[r] = __fma_rn(widen_normal(af[r].y), x1, acc2[r]);
+          acc[r] = __fma_rn(widen_normal(af[r].z), x2, acc[r]);
+          acc2[r] = __fma_rn(widen_normal(af[r].w), x3, acc2[r]);
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = __dadd_rn(acc[r], acc2[r]);
+  } else {
+#pragma unroll 2
+    for (int j = lane * 4; j < n4; j += 128) {
+      double xv[4];
+      Ld4<X>::vec(x + j, xv);
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        double av[4];
+        Ld4<A0>::row(row[r] + j, av);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[r] = __fma_rn(av[q], xv[q], acc[r]);
+      }
     }
   }
   for (int j = n4 + lane; j < n; j += 32) {
@@ -522,6 +574,35 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// Distributed shared memory: the address of `p` (this CTA's shared memory)
+// in cluster peer `rank`, a relaxed store there, and a relaxed load of this
+// CTA's own copy that observes such stores.
+__device__ __forceinline__ unsigned peer_addr(const void* p, unsigned rank) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  unsigned r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void st_peer_u64(unsigned addr, unsigned long long v) {
+  asm volatile("st.relaxed.cluster.shared::cluster.u64 [%0], %1;" ::"r"(addr), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_inbox_u64(const unsigned long long* p) {
+  unsigned long long v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.relaxed.cluster.shared::cta.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+  return v;
+}
+// Cluster-wide barrier of all threads (release / acquire at cluster scope).
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Tag of an inbox word: the solve's epoch and the block's round (block /
+// number of teams), bit 31 clear so that it never equals the all-ones fill
+// of a fresh inbox.
+__device__ __forceinline__ unsigned inbox_tag(unsigned epoch, int round) {
+  return ((epoch << 8) | ((unsigned)round & 0xffu)) & 0x7fffffffu;
+}
+
 // Payload words of one block held by one lane: values lane and lane + 32.
 template <int W>
 struct LLRaw {
@@ -587,6 +668,46 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
       if (bad) return false;
     }
     ll_issue<W>(blk, lane, r);
+  }
+  __syncwarp();  // the previous block's staged values have been consumed
+#pragma unroll
+  for (int m = 0; m < 2; ++m) {
+    unsigned p[W];
+#pragma unroll
+    for (int k = 0; k < W; ++k) p[k] = (unsigned)r.w[m][k];
+    stage[lane + 32 * m] = ACC::unword(p);
+  }
+  __syncwarp();
+  return true;
+}
+
+// ll_complete for a block that a cluster peer writes into this CTA's inbox
+// slot: poll shared memory (no L2 round trip) until every word carries
+// `tag`, then stage the values.  Bounded like every device wait.
+template <typename ACC>
+__device__ __forceinline__ bool ib_complete(const unsigned long long* slot, unsigned tag, int lane,
+                                            typename ACC::V* stage, int* err, int where) {
+  constexpr int W = ACC::kW;
+  LLRaw<W> r;
+  unsigned long long t0 = 0;
+  unsigned spins = 0;
+  while (true) {
+#pragma unroll
+    for (int m = 0; m < 2; ++m)
+#pragma unroll
+      for (int k = 0; k < W; ++k) r.w[m][k] = ld_inbox_u64(slot + (size_t)(lane + 32 * m) * W + k);
+    if (ll_ready<W>(r, tag)) break;
+    if ((++spins & 1023u) == 0u) {
+      int bad = 0;
+      if (lane == 0) {
+        if (t0 == 0) t0 = gtimer();
+        if (ld_volatile_i32(err) != 0) bad = 1;
+        else if (gtimer() - t0 > kWaitTimeoutNs) bad = 2;
+      }
+      bad = __shfl_sync(0xffffffffu, bad, 0);
+      if (bad == 2 && lane == 0) record_timeout(err, 2, where, (int)tag, -1);
+      if (bad) return false;
+    }
   }
   __syncwarp();  // the previous block's staged values have been consumed
 #pragma unroll
@@ -747,13 +868,31 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
   const int T = cx.G / K;
   const int team = cx.cta / K, member = cx.cta % K;
   const int nmine = team < T && team < cx.nblk ? (cx.nblk - 1 - team) / T + 1 : 0;
+  // Clusters (cx.C > 1, K | C): the C / K teams of a cluster own
+  // consecutive blocks of each round, and a team takes the blocks of the
+  // teams before it in its cluster (forward; after it, backward) from its
+  // inbox, where their owners write them through distributed shared memory,
+  // instead of from the L2 hand-off words.  Every block is also published to
+  // L2 for the other clusters.
+  const bool clus = cx.C > 1 && K <= cx.C;
+  const int TPC = clus ? cx.C / K : 1;  // teams per cluster
+  const int tpos = team % TPC;          // this team's position in its cluster
   for (int q = 0; q < nmine; ++q) {
     const int b = LOWER ? team + q * T : team + (nmine - 1 - q) * T;
     const int r0 = b * kBlk;
     const int nr = min(kBlk, n - r0);
     const int rr = member * R + r;  // row within the block
     const int row = r0 + rr;
-    unsigned long long* ts = a.tsv ? a.tsv + ((LOWER ? 0 : 1) * (size_t)cx.nblk + b) * 3 : nullptr;
+    const unsigned itag = inbox_tag(epoch, b / T);
+    // dependencies taken from the inbox: forward b - tpos .. b - 1, backward
+    // b + 1 .. b + TPC - 1 - tpos (the same round, this cluster)
+    const int ib_lo = LOWER ? b - tpos : b + 1;
+    const int ib_hi = LOWER ? b - 1 : b + (TPC - 1 - tpos);
+    auto from_inbox = [&](int j) { return clus && j >= ib_lo && j <= ib_hi; };
+    auto inbox_slot = [&](int j) {  // the source team's position
+      return cx.inbox + (size_t)(tpos + (j - b)) * kBlk * W;
+    };
+    unsigned long long* ts = a.tsv ? a.tsv + ((LOWER ? 0 : 1) * (size_t)cx.nblk + b) * 4 : nullptr;
     if (ts && cx.tid == 0 && member == 0) ts[0] = gtimer();
     bool ok = true;  // a failed wait ends the warp's work; the CTA leaves together below
     // w_r = (row rr of inv(D_b)) c_b
@@ -788,7 +927,9 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
     const V wr = ACC::fin(wa);
     // dependencies in the order they become available
     const int ndep = LOWER ? b : cx.nblk - 1 - b;
-    typename ACC::A acc = ACC::azero();
+    // two interleaved partial sums (even and odd columns), merged at the
+    // end: the tile product on the dependency chain is half as deep
+    typename ACC::A acc = ACC::azero(), acc2 = ACC::azero();
     // fp32/fp64 tiles of at most a sixth of the staging area stream through a
     // ring in shared memory; wider ones (fp64 without teams) and dd tiles
     // are loaded into registers
@@ -821,12 +962,12 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
         for (int t = 0; t < kTileRing - 1; ++t) issue(t);
         LLRaw<W> pc, pn;
         int jb = LOWER ? 0 : cx.nblk - 1;
-        ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
+        if (!from_inbox(jb)) ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
         for (int t = 0; t < ndep; ++t) {
           const int jn = LOWER ? jb + 1 : jb - 1;
           const bool more = t + 1 < ndep;
           issue(t + kTileRing - 1);
-          if (more) ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
+          if (more && !from_inbox(jn)) ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
           cp_async_wait<kTileRing - 1>();  // this thread's copies of tile t are done
           Tm tc[NC];
           const Tm* slot = ring + (size_t)(t % kTileRing) * NCH * NACT * EPC;
@@ -834,14 +975,19 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
           for (int c = 0; c < NCH; ++c)
 #pragma unroll
             for (int e = 0; e < EPC; ++e) tc[c * EPC + e] = slot[((size_t)c * NACT + cx.tid) * EPC + e];
-          if (!ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err,
-                                (tri << 24) | (b << 12) | jb)) {
+          const int where = (tri << 24) | (b << 12) | jb;
+          if (!(from_inbox(jb) ? ib_complete<ACC>(inbox_slot(jb), itag, cx.lane, stage, a.err, where | (1 << 22))
+                               : ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err, where))) {
             ok = false;
             break;
           }
+          if (ts && !more && cx.tid == 0 && member == 0) ts[3] = gtimer();
           const V* ys = stage + seg * NC;
 #pragma unroll
-          for (int k = 0; k < NC; ++k) acc = ACC::tfma(tc[k], ys[k], acc);
+          for (int k = 0; k < NC; k += 2) {
+            acc = ACC::tfma(tc[k], ys[k], acc);
+            acc2 = ACC::tfma(tc[k + 1], ys[k + 1], acc2);
+          }
           if (!more) break;
           pc = pn;
           jb = jn;
@@ -856,22 +1002,27 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
         LLRaw<W> pc, pn;
         int jb = LOWER ? 0 : cx.nblk - 1;
         ACC::template tile<NC>(a, n, row, jb * kBlk + seg * NC, tc);
-        ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
+        if (!from_inbox(jb)) ll_issue<W>(ll_y + (size_t)jb * llblk, cx.lane, pc);
         for (int t = 0; t < ndep; ++t) {
           const int jn = LOWER ? jb + 1 : jb - 1;
           const bool more = t + 1 < ndep;
           if (kDouble && more) {
             ACC::template tile<NC>(a, n, row, jn * kBlk + seg * NC, *(Tm(*)[NC])tn);
-            ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
+            if (!from_inbox(jn)) ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pn);
           }
-          if (!ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err,
-                                (tri << 24) | (b << 12) | jb)) {
+          const int where = (tri << 24) | (b << 12) | jb;
+          if (!(from_inbox(jb) ? ib_complete<ACC>(inbox_slot(jb), itag, cx.lane, stage, a.err, where | (1 << 22))
+                               : ll_complete<ACC>(ll_y + (size_t)jb * llblk, epoch, cx.lane, pc, stage, a.err, where))) {
             ok = false;
             break;
           }
+          if (ts && !more && cx.tid == 0 && member == 0) ts[3] = gtimer();
           const V* ys = stage + seg * NC;
 #pragma unroll
-          for (int k = 0; k < NC; ++k) acc = ACC::tfma(tc[k], ys[k], acc);
+          for (int k = 0; k < NC; k += 2) {
+            acc = ACC::tfma(tc[k], ys[k], acc);
+            acc2 = ACC::tfma(tc[k + 1], ys[k + 1], acc2);
+          }
           if (!more) break;
           if (kDouble) {
 #pragma unroll
@@ -879,12 +1030,13 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
             pc = pn;
           } else {
             ACC::template tile<NC>(a, n, row, jn * kBlk + seg * NC, tc);
-            ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pc);
+            if (!from_inbox(jn)) ll_issue<W>(ll_y + (size_t)jn * llblk, cx.lane, pc);
           }
           jb = jn;
         }
       }
     }
+    acc = ACC::merge(acc, acc2);
     if (ts && cx.tid == 0 && member == 0) ts[1] = gtimer();
     if (act && ok) {
       // the TPR segments of the row: s_r, then y_r = S(T(w_r - s_r))
@@ -896,6 +1048,19 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
       if (seg < W)
         st_relaxed_u64(ll_y + (size_t)b * llblk + (size_t)rr * W + seg,
                        ((unsigned long long)epoch << 32) | ACC::word(y, seg));
+      if (clus) {
+        // and into the inboxes of the cluster's teams that take this block
+        // next (their K members each): word k of the row for target CTA c,
+        // spread over the row's TPR threads
+        const int nteams = LOWER ? min(TPC - 1 - tpos, cx.nblk - 1 - b) : tpos;
+        const unsigned long long* dst = cx.inbox + ((size_t)tpos * kBlk + rr) * W;
+        for (int e = seg; e < nteams * K * W; e += TPR) {
+          const int ci = e / W, k = e % W;
+          const int cpos = LOWER ? tpos + 1 + ci / K : tpos - 1 - ci / K;
+          st_peer_u64(peer_addr(dst + k, (unsigned)(cpos * K + ci % K)),
+                      ((unsigned long long)itag << 32) | ACC::word(y, k));
+        }
+      }
       if (seg == 0 && rr < nr) ACC::save(out_hi, out_lo, row, y);
     }
     if (ts && cx.tid == 0 && member == 0) ts[2] = gtimer();
@@ -906,19 +1071,24 @@ __device__ __noinline__ bool trsv_team(Cx& cx, const RefineArgs& a, int store_fm
 
 // Team size of a solve in arithmetic ACC: fp32 solves keep one CTA per
 // block (their products are cheap; teams need two grid barriers per
-// solve); fp64 and dd solves use the largest K in {8, 4, 2} for which each
-// team owns at most two blocks, else 1 (the products of a block, not the
-// hand-offs, bound these solves, so splitting them pays even when a team
-// then works through two blocks).
+// solve).  fp64 and dd solves split each block's rows over K CTAs, which
+// shortens the tile product on the dependency chain K-fold (on GB300's
+// narrow fp64 pipe it costs more than the hand-off): K = 8 when each team
+// then owns at most two blocks, else 4 when each owns at most four, else 2.
+// Measured (one GPU, fp64 solves at n = 8192, dd solves at n = 4096): K = 4
+// beats K = 2 by 15-20 %; K = 8, whose teams then own 7 or 4 blocks,
+// gains nothing more.
 template <typename ACC>
 __device__ __forceinline__ int team_size(const Cx& cx) {
   if (ACC::kW == 1) return 1;
-  if (cx.team_k > 0) return cx.team_k <= cx.G ? cx.team_k : 1;
-  const int half = (cx.nblk + 1) / 2;
-  if (cx.G / 8 >= half) return 8;
-  if (cx.G / 4 >= half) return 4;
-  if (cx.G / 2 >= half) return 2;
-  return 1;
+  int k;
+  if (cx.team_k > 0) {
+    k = cx.team_k <= cx.G ? cx.team_k : 1;
+  } else {
+    const int half = (cx.nblk + 1) / 2, quarter = (cx.nblk + 3) / 4;
+    k = cx.G / 8 >= half ? 8 : (cx.G / 4 >= quarter ? 4 : (cx.G >= 2 ? 2 : 1));
+  }
+  return cx.C > 1 ? min(k, cx.C) : k;  // a team stays inside one cluster
 }
 
 template <typename F, typename ACC, bool LOWER>
@@ -1000,7 +1170,7 @@ static __device__ __forceinline__ double cscale(const RefineArgs& a, int col) {
 // ferr = ||x - x_ref||_inf / ||x_ref||_inf.  The caller has made x complete
 // (barrier).
 template <typename A0>
-__device__ bool residual(Cx& cx, const RefineArgs& a, const double* x, int ur, double& s,
+__device__ __noinline__ bool residual(Cx& cx, const RefineArgs& a, const double* x, int ur, double& s,
                          double& xnorm, double* ferr = nullptr) {
   PhaseTimer pt(cx, 0);
   const A0* A = (const A0*)a.A;
@@ -1099,7 +1269,7 @@ template <> struct UA<double> {
 // the substitution); FP64 / DD: rows over every warp of the grid, followed
 // by a grid barrier.
 template <typename A0, typename U>
-__device__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
+__device__ __noinline__ bool apply_A(Cx& cx, const RefineArgs& a, const U* v, int op) {
   PhaseTimer pt(cx, 4);
   const A0* A = (const A0*)a.A;
   if (op == MSIR_FP32) {
@@ -1239,65 +1409,168 @@ __device__ bool cgs_reduce(Cx& cx, const RefineArgs& a, int kp1, U* s_h) {
   return true;
 }
 
-// partial sums p_j = sum over my rows of V_j[i] * w[i], j = 0..k.  Sums are
-// accumulated in fp64 (a product of two fp32 values is exact in fp64), then
-// rounded to u, as the oracle's reading of "inner products in u" states.
+// partial sums p_j = sum over my rows of V_j[i] * w[i], j = 0..k, then
+// summed over the CTAs in fp64 and rounded to u (the oracle's reading of
+// "inner products in u": an accurate sum rounded once).  u = fp64: fp64
+// sums.  u = fp32: compensated fp32 sums (Dot2: every product's and
+// addition's rounding error kept in a second word), passed on as the fp64
+// value s + c; fp64 arithmetic on fp32 data spends most of its time
+// widening operands on GB300's narrow fp64 pipe.
+//
+// The phase is bound by load latency, not bandwidth: each thread takes
+// kVec consecutive basis vectors (one 16-byte load per row; the basis is
+// row-major with ldv a multiple of 32) and loads kChunk rows ahead of the
+// sums, so a CTA keeps about 50 KB of loads in flight.
 template <typename U>
-__device__ void cgs_partials(Cx& cx, const RefineArgs& a, const U* V, const U* w, int kp1) {
+__device__ __noinline__ void cgs_partials(Cx& cx, const RefineArgs& a, const U* V, const U* w, int kp1) {
   PhaseTimer pt(cx, 3);
-  // one thread per basis vector: its dot product with w over this CTA's
-  // flat rows, in row order (the loads are independent of the running sum)
+  constexpr int kVec = 16 / (int)sizeof(U);
+  constexpr int kChunk = 12;
+  using Vec = typename std::conditional<sizeof(U) == 4, float4, double2>::type;
   int r0, r1;
   flat_rows(cx, r0, r1);
-  // (the basis is row-major, so a warp's loads of one row are coalesced)
-  for (int j = cx.tid; j < kp1; j += kRefThreads) {
-    double acc = 0.0;
-#pragma unroll 16
-    for (int i = r0; i < r1; ++i)
-      acc = __fma_rn((double)__ldcg(V + (size_t)i * a.ldv + j), (double)__ldcg(w + i), acc);
-    a.hred[(size_t)cx.cta * (a.kcap + 1) + j] = acc;
+  const int nq = (kp1 + kVec - 1) / kVec;
+  for (int jq = cx.tid; jq < nq; jq += kRefThreads) {
+    const int j0 = jq * kVec;
+    // columns j0 .. j0 + kVec - 1 (those past k are summed and not stored)
+    ff_t af[kVec];
+    double ad[kVec];
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) {
+      af[e] = ff_t{0.0f, 0.0f};
+      ad[e] = 0.0;
+    }
+    for (int i0 = r0; i0 < r1; i0 += kChunk) {
+      U vv[kChunk][kVec], wv[kChunk];
+#pragma unroll
+      for (int c = 0; c < kChunk; ++c) {
+        const int i = i0 + c;
+        if (i < r1) {
+          const Vec t = __ldcg((const Vec*)(V + (size_t)i * a.ldv + j0));
+          const U* tp = (const U*)&t;
+#pragma unroll
+          for (int e = 0; e < kVec; ++e) vv[c][e] = tp[e];
+          wv[c] = __ldcg(w + i);
+        } else {
+#pragma unroll
+          for (int e = 0; e < kVec; ++e) vv[c][e] = (U)0;
+          wv[c] = (U)0;
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < kChunk; ++c)
+#pragma unroll
+        for (int e = 0; e < kVec; ++e) {
+          if constexpr (sizeof(U) == 4) af[e] = ff_fma(vv[c][e], wv[c], af[e]);
+          else ad[e] = __fma_rn(vv[c][e], wv[c], ad[e]);
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) {
+      if (j0 + e >= kp1) break;
+      a.hred[(size_t)cx.cta * (a.kcap + 1) + j0 + e] =
+          sizeof(U) == 4 ? __dadd_rn((double)af[e].s, (double)af[e].c) : ad[e];
+    }
   }
 }
 
 // sum_j V_j[i] c_j for the rows i0 .. i0+kRows-1 (those below r1) by one
-// warp: lane l sums j = l, l+32, ... in order, then a butterfly over the
-// lanes.  The rows' loads and reductions are independent, so their
-// latencies overlap.  Lane q < kRows returns row i0+q.
+// warp: lane l sums the columns 4l .. 4l+3 (fp64: 2l, 2l+1) of every
+// 128-column (64) step, in order, with 16-byte loads two steps ahead, then a
+// butterfly over the lanes.  The rows' loads and reductions are
+// independent, so their latencies overlap.  Lane q < kRows returns row
+// i0+q's sum as a compensated pair (u = fp32: Dot2 in fp32, the pair's sum
+// is the value; u = fp64: an fp64 sum in .s, .c = 0).
 constexpr int kRows = 8;
+struct RowSum {
+  double s, c;
+};
 template <typename U>
-__device__ __forceinline__ double basis_rows_dot(const RefineArgs& a, const U* V, int i0, int r1, int kp1,
+__device__ __forceinline__ RowSum basis_rows_dot(const RefineArgs& a, const U* V, int i0, int r1, int kp1,
                                                  const U* c, int lane) {
-  double acc[kRows];
-#pragma unroll
-  for (int q = 0; q < kRows; ++q) acc[q] = 0.0;
-  for (int j = lane; j < kp1; j += 32) {
-    const double cj = (double)c[j];
-#pragma unroll
-    for (int q = 0; q < kRows; ++q)
-      if (i0 + q < r1) acc[q] = __fma_rn((double)__ldcg(V + (size_t)(i0 + q) * a.ldv + j), cj, acc[q]);
-  }
-  double mine = 0.0;
+  constexpr int kVec = 16 / (int)sizeof(U);
+  constexpr int kStep = 32 * kVec;
+  using Vec = typename std::conditional<sizeof(U) == 4, float4, double2>::type;
+  ff_t af[kRows];
+  double ad[kRows];
 #pragma unroll
   for (int q = 0; q < kRows; ++q) {
-    const double t = warp_sum_d(acc[q]);
-    if (lane == q) mine = t;
+    af[q] = ff_t{0.0f, 0.0f};
+    ad[q] = 0.0;
+  }
+  const int nr = min(kRows, r1 - i0);
+#pragma unroll 2
+  for (int j0 = lane * kVec; j0 < kp1; j0 += kStep) {
+    U vv[kRows][kVec], cj[kVec];
+#pragma unroll
+    for (int e = 0; e < kVec; ++e) cj[e] = j0 + e < kp1 ? c[j0 + e] : (U)0;
+#pragma unroll
+    for (int q = 0; q < kRows; ++q) {
+      if (q < nr) {
+        const Vec t = __ldcg((const Vec*)(V + (size_t)(i0 + q) * a.ldv + j0));
+        const U* tp = (const U*)&t;
+#pragma unroll
+        for (int e = 0; e < kVec; ++e) vv[q][e] = j0 + e < kp1 ? tp[e] : (U)0;  // columns past k may hold anything
+      } else {
+#pragma unroll
+        for (int e = 0; e < kVec; ++e) vv[q][e] = (U)0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kRows; ++q)
+#pragma unroll
+      for (int e = 0; e < kVec; ++e) {
+        if constexpr (sizeof(U) == 4) af[q] = ff_fma(vv[q][e], cj[e], af[q]);
+        else ad[q] = __fma_rn(vv[q][e], cj[e], ad[q]);
+      }
+  }
+  RowSum mine{0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < kRows; ++q) {
+    if constexpr (sizeof(U) == 4) {
+#pragma unroll
+      for (int m = 16; m > 0; m >>= 1) af[q] = ff_merge(af[q], ff_shfl_xor(af[q], m));
+      if (lane == q) mine = RowSum{(double)af[q].s, (double)af[q].c};
+    } else {
+      const double t = warp_sum_d(ad[q]);
+      if (lane == q) mine.s = t;
+    }
   }
   return mine;
 }
 
-// w_i = fl_u(w_i - sum_j V_j[i] h_j), the sum in fp64; flat rows, kRows
-// rows per warp at a time
+// w_i = fl_u(w_i - sum_j V_j[i] h_j) with the difference taken from the
+// accurate sum (fp32: w - (s + c) by ff_sub_from); flat rows, kRows rows
+// per warp at a time
 template <typename U>
-__device__ void cgs_update(Cx& cx, const RefineArgs& a, const U* V, U* w, int kp1, const U* s_h) {
+__device__ __noinline__ void cgs_update(Cx& cx, const RefineArgs& a, const U* V, U* w, int kp1, const U* s_h) {
   PhaseTimer pt(cx, 3);
   int r0, r1;
   flat_rows(cx, r0, r1);
   for (int i0 = r0 + cx.warp * kRows; i0 < r1; i0 += (kRefThreads / 32) * kRows) {
-    const double acc = basis_rows_dot<U>(a, V, i0, r1, kp1, s_h, cx.lane);
+    const RowSum acc = basis_rows_dot<U>(a, V, i0, r1, kp1, s_h, cx.lane);
     const int i = i0 + cx.lane;
-    if (cx.lane < kRows && i < r1) w[i] = UA<U>::rnd(__dsub_rn((double)w[i], acc));
+    if (cx.lane < kRows && i < r1) {
+      if constexpr (sizeof(U) == 4)
+        w[i] = ff_sub_from(w[i], ff_t{(float)acc.s, (float)acc.c});
+      else
+        w[i] = UA<U>::rnd(__dsub_rn((double)w[i], acc.s));
+    }
   }
   __syncthreads();
+}
+
+// d_i = fl_u(sum_j V_j[i] y_j) over the flat rows (the GMRES correction)
+template <typename U>
+__device__ __noinline__ void basis_combine(Cx& cx, const RefineArgs& a, const U* V, int kdone, const U* y) {
+  int f0, f1;
+  flat_rows(cx, f0, f1);
+  for (int i0 = f0 + cx.warp * kRows; i0 < f1; i0 += (kRefThreads / 32) * kRows) {
+    const RowSum acc = basis_rows_dot<U>(a, V, i0, f1, kdone, y, cx.lane);
+    const int i = i0 + cx.lane;
+    if (cx.lane < kRows && i < f1)
+      a.d[i] = sizeof(U) == 4 ? (double)ff_fin(ff_t{(float)acc.s, (float)acc.c}) : (double)UA<U>::rnd(acc.s);
+  }
 }
 
 template <typename U>
@@ -1470,11 +1743,7 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
   if (!grid_barrier(a.bar, a.err, cx.G)) return false;
   for (int j = cx.tid; j < kdone; j += kRefThreads) s_h[j] = (U)__ldcg(a.yv + j);
   __syncthreads();
-  for (int i0 = f0 + cx.warp * kRows; i0 < f1; i0 += (kRefThreads / 32) * kRows) {
-    const double acc = basis_rows_dot<U>(a, V, i0, f1, kdone, s_h, cx.lane);
-    const int i = i0 + cx.lane;
-    if (cx.lane < kRows && i < f1) a.d[i] = (double)M::rnd(acc);
-  }
+  basis_combine<U>(cx, a, V, kdone, s_h);
   out.k = kdone;
   return grid_barrier(a.bar, a.err, cx.G);  // d is read by the block partition
 }
@@ -1531,7 +1800,7 @@ template <typename A0, typename F>
 // of one system then slow the other's.)
 __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  unsigned char* gsm = smem_raw + kTrsvSmem + kScaledSmem;  // GMRES scalars
+  unsigned char* gsm = smem_raw + kTrsvSmem + kScaledSmem + kInboxSmem;  // GMRES scalars
   __shared__ RefState S;
   __shared__ int s_act, s_reset, s_alg;
 
@@ -1547,6 +1816,19 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   cx.nblk = (a.n + kBlk - 1) / kBlk;
   cx.team_k = a.team_k;
   cx.redbuf = 0;
+  cx.inbox = (unsigned long long*)(smem_raw + kTrsvSmem + kScaledSmem);
+  cx.C = 1;
+  if (a.cluster > 1) {
+    // the inbox starts all ones (a tag no hand-off uses); peers write into
+    // it only after every CTA of the cluster has filled its own
+    for (int i = cx.tid; i < kInboxSmem / 8; i += kRefThreads) cx.inbox[i] = ~0ull;
+    unsigned rank, nrank;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(nrank));
+    // the block-to-team mapping assumes rank = block index mod cluster size
+    if ((int)nrank == a.cluster && (int)rank == cx.cta % a.cluster && a.cluster <= kMaxCluster) cx.C = a.cluster;
+    cluster_sync_all();
+  }
   if (cx.tid == 0) S = *a.st;
   __syncthreads();
   cx.epoch = S.epoch;
@@ -1791,6 +2073,9 @@ finish:
   }
   __syncthreads();
   if (cx.cta == 0 && cx.tid == 0) *a.st = S;
+  // no CTA leaves while a cluster peer may still write into its inbox (every
+  // wait before this point is bounded, so every peer arrives)
+  if (a.cluster > 1) cluster_sync_all();
 }
 
 // Entry point of one instantiation (defined in refine_<a>_<f>.cu).

@@ -551,6 +551,58 @@ def test_server_with_a_tight_budget_runs_one_request_at_a_time(ctx, M):
         srv.close()
 
 
+def test_integer_widening_matches_the_hardware_conversion(M):
+    """The fp64 operator on fp32 data widens operands with integer
+    instructions; on all 2^32 fp32 bit patterns that widening equals the
+    hardware conversion, and exactly the subnormals, infinities and NaNs are
+    left to the hardware."""
+    bad, checked = M.probe_widen_check(0)
+    assert bad == 0
+    # 2^32 minus the 2 (2^23 - 1) subnormals, 2 infinities and 2 (2^23 - 1) NaNs
+    assert checked == 2 ** 32 - 2 * (2 ** 23 - 1) - 2 - 2 * (2 ** 23 - 1)
+
+
+def test_server_backlog_limit_refuses_and_the_rest_finish(ctx, M):
+    """With a backlog limit, a submission is refused (MSIR_ERR_BUSY, nothing
+    queued) once the queued work exceeds the limit at the server's measured
+    completion rate; before 4 completions there is no rate and every
+    submission is queued.  Every accepted request finishes with the result of
+    solving it alone."""
+    import time
+    from paper_2107_06200_gb300 import MsirError
+    srv = M.Server(ctx, max_slots=1, max_backlog_ms=1.0)
+    try:
+        A, B, _ = randsvd_system(256, 1e2, 300)
+        b = B[:, 0].copy()
+
+        def wait(t):
+            t0 = time.time()
+            while time.time() - t0 < 60:
+                state, x, rep, lat = srv.poll(t, 256)
+                if state == 2:
+                    return x, rep
+                time.sleep(0.002)
+            raise AssertionError("request did not finish")
+
+        first = [srv.submit(A, b, HSD) for _ in range(5)]  # no rate yet: all queued
+        results = [wait(t) for t in first]
+        accepted, refused = [], 0
+        for _ in range(12):
+            try:
+                accepted.append(srv.submit(A, b, HSD))
+            except MsirError as e:
+                assert e.code == -7
+                refused += 1
+        assert refused >= 1 and len(accepted) >= 1
+        results += [wait(t) for t in accepted]
+        x1, r1, _ = ctx.solve(to_dev(A), to_dev(b), HSD)
+        for x, rep in results:
+            assert rep["call_status"] >= 0
+            same_result(A, b, _trip(M, HSD)[1], x, rep, x1.cpu().numpy(), r1[0])
+    finally:
+        srv.close()
+
+
 @pytest.mark.parametrize("n,kappa,spec", [(100, 1e2, HSD), (100, 1e4, HSD), (150, 1e9, SDQ), (120, 1e6, HDQ)])
 def test_true_convergence_mode(ctx, M, n, kappa, spec):
     """The stopping rule of the paper's experiments (Sec. 3): converged when

@@ -111,26 +111,34 @@ def test_overloaded_server_queues_and_the_byte_cap_rejects():
 
 
 def test_server_back_pressure_counts_as_rejected():
-    """A submission the server refuses with MSIR_ERR_NOMEM (its bound on held
-    host copies) is a rejected arrival, not an error of the harness."""
+    """A submission the server refuses with MSIR_ERR_BUSY (its bound on held
+    host copies or on queued work) or MSIR_ERR_NOMEM (no host memory for the
+    copy) is a rejected arrival, not an error of the harness; any other error
+    propagates."""
     import bench
 
     class Refusing:
-        def __init__(self):
+        def __init__(self, codes):
             self.calls = 0
+            self.codes = list(codes)
 
         def submit(self, A, b, spec):
             self.calls += 1
-            err = RuntimeError("server_submit: out of device memory (-2)")
-            err.code = -2
+            err = RuntimeError("server_submit: refused")
+            err.code = self.codes.pop(0)
             raise err
 
         def poll(self, t, n):
             raise AssertionError("nothing was queued")
 
     A = np.eye(4)
-    srv = Refusing()
+    srv = Refusing([-7, -2])
     clock = iter([0.0, 0.0, 0.5, 0.6, 1.5, 2.5, 3.0]).__next__
     recs = bench.run_serving(srv, [(A, np.ones(4), "fp16,fp32,fp64")], [0.1, 0.4], [0, 0], 1.0, None,
                              clock=clock, sleep=lambda s: None)
     assert srv.calls == 2 and [r["status"] for r in recs] == ["rejected", "rejected"]
+    srv = Refusing([-1])
+    clock = iter([0.0, 0.0, 0.5, 0.6, 1.5, 2.5, 3.0]).__next__
+    with pytest.raises(RuntimeError):
+        bench.run_serving(srv, [(A, np.ones(4), "fp16,fp32,fp64")], [0.1], [0], 1.0, None,
+                          clock=clock, sleep=lambda s: None)
