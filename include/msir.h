@@ -253,14 +253,38 @@ msir_status msir_solve_host(msir_ctx* ctx, int n, const double* A_host, int lda,
 /* Solves `count` independent systems of possibly different sizes.  n[i],
  * A_dev[i] (n[i] x n[i], column-major, lda = n[i]), b_dev[i], x_dev[i]
  * (n[i] doubles) and t[i] are host arrays of device pointers / values;
- * reps: count reports (may be NULL).  Systems are grouped and their
- * refinement runs as persistent launches over groups of SMs.  Returns
- * MSIR_OK if all converged, MSIR_NOT_CONVERGED if some did not.
- * MSIR_CONV_TRUE is not accepted here (MSIR_ERR_INVALID). */
+ * reps: count reports (may be NULL).
+ * Systems with n <= 512 go to the batched engine: one persistent launch per
+ * working precision u (captured in a CUDA graph), in which each thread
+ * block takes the next system and runs all of Algorithm 4 on it (ingest,
+ * the LU of msir_factor_batched, the factor check and squeezed retry, SIR /
+ * SGMRES-IR / GMRES-IR with the stopping logic, escalation of u_f with
+ * refactoring on the device).  A cost-aware k_max (kmax_frac < 0) is taken
+ * there as the fixed k_max = |kmax_frac| n.  Larger systems share the GPU
+ * as concurrent solves whose refinement runs as persistent launches over
+ * groups of SMs.  Returns MSIR_OK if all converged, MSIR_NOT_CONVERGED if
+ * some did not.  MSIR_CONV_TRUE is not accepted here (MSIR_ERR_INVALID). */
 msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n,
                                const double* const* A_dev, const double* const* b_dev,
                                double* const* x_dev, const msir_triple* t,
                                const msir_params* params, msir_report* reps);
+
+/* Batched LU, the factorisation of the batched engine (Algorithm 4's first
+ * step for many small systems in one launch; Sec. 1).  System i:
+ * A_dev[i] is n[i] x n[i] fp64 column-major (lda = n[i]), 1 <= n[i] <= 512;
+ * it is rounded to u_f = fmt (bf16 / fp16 through fp32) and factored by one
+ * thread block with blocking nb, nbo (<= 0: 32, or 16 for fp64, and 64;
+ * nb <= 32 (16), nbo a multiple of nb, nbo <= 64).  The bf16 / fp16 outer
+ * trailing update is the fp32 fused multiply-add chain in ascending order
+ * (no tensor cores).  Outputs, device memory the caller owns: F_dev[i] n x n
+ * fp64 row-major, the stored u_f values of L (strictly lower, unit diagonal
+ * implied) and U; ipiv_dev[i] n ints, LAPACK-style (row j was swapped with
+ * row ipiv[j], 0-based); flags_dev[i] 2 ints: the first zero pivot
+ * (1-based, 0: none) and 1 if a stored value is Inf or NaN.  Blocks until
+ * done.  MSIR_ERR_INVALID for bad arguments. */
+msir_status msir_factor_batched(msir_ctx* ctx, int count, const int* n, const double* const* A_dev, int fmt,
+                                int nb, int nbo, double* const* F_dev, int* const* ipiv_dev,
+                                int* const* flags_dev);
 
 /* Continuous-batching solve server on the context's device.
  * hbm_budget_bytes: device memory the server may hold (0 = 90% of the free

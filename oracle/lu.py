@@ -138,7 +138,7 @@ def _update(F, r0, w, c0, c1, fmt_f, tensor_core=False):
     F[r0 + w:, c0:c1] = fl(upd, fmt_f).astype(np.float64)
 
 
-def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None):
+def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None, outer_tc=True):
     """Factor A (float32/float64 array of working-precision values).
 
     Two-level right-looking blocking: outer blocks of nbo columns, each
@@ -147,6 +147,10 @@ def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None):
     applied to the other columns, U12 is formed by substitution with the
     nbo x nbo unit lower block and the trailing matrix is updated with K =
     nbo.  nbo = nb gives the one-level algorithm.
+
+    outer_tc=False models the bf16 / fp16 outer update like the others (the
+    fp32 fused multiply-add chain in ascending order), as a factorisation
+    without tensor cores computes it (the library's batched engine).
 
     Returns (F, ipiv, info): F float64 n x n holding the stored u_f values of
     L (strictly lower, unit diagonal implied) and U; ipiv int64; info = 1-based
@@ -176,7 +180,7 @@ def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None):
             _swap_cols(F, ipiv, k, W, 0, k)
             _swap_cols(F, ipiv, k, W, k + W, n)
             _trsm(F, k, W, k + W, n, T, fmt_f)
-            _update(F, k, W, k + W, n, fmt_f, tensor_core=fmt_f in (FP16, BF16))
+            _update(F, k, W, k + W, n, fmt_f, tensor_core=outer_tc and fmt_f in (FP16, BF16))
     return F, ipiv, info
 
 

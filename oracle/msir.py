@@ -78,6 +78,7 @@ class Params:
     nb: int = 0               # <= 0: default for u_f (lu.default_blocking)
     nbo: int = 0
     allow_escalation: bool = True
+    outer_tc: bool = True     # bf16 / fp16 outer update on tensor cores (lu.lu_factor)
 
 
 @dataclass
@@ -122,18 +123,18 @@ class Result:
     history: list
 
 
-def factorize(A_u, fmt_f, nb=0, nbo=0):
+def factorize(A_u, fmt_f, nb=0, nbo=0, outer_tc=True):
     """LU in u_f with the factor check and one squeezed retry (R10).
 
     Returns (Factorization or None, scaled_flag)."""
-    F, ipiv, info = lu_mod.lu_factor(A_u, fmt_f, nb or None, nbo or None)
+    F, ipiv, info = lu_mod.lu_factor(A_u, fmt_f, nb or None, nbo or None, outer_tc=outer_tc)
     if lu_mod.factors_finite(F) and info == 0:
         return Factorization(fmt_f, F, ipiv, lu_mod.ipiv_to_perm(ipiv), info), False
     if fmt_f == FP64:
         return None, False
     R, S, mu = sq_mod.scalings(A_u, fmt_f)
     B = sq_mod.scaled_matrix(A_u, R, S, mu)
-    F, ipiv, info = lu_mod.lu_factor(B.astype(np.float32), fmt_f, nb or None, nbo or None)
+    F, ipiv, info = lu_mod.lu_factor(B.astype(np.float32), fmt_f, nb or None, nbo or None, outer_tc=outer_tc)
     if lu_mod.factors_finite(F) and info == 0:
         return Factorization(fmt_f, F, ipiv, lu_mod.ipiv_to_perm(ipiv), info, R, S, mu), True
     return None, True
@@ -273,7 +274,7 @@ def msir(A_in, b_in, triple, params=None, x_ref=None, factor_hook=None):
             if hooked is not None:
                 scaled_flags.append(False)
                 return hooked
-            fac, sc = factorize(A_u.astype(arith_dtype(u0)), fmt, p.nb, p.nbo)
+            fac, sc = factorize(A_u.astype(arith_dtype(u0)), fmt, p.nb, p.nbo, p.outer_tc)
             scaled_flags.append(sc)
             if fac is not None:
                 return fac

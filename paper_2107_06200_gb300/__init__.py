@@ -281,6 +281,31 @@ class Context:
                     "solve_batched")
         return xs, [report_to_dict(reps[i]) for i in range(cnt)], st
 
+    def factor_batched(self, As, fmt, nb=0, nbo=0):
+        """msir_factor_batched: As, a list of (n_i x n_i) fp64 torch cuda
+        tensors; fmt, the u_f name or code.  Returns a list of (F (fp64 row-
+        major, L below and U on and above the diagonal), ipiv, info,
+        nonfinite), torch tensors on the device."""
+        import torch
+        cnt = len(As)
+        code = PREC_CODES[fmt] if isinstance(fmt, str) else int(fmt)
+        Acs = [_colmajor(A) for A in As]
+        Fs = [torch.empty((A.shape[0], A.shape[0]), dtype=torch.float64, device=A.device) for A in As]
+        ips = [torch.empty(A.shape[0], dtype=torch.int32, device=A.device) for A in As]
+        fls = [torch.empty(2, dtype=torch.int32, device=A.device) for A in As]
+        ns = (ctypes.c_int * cnt)(*[A.shape[0] for A in As])
+        Ap = (ctypes.c_void_p * cnt)(*[A.data_ptr() for A in Acs])
+        Fp = (ctypes.c_void_p * cnt)(*[F.data_ptr() for F in Fs])
+        Ip = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in ips])
+        Gp = (ctypes.c_void_p * cnt)(*[t.data_ptr() for t in fls])
+        _inputs_ready()
+        _check(_L.msir_factor_batched(self.h, cnt, ns, Ap, code, nb, nbo, Fp, Ip, Gp), "factor_batched")
+        out = []
+        for F, ip, fl in zip(Fs, ips, fls):
+            f = fl.cpu()
+            out.append((F, ip, int(f[0]), int(f[1])))
+        return out
+
 
 class Server:
     """Continuous-batching solve server (msir_server_*)."""

@@ -26,7 +26,7 @@ EXPORTED = [
     "msir_factors_export", "msir_factors_apply", "msir_residual", "msir_solve", "msir_solve_host",
     "msir_solve_batched", "msir_server_create", "msir_server_submit", "msir_server_poll",
     "msir_server_destroy", "msir_server_set_backlog_limit", "msir_status_string", "msir_residual_noalloc", "msir_probe_fma_rate",
-    "msir_probe_wait_timeout", "msir_probe_widen_check",
+    "msir_probe_wait_timeout", "msir_probe_widen_check", "msir_factor_batched",
 ]
 
 
@@ -95,6 +95,8 @@ def load(path=LIB_PATH):
         "msir_probe_fma_rate": [I, I, I, pD, pD],
         "msir_probe_wait_timeout": [I, D, pI],
         "msir_probe_widen_check": [I, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)],
+        "msir_factor_batched": [P, I, pI, ctypes.POINTER(P), I, I, I, ctypes.POINTER(P), ctypes.POINTER(P),
+                                ctypes.POINTER(P)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmsir.so")
-SOURCES = ["api.cu", "ingest.cu", "lu.cu", "lu_tc.cu", "inv.cu", "refine_launch.cu", "noalloc.cu", "probe.cu"] + [
+SOURCES = ["api.cu", "ingest.cu", "lu.cu", "lu_tc.cu", "inv.cu", "refine_launch.cu", "noalloc.cu", "probe.cu",
+           "batched.cu", "batched_f32.cu", "batched_f64.cu"] + [
     f"refine_{a}_{f}.cu" for a in ("f32", "f64") for f in ("f16", "bf16", "f32", "f64")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

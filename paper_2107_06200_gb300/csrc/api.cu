@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "../../include/msir.h"
+#include "batched.h"
 #include "ingest.h"
 #include "kernels.h"
 #include "refine.h"
@@ -748,6 +749,7 @@ static void fill_args(msir_ctx* ctx, Slot& s, RefineArgs& a, int mode) {
   a.b = w.b_u;
   a.LU = L.F;
   a.ldf = w.ldu;
+  a.f_fmt = L.fmt;
   a.perm = L.perm;
   a.Rsc = L.scaled ? L.R : nullptr;
   a.Ssc = L.scaled ? L.S : nullptr;
@@ -1616,6 +1618,188 @@ msir_status msir_solve_host(msir_ctx* ctx, int n, const double* A_host, int lda,
   return r;
 }
 
+// ------------------------------------------------- batched engine (host)
+
+// Byte offsets of one block workspace of the batched engine: the
+// single-system layout for (nmax, kcap) and a grid of one block.
+static BatchLayout batch_layout(int nmax, int kcap) {
+  Workspace w;
+  char* const base = reinterpret_cast<char*>((uintptr_t)1 << 20);  // any aligned non-null base
+  const size_t bytes = ws_layout(w, nmax, kcap, 1, true, base);
+  auto off = [&](const void* p) { return (size_t)((const char*)p - base); };
+  BatchLayout L;
+  memset(&L, 0, sizeof(L));
+  L.Au = off(w.Au); L.b_u = off(w.b_u); L.rowsum = off(w.rowsum); L.rowmax = off(w.rowmax);
+  L.colmax = off(w.colmax);
+  for (int l = 0; l < 3; ++l) {
+    L.F[l] = off(w.Fbuf[l]); L.ipiv[l] = off(w.ipiv[l]); L.perm[l] = off(w.perm[l]);
+    L.R[l] = off(w.R[l]); L.S[l] = off(w.S[l]); L.inv32[l] = off(w.inv32[l]);
+    L.inv_hi[l] = off(w.inv_hi[l]); L.inv_lo[l] = off(w.inv_lo[l]);
+  }
+  L.x = off(w.x); L.xn = off(w.xn); L.x0 = off(w.x0); L.xbest = off(w.xbest);
+  L.r_hi = off(w.r_hi); L.r_lo = off(w.r_lo); L.c_hi = off(w.c_hi); L.c_lo = off(w.c_lo);
+  L.y_hi = off(w.y_hi); L.y_lo = off(w.y_lo); L.z_hi = off(w.z_hi); L.z_lo = off(w.z_lo);
+  L.d = off(w.d); L.w = off(w.w); L.vk = off(w.vk);
+  L.V = off(w.V); L.H = off(w.H); L.yv = off(w.yv); L.red = off(w.red); L.hred = off(w.hred);
+  L.hvec = off(w.hvec); L.ll = off(w.ll); L.M32 = off(w.M32); L.M64 = off(w.M64); L.Mdh = off(w.Mdh);
+  L.Mdl = off(w.Mdl); L.bar = off(w.bar); L.iflags = off(w.iflags);
+  L.ldu = w.ldu;
+  L.ldv = w.ldv;
+  L.kcap = kcap;
+  L.nmax = nmax;
+  L.bytes = round_up(bytes, 256);
+  return L;
+}
+
+// Systems of the batch that the engine takes: n <= kBatchMaxN.  One launch
+// per working precision u0, captured in a CUDA graph (the work counter's
+// reset and the persistent kernel) and replayed once.
+static msir_status run_batch_engine(msir_ctx* ctx, const std::vector<int>& idx, int u0, const int* n,
+                                    const double* const* A_dev, const double* const* b_dev,
+                                    double* const* x_dev, const msir_triple* t, const msir_params& p,
+                                    msir_report* reps, std::vector<int>& status) {
+  const int count = (int)idx.size();
+  if (count == 0) return MSIR_OK;
+  int nmax = 0;
+  for (int i : idx) nmax = std::max(nmax, n[i]);
+  const int kcap = kcap_of(nmax, std::fabs(p.kmax_frac));
+  const BatchLayout L = batch_layout(nmax, kcap);
+  const int gmax = batched_max_grid(u0, kcap);
+  if (gmax <= 0) return MSIR_ERR_UNSUPPORTED;
+  const int grid = std::max(1, std::min(gmax, count));
+  // largest systems first, so the last systems to start are small ones
+  std::vector<int> order(idx);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
+  std::vector<BatchTask> tasks(count);
+  for (int q = 0; q < count; ++q) {
+    const int i = order[q];
+    tasks[q].A = A_dev[i];
+    tasks[q].b = b_dev[i];
+    tasks[q].x = x_dev[i];
+    tasks[q].n = n[i];
+    tasks[q].uf = t[i].uf;
+    tasks[q].u = t[i].u;
+    tasks[q].ur = t[i].ur;
+  }
+  cudaStream_t st = ctx->stream;
+  char* ws = nullptr;
+  BatchTask* d_tasks = nullptr;
+  msir_report* d_reps = nullptr;
+  int* d_status = nullptr;
+  unsigned* d_next = nullptr;
+  msir_status r = MSIR_OK;
+  auto alloc = [&](void** ptr, size_t bytes) {
+    if (r == MSIR_OK) r = cuda_status(cudaMallocAsync(ptr, bytes, st));
+  };
+  alloc((void**)&ws, L.bytes * (size_t)grid);
+  alloc((void**)&d_tasks, sizeof(BatchTask) * count);
+  alloc((void**)&d_reps, sizeof(msir_report) * count);
+  alloc((void**)&d_status, sizeof(int) * count);
+  alloc((void**)&d_next, 256);
+  std::vector<msir_report> h_reps(count);
+  std::vector<int> h_status(count, 0);
+  if (r == MSIR_OK)
+    r = cuda_status(cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(BatchTask) * count, cudaMemcpyHostToDevice, st));
+  if (r == MSIR_OK) {
+    BatchArgs B;
+    memset(&B, 0, sizeof(B));
+    B.tasks = d_tasks;
+    B.count = count;
+    B.next = d_next;
+    B.ws = ws;
+    B.layout = L;
+    B.reps = d_reps;
+    B.status = d_status;
+    B.i_max = p.i_max;
+    B.rho_thresh = p.rho_thresh;
+    B.kmax_frac = std::fabs(p.kmax_frac);
+    B.tau = p.tau;
+    B.gamma = p.gamma;
+    B.conv = p.conv;
+    B.allow_escalation = p.allow_escalation;
+    B.nb = p.nb;
+    B.nbo = p.nbo;
+    B.mu_half = std::ldexp(1.0, (int)std::floor(std::log2(0.1 * xmax_of(MSIR_FP16))));
+    B.mu_bf16 = std::ldexp(1.0, (int)std::floor(std::log2(0.1 * xmax_of(MSIR_BF16))));
+    B.mu_single = std::ldexp(1.0, (int)std::floor(std::log2(0.1 * xmax_of(MSIR_FP32))));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaError_t e1 = cudaMemsetAsync(d_next, 0, sizeof(unsigned), st);
+      cudaError_t e2 = e1 == cudaSuccess ? launch_batched(u0, B, grid, st) : e1;
+      e = cudaStreamEndCapture(st, &graph);
+      if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_reps.data(), d_reps, sizeof(msir_report) * count,
+                                              cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h_status.data(), d_status, sizeof(int) * count,
+                                              cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    r = cuda_status(e);
+  }
+  if (ws) cudaFreeAsync(ws, st);
+  if (d_tasks) cudaFreeAsync(d_tasks, st);
+  if (d_reps) cudaFreeAsync(d_reps, st);
+  if (d_status) cudaFreeAsync(d_status, st);
+  if (d_next) cudaFreeAsync(d_next, st);
+  cudaStreamSynchronize(st);
+  if (r != MSIR_OK) return r;
+  for (int q = 0; q < count; ++q) {
+    const int i = order[q];
+    status[i] = h_status[q];
+    if (reps) {
+      reps[i] = h_reps[q];
+      reps[i].n_launches = q == 0 ? 1 : 0;  // the batch's one launch, counted on its first system
+    }
+  }
+  return MSIR_OK;
+}
+
+msir_status msir_factor_batched(msir_ctx* ctx, int count, const int* n, const double* const* A_dev, int fmt,
+                                int nb, int nbo, double* const* F_dev, int* const* ipiv_dev,
+                                int* const* flags_dev) {
+  if (!ctx || count < 0 || (count > 0 && (!n || !A_dev || !F_dev || !ipiv_dev || !flags_dev)))
+    return MSIR_ERR_INVALID;
+  if (fmt != MSIR_FP16 && fmt != MSIR_BF16 && fmt != MSIR_FP32 && fmt != MSIR_FP64) return MSIR_ERR_INVALID;
+  if (nb <= 0) nb = fmt == MSIR_FP64 ? 16 : 32;
+  if (nbo <= 0) nbo = 64;
+  if (nb > (fmt == MSIR_FP64 ? 16 : 32) || nbo % nb != 0 || nbo > 64) return MSIR_ERR_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (n[i] < 1 || n[i] > kBatchMaxN || !A_dev[i] || !F_dev[i] || !ipiv_dev[i] || !flags_dev[i])
+      return MSIR_ERR_INVALID;
+  if (count == 0) return MSIR_OK;
+  CK(cudaSetDevice(ctx->device));
+  std::vector<BatchFactorTask> tasks(count);
+  for (int i = 0; i < count; ++i) tasks[i] = BatchFactorTask{A_dev[i], n[i], F_dev[i], ipiv_dev[i], flags_dev[i]};
+  const int grid = std::max(1, std::min(count, ctx->num_sms));
+  const size_t stride = batched_factor_ws_bytes(fmt);
+  cudaStream_t st = ctx->stream;
+  BatchFactorTask* d_tasks = nullptr;
+  char* ws = nullptr;
+  msir_status r = cuda_status(cudaMallocAsync((void**)&d_tasks, sizeof(BatchFactorTask) * count, st));
+  if (r == MSIR_OK) r = cuda_status(cudaMallocAsync((void**)&ws, stride * grid, st));
+  if (r == MSIR_OK)
+    r = cuda_status(cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(BatchFactorTask) * count, cudaMemcpyHostToDevice, st));
+  if (r == MSIR_OK) r = cuda_status(launch_batched_factor(fmt, d_tasks, count, ws, stride, nb, nbo, grid, st));
+  if (r == MSIR_OK) r = cuda_status(cudaStreamSynchronize(st));
+  if (ws) cudaFreeAsync(ws, st);
+  if (d_tasks) cudaFreeAsync(d_tasks, st);
+  cudaStreamSynchronize(st);
+  return r;
+}
+
+// MSIR_BATCH_ENGINE=0 sends every system of msir_solve_batched through the
+// concurrent slots (as systems larger than kBatchMaxN always go).
+static bool batch_engine_enabled() {
+  static const int v = env_int("MSIR_BATCH_ENGINE", 1, 0, 1);
+  return v == 1;
+}
+
 msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n, const double* const* A_dev,
                                const double* const* b_dev, double* const* x_dev, const msir_triple* t,
                                const msir_params* params, msir_report* reps) {
@@ -1627,13 +1811,31 @@ msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n, const dou
     if (n[i] <= 0 || !valid_triple(t[i]) || !A_dev[i] || !b_dev[i] || !x_dev[i]) return MSIR_ERR_INVALID;
   if (count == 0) return MSIR_OK;
   CK(cudaSetDevice(ctx->device));
+  // small systems: the batched engine (one persistent launch per u0)
+  std::vector<int> eng32, eng64, rest;
+  for (int i = 0; i < count; ++i) {
+    if (batch_engine_enabled() && n[i] <= kBatchMaxN)
+      (t[i].u == MSIR_FP32 ? eng32 : eng64).push_back(i);
+    else
+      rest.push_back(i);
+  }
+  std::vector<int> eng_status(count, 0);
+  msir_status re = run_batch_engine(ctx, eng32, MSIR_FP32, n, A_dev, b_dev, x_dev, t, p, reps, eng_status);
+  if (re == MSIR_OK) re = run_batch_engine(ctx, eng64, MSIR_FP64, n, A_dev, b_dev, x_dev, t, p, reps, eng_status);
+  if (re != MSIR_OK) return re;
+  msir_status agg = MSIR_OK;
+  for (int i = 0; i < count; ++i) {
+    if (eng_status[i] < 0) agg = (msir_status)eng_status[i];
+    else if (eng_status[i] == MSIR_NOT_CONVERGED && agg == MSIR_OK) agg = MSIR_NOT_CONVERGED;
+  }
+  if (rest.empty()) return agg;
+  // the others: concurrent slots, largest systems first (longest-processing-time order)
+  const int nrest = (int)rest.size();
   std::vector<Job> jobs(count);
-  std::vector<Job*> jp(count);
-  // largest systems first (longest-processing-time order)
-  std::vector<int> order(count);
-  for (int i = 0; i < count; ++i) order[i] = i;
+  std::vector<Job*> jp(nrest);
+  std::vector<int> order(rest);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return n[a] > n[b]; });
-  for (int q = 0; q < count; ++q) {
+  for (int q = 0; q < nrest; ++q) {
     const int i = order[q];
     jobs[i].n = n[i];
     jobs[i].A = A_dev[i];
@@ -1645,17 +1847,17 @@ msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n, const dou
     jp[q] = &jobs[i];
   }
   int nmax = 0;
-  for (int i = 0; i < count; ++i) nmax = std::max(nmax, n[i]);
+  for (int i : rest) nmax = std::max(nmax, n[i]);
   // Concurrency: each system gets about 7/6 CTAs per 64-row block (at least
   // 16): its substitution chains need a CTA per block, and the rest of the
   // SMs are better spent on other systems than on wider grids (the
   // measured optimum for the n = 2000 sweep is 4 systems of 38 CTAs).
   const int nblk_max = (nmax + kBlk - 1) / kBlk;
   const int per_sys = std::max(16, (7 * nblk_max + 5) / 6);
-  int nslots = std::max(1, std::min(count, std::min(32, ctx->num_sms / per_sys)));
+  int nslots = std::max(1, std::min(nrest, std::min(32, ctx->num_sms / per_sys)));
   if (const char* e = getenv("MSIR_BATCH_SLOTS")) {  // tuning override of the concurrency
     const int v = atoi(e);
-    if (v > 0) nslots = std::max(1, std::min(count, std::min(32, v)));
+    if (v > 0) nslots = std::max(1, std::min(nrest, std::min(32, v)));
   }
   std::vector<Slot*> slots;
   msir_status r = pooled_slots(ctx, nslots, slots);
@@ -1668,8 +1870,7 @@ msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n, const dou
   }
   for (Slot* s : slots) cudaStreamSynchronize(s->st);
   if (r != MSIR_OK) return r;
-  msir_status agg = MSIR_OK;
-  for (int i = 0; i < count; ++i) {
+  for (int i : rest) {
     if (reps) reps[i] = jobs[i].rep;
     if (jobs[i].status < 0) agg = (msir_status)jobs[i].status;
     else if (jobs[i].status == MSIR_NOT_CONVERGED && agg == MSIR_OK) agg = MSIR_NOT_CONVERGED;

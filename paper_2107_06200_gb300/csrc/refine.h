@@ -69,6 +69,7 @@ struct RefineArgs {
   const double* b;         // b_u (values in u0)
   const void* LU;          // packed factors in u_f storage, row-major
   int ldf;
+  int f_fmt;               // storage format of LU (MSIR_BF16 .. MSIR_FP64)
   const int* perm;         // (P A)[i] = A[perm[i]]
   const double* Rsc;       // squeezing row scalings (nullptr: none)
   const double* Ssc;       // column scalings

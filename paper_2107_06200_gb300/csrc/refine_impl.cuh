@@ -721,6 +721,34 @@ __device__ __forceinline__ bool ib_complete(const unsigned long long* slot, unsi
   return true;
 }
 
+// The factor storage type F of the refinement code is a template parameter
+// of the single-system kernels (one instantiation per u_f); FAny stands for
+// "the format in RefineArgs::f_fmt", read at run time, so that the batched
+// engine, whose systems change u_f as they escalate, needs one
+// instantiation.  Only the scaled-block construction reads the factors.
+struct FAny {};
+template <typename F>
+__device__ __forceinline__ int factor_fmt(const RefineArgs&) {
+  return Fmt<F>::code;
+}
+template <>
+__device__ __forceinline__ int factor_fmt<FAny>(const RefineArgs& a) {
+  return a.f_fmt;
+}
+template <typename F>
+__device__ __forceinline__ double factor_at(const RefineArgs& a, size_t i) {
+  return (double)to_f(((const F*)a.LU)[i]);
+}
+template <>
+__device__ __forceinline__ double factor_at<FAny>(const RefineArgs& a, size_t i) {
+  switch (a.f_fmt) {
+    case MSIR_FP16: return (double)to_f(((const __half*)a.LU)[i]);
+    case MSIR_BF16: return (double)to_f(((const __nv_bfloat16*)a.LU)[i]);
+    case MSIR_FP32: return (double)((const float*)a.LU)[i];
+    default: return ((const double*)a.LU)[i];
+  }
+}
+
 // Scaled off-diagonal blocks M_bj = D_b^{-1} F_bj (j != b; L below the
 // diagonal blocks, U above), formed by all CTAs of the grid once per
 // factorisation and precision, the first time a solve needs them.  One
@@ -738,7 +766,6 @@ __device__ __noinline__ bool build_scaled(Cx& cx, const RefineArgs& a, bool dd) 
   double* Xh = (double*)cx.ssm;       // 64 x (KH + 1)
   double* Xl = Xh + kBlk * (KH + 1);  // 64 x (KH + 1)
   double* Fb = Xl + kBlk * (KH + 1);  // KH x kScLd
-  const F* LU = (const F*)a.LU;
   const int n = cx.n, nb = cx.nblk, ld = a.ldf;
   const int i = cx.tid >> 2, cg = cx.tid & 3;
   for (int t = cx.cta; t < nb * nb; t += cx.G) {
@@ -761,7 +788,7 @@ __device__ __noinline__ bool build_scaled(Cx& cx, const RefineArgs& a, bool dd) 
       for (int e = cx.tid; e < KH * kBlk; e += kRefThreads) {
         const int kk = e / kBlk, cc = e % kBlk;
         const int frow = r0 + k0 + kk, col = c0 + cc;
-        Fb[kk * kScLd + cc] = (frow < n && col < n) ? (double)to_f(LU[(size_t)frow * ld + col]) : 0.0;
+        Fb[kk * kScLd + cc] = (frow < n && col < n) ? factor_at<F>(a, (size_t)frow * ld + col) : 0.0;
       }
       __syncthreads();
       if (!dd) {
@@ -1794,6 +1821,230 @@ static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, doubl
   return 0;
 }
 
+// Algorithm 4 after the factorisation (the MSIR mode of the refinement
+// kernel): x0, then SIR / SGMRES-IR / GMRES-IR steps with the stopping
+// logic, until convergence, a stage that needs a finer u_f (S.phase =
+// PH_NEED_ESC) or the end.  Run by every CTA of a cooperative launch, or by
+// one CTA alone (cx.G = 1) in the batched engine.  S, s_act, s_reset and
+// s_alg live in shared memory.  Returns false if a device wait failed.
+template <typename A0, typename F>
+__device__ bool refine_msir(Cx& cx, const RefineArgs& a, RefState& S, unsigned char* gsm, int& s_act,
+                            int& s_reset, int& s_alg) {
+  bool ok = true;
+  const int ff = factor_fmt<F>(a);
+  const int arith_f = ff == MSIR_FP64 ? MSIR_FP64 : MSIR_FP32;
+  double s = S.s, xnorm = 0.0, nbe = S.nbe;
+  if (S.phase == PH_START) {
+    if (a.normb == 0.0) {
+      FOR_MY_ROWS(cx, i) { a.x[i] = 0.0; a.xbest[i] = 0.0; }
+      if (cx.tid == 0) { S.cged = 1; S.status = MSIR_OK; S.phase = PH_DONE; S.nbe = 0.0; S.s = 0.0; }
+      __syncthreads();
+      return false;
+    }
+    // x0 = fl_u(fl_u(||b||) M_f^{-1} fl_u(b / ||b||)) with the u_f model
+    for (int b = cx.cta; b < cx.nblk; b += cx.G)
+      for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads) {
+        const int pr = a.perm[i];
+        const double bt = urnd(__ddiv_rn(a.b[pr], a.normb), S.u);
+        put_c(a, arith_f, i, round_to(bt * rscale(a, pr), S.uf), 0.0);
+      }
+    __syncthreads();
+    ok = msolve_arith<F>(cx, a, arith_f, S.uf);
+    if (!ok) return false;
+    {
+      const double nb_u = urnd(a.normb, S.u);
+      double mx = 0.0;
+      FOR_MY_ROWS(cx, i) {
+        const double d0 = urnd(get_z(a, arith_f, i) * cscale(a, i), S.u);
+        const double x0 = urnd(nb_u * d0, S.u);
+        a.x0[i] = x0;
+        mx = nanmax(mx, fabs(x0));
+      }
+      mx = cta_reduce(mx, 1, cx.tid);
+      double v[1] = {mx};
+      const int op[1] = {1};
+      if (!(ok = grid_reduce<1>(cx, a, v, op))) return false;
+      const bool bad = !isfinite(v[0]);
+      FOR_MY_ROWS(cx, i) {
+        if (bad) a.x0[i] = 0.0;
+        a.x[i] = a.x0[i];
+        a.xbest[i] = a.x0[i];
+      }
+    }
+    if (!(ok = grid_barrier(a.bar, a.err, cx.G))) return false;
+    if (!(ok = residual<A0>(cx, a, a.x, S.ur, s, xnorm))) return false;
+    nbe = s / (a.normA * xnorm + a.normb);
+    if (cx.tid == 0) {
+      S.best_nbe = nbe;
+      S.alg = MSIR_ALG_SIR;
+      S.it = 0;
+      S.rho_max = 0.0;
+      S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
+      S.phase = PH_ESCALATED + 10;  // running
+      rep_new_stage(a, S);
+    }
+    __syncthreads();
+  } else if (S.phase == PH_ESCALATED) {
+    if (!(ok = grid_barrier(a.bar, a.err, cx.G))) return false;
+    if (!(ok = residual<A0>(cx, a, a.x, S.ur, s, xnorm))) return false;
+    nbe = s / (a.normA * xnorm + a.normb);
+    if (cx.tid == 0) {
+      if (nbe < S.best_nbe) S.best_nbe = nbe;
+      S.alg = MSIR_ALG_SIR;
+      S.it = 0;
+      S.rho_max = 0.0;
+      S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
+      S.phase = PH_ESCALATED + 10;
+      rep_new_stage(a, S);
+    }
+    __syncthreads();
+    if (nbe <= S.best_nbe) FOR_MY_ROWS(cx, i) a.xbest[i] = a.x[i];
+  }
+
+  while (true) {
+    if (s == 0.0) {
+      if (cx.tid == 0) { S.cged = 1; S.status = MSIR_OK; }
+      break;
+    }
+    if (!isfinite(s)) break;
+    const int u = S.u, ur = S.ur;
+    int kg = -1;
+    bool nonfinite = false;
+    if (S.alg == MSIR_ALG_SIR) {
+      for (int b = cx.cta; b < cx.nblk; b += cx.G)
+        for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads) {
+          const double rt = scaled_r(a, i, s, ur, u);
+          put_c(a, arith_f, i, round_to(rt * rscale(a, a.perm[i]), S.uf), 0.0);
+        }
+      __syncthreads();
+      if (!(ok = msolve_arith<F>(cx, a, arith_f, S.uf))) break;
+      FOR_MY_ROWS(cx, i) a.d[i] = urnd(get_z(a, arith_f, i) * cscale(a, i), u);
+      __syncthreads();
+    } else {
+      const int op = S.alg == MSIR_ALG_SGMRES ? u : square_of(u);
+      const double tau = a.tau > 0.0 ? a.tau : (u == MSIR_FP32 ? 1e-6 : 1e-10);
+      GmresOut go;
+      if (u == MSIR_FP32) {
+        if (!(ok = gmres<A0, F, float>(cx, a, s, ur, u, op, tau, gsm, go))) break;
+      } else {
+        if (!(ok = gmres<A0, F, double>(cx, a, s, ur, u, op, tau, gsm, go))) break;
+      }
+      kg = go.k;
+      nonfinite = go.nonfinite;
+    }
+    // tentative update x_{i+1} = fl_u(x_i + fl_u(fl_u(s) d)) and the norms
+    double md = 0.0, mx = 0.0;
+    const double su = urnd(s, u);
+    FOR_MY_ROWS(cx, i) {
+      const double dv = nonfinite ? 0.0 : a.d[i];
+      const double xv = a.x[i];
+      a.xn[i] = urnd(xv + urnd(su * dv, u), u);
+      md = nanmax(md, fabs(dv));
+      mx = nanmax(mx, fabs(xv));
+    }
+    md = cta_reduce(md, 1, cx.tid);
+    mx = cta_reduce(mx, 1, cx.tid);
+    {
+      double v[2] = {md, mx};
+      const int op[2] = {1, 1};
+      if (!(ok = grid_reduce<2>(cx, a, v, op))) break;
+      md = v[0];
+      mx = v[1];
+    }
+    if (nonfinite || !isfinite(md)) {
+      // Inf/NaN correction: no update, the step is not counted, next stage
+      if (cx.tid == 0) {
+        if (cx.cta == 0 && S.nstages >= 1 && S.nstages <= MSIR_MAX_STAGES)
+          a.rep->stage[S.nstages - 1].nonfinite = 1;
+        if (S.alg == MSIR_ALG_GMRES) {
+          S.phase = PH_NEED_ESC;
+        } else {
+          S.alg += 1;
+          S.it = 0;
+          S.rho_max = 0.0;
+          S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
+          rep_new_stage(a, S);
+        }
+      }
+      __syncthreads();
+      if (S.phase == PH_NEED_ESC) break;
+      continue;
+    }
+    const double s_old = s, xnorm_old = mx;
+    FOR_MY_ROWS(cx, i) a.x[i] = a.xn[i];
+    if (!(ok = grid_barrier(a.bar, a.err, cx.G))) break;
+    double ferr = 0.0;
+    if (!(ok = residual<A0>(cx, a, a.x, ur, s, xnorm, &ferr))) break;
+    nbe = s / (a.normA * xnorm + a.normb);
+    const bool better = nbe < S.best_nbe;
+    // every thread has read S before thread 0 updates it (shared memory)
+    __syncthreads();
+    if (better) FOR_MY_ROWS(cx, i) a.xbest[i] = a.x[i];
+    if (cx.tid == 0) {
+      if (better) S.best_nbe = nbe;
+      S.it += 1;
+      S.total_steps += 1;
+      if (kg >= 0) S.total_gmres += kg;
+      if (cx.cta == 0 && S.nstages >= 1 && S.nstages <= MSIR_MAX_STAGES) {
+        msir_stage& g = a.rep->stage[S.nstages - 1];
+        if (kg >= 0 && g.steps < MSIR_MAX_STEPS) g.gmres_iters[g.steps] = kg;
+        g.steps += 1;
+      }
+      int rs = 0;
+      s_act = ctl_step(S, a, s_old, md, xnorm_old, nbe, ferr, kg, &rs);
+      s_reset = rs;
+      s_alg = S.alg;
+      S.nbe = nbe;
+    }
+    __syncthreads();
+    // decisions below use s_act/s_reset/s_alg: thread 0 changes S.alg
+    // inside this branch while other warps may not have reached it yet
+    if (s_act == 1) {
+      if (cx.tid == 0) { S.cged = 1; S.status = MSIR_OK; }
+      break;
+    }
+    if (s_act == 2) {
+      const bool reset = s_reset != 0;
+      if (reset) FOR_MY_ROWS(cx, i) a.x[i] = a.x0[i];
+      if (s_alg == MSIR_ALG_GMRES) {
+        if (cx.tid == 0) S.phase = PH_NEED_ESC;
+        __syncthreads();
+        break;
+      }
+      if (cx.tid == 0) {
+        S.alg += 1;
+        S.it = 0;
+        S.rho_max = 0.0;
+        S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
+        rep_new_stage(a, S);
+      }
+      __syncthreads();
+      if (reset) {
+        if (!(ok = grid_barrier(a.bar, a.err, cx.G))) break;
+        if (!(ok = residual<A0>(cx, a, a.x, ur, s, xnorm))) break;
+        nbe = s / (a.normA * xnorm + a.normb);
+        const bool b2 = nbe < S.best_nbe;
+        if (b2) FOR_MY_ROWS(cx, i) a.xbest[i] = a.x[i];
+        __syncthreads();
+        if (cx.tid == 0 && b2) S.best_nbe = nbe;
+        __syncthreads();
+      }
+    }
+  }
+  if (cx.tid == 0) {
+    S.s = s;
+    S.nbe = nbe;
+    if (S.phase != PH_NEED_ESC) S.phase = PH_DONE;
+  }
+  __syncthreads();
+  if (ok && S.phase == PH_DONE && !S.cged) {
+    // not converged: return the iterate of smallest nbe
+    FOR_MY_ROWS(cx, i) a.x[i] = a.xbest[i];
+    if (cx.tid == 0) { S.status = MSIR_NOT_CONVERGED; S.nbe = S.best_nbe; }
+  }
+  return ok;
+}
+
 template <typename A0, typename F>
 // One CTA per SM.  (Two per SM, with 128 registers per thread, let
 // concurrent systems share SMs, but measured slower: spinning and fp64 work
@@ -1835,9 +2086,6 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
   cx.mready = S.mready;
   cx.t_ns = S.t_ns;
   bool ok = true;
-  const int ff = Fmt<F>::code;
-  const int arith_f = ff == MSIR_FP64 ? MSIR_FP64 : MSIR_FP32;
-
   if (a.mode == MODE_RESIDUAL) {
     double s = 0.0, xn = 0.0;
     ok = grid_barrier(a.bar, a.err, cx.G) && residual<A0>(cx, a, a.x, a.ap_arith, s, xn);
@@ -1853,218 +2101,8 @@ __global__ void __launch_bounds__(kRefThreads, 1) refine_kernel(RefineArgs a) {
     ok = msolve_arith<F>(cx, a, a.ap_arith, a.ap_store);
     if (ok) FOR_MY_ROWS(cx, i) a.ap_out[i] = get_z(a, a.ap_arith, i) * cscale(a, i);
   } else {
-    // ------------------------------------------------------------ MSIR
-    double s = S.s, xnorm = 0.0, nbe = S.nbe;
-    if (S.phase == PH_START) {
-      if (a.normb == 0.0) {
-        FOR_MY_ROWS(cx, i) { a.x[i] = 0.0; a.xbest[i] = 0.0; }
-        if (cx.tid == 0) { S.cged = 1; S.status = MSIR_OK; S.phase = PH_DONE; S.nbe = 0.0; S.s = 0.0; }
-        __syncthreads();
-        goto finish;
-      }
-      // x0 = fl_u(fl_u(||b||) M_f^{-1} fl_u(b / ||b||)) with the u_f model
-      for (int b = cx.cta; b < cx.nblk; b += cx.G)
-        for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads) {
-          const int pr = a.perm[i];
-          const double bt = urnd(__ddiv_rn(a.b[pr], a.normb), S.u);
-          put_c(a, arith_f, i, round_to(bt * rscale(a, pr), S.uf), 0.0);
-        }
-      __syncthreads();
-      ok = msolve_arith<F>(cx, a, arith_f, S.uf);
-      if (!ok) goto finish;
-      {
-        const double nb_u = urnd(a.normb, S.u);
-        double mx = 0.0;
-        FOR_MY_ROWS(cx, i) {
-          const double d0 = urnd(get_z(a, arith_f, i) * cscale(a, i), S.u);
-          const double x0 = urnd(nb_u * d0, S.u);
-          a.x0[i] = x0;
-          mx = nanmax(mx, fabs(x0));
-        }
-        mx = cta_reduce(mx, 1, cx.tid);
-        double v[1] = {mx};
-        const int op[1] = {1};
-        if (!(ok = grid_reduce<1>(cx, a, v, op))) goto finish;
-        const bool bad = !isfinite(v[0]);
-        FOR_MY_ROWS(cx, i) {
-          if (bad) a.x0[i] = 0.0;
-          a.x[i] = a.x0[i];
-          a.xbest[i] = a.x0[i];
-        }
-      }
-      if (!(ok = grid_barrier(a.bar, a.err, cx.G))) goto finish;
-      if (!(ok = residual<A0>(cx, a, a.x, S.ur, s, xnorm))) goto finish;
-      nbe = s / (a.normA * xnorm + a.normb);
-      if (cx.tid == 0) {
-        S.best_nbe = nbe;
-        S.alg = MSIR_ALG_SIR;
-        S.it = 0;
-        S.rho_max = 0.0;
-        S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
-        S.phase = PH_ESCALATED + 10;  // running
-        rep_new_stage(a, S);
-      }
-      __syncthreads();
-    } else if (S.phase == PH_ESCALATED) {
-      if (!(ok = grid_barrier(a.bar, a.err, cx.G))) goto finish;
-      if (!(ok = residual<A0>(cx, a, a.x, S.ur, s, xnorm))) goto finish;
-      nbe = s / (a.normA * xnorm + a.normb);
-      if (cx.tid == 0) {
-        if (nbe < S.best_nbe) S.best_nbe = nbe;
-        S.alg = MSIR_ALG_SIR;
-        S.it = 0;
-        S.rho_max = 0.0;
-        S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
-        S.phase = PH_ESCALATED + 10;
-        rep_new_stage(a, S);
-      }
-      __syncthreads();
-      if (nbe <= S.best_nbe) FOR_MY_ROWS(cx, i) a.xbest[i] = a.x[i];
-    }
-
-    while (true) {
-      if (s == 0.0) {
-        if (cx.tid == 0) { S.cged = 1; S.status = MSIR_OK; }
-        break;
-      }
-      if (!isfinite(s)) break;
-      const int u = S.u, ur = S.ur;
-      int kg = -1;
-      bool nonfinite = false;
-      if (S.alg == MSIR_ALG_SIR) {
-        for (int b = cx.cta; b < cx.nblk; b += cx.G)
-          for (int i = b * kBlk + cx.tid; i < min((b + 1) * kBlk, cx.n); i += kRefThreads) {
-            const double rt = scaled_r(a, i, s, ur, u);
-            put_c(a, arith_f, i, round_to(rt * rscale(a, a.perm[i]), S.uf), 0.0);
-          }
-        __syncthreads();
-        if (!(ok = msolve_arith<F>(cx, a, arith_f, S.uf))) break;
-        FOR_MY_ROWS(cx, i) a.d[i] = urnd(get_z(a, arith_f, i) * cscale(a, i), u);
-        __syncthreads();
-      } else {
-        const int op = S.alg == MSIR_ALG_SGMRES ? u : square_of(u);
-        const double tau = a.tau > 0.0 ? a.tau : (u == MSIR_FP32 ? 1e-6 : 1e-10);
-        GmresOut go;
-        if (u == MSIR_FP32) {
-          if (!(ok = gmres<A0, F, float>(cx, a, s, ur, u, op, tau, gsm, go))) break;
-        } else {
-          if (!(ok = gmres<A0, F, double>(cx, a, s, ur, u, op, tau, gsm, go))) break;
-        }
-        kg = go.k;
-        nonfinite = go.nonfinite;
-      }
-      // tentative update x_{i+1} = fl_u(x_i + fl_u(fl_u(s) d)) and the norms
-      double md = 0.0, mx = 0.0;
-      const double su = urnd(s, u);
-      FOR_MY_ROWS(cx, i) {
-        const double dv = nonfinite ? 0.0 : a.d[i];
-        const double xv = a.x[i];
-        a.xn[i] = urnd(xv + urnd(su * dv, u), u);
-        md = nanmax(md, fabs(dv));
-        mx = nanmax(mx, fabs(xv));
-      }
-      md = cta_reduce(md, 1, cx.tid);
-      mx = cta_reduce(mx, 1, cx.tid);
-      {
-        double v[2] = {md, mx};
-        const int op[2] = {1, 1};
-        if (!(ok = grid_reduce<2>(cx, a, v, op))) break;
-        md = v[0];
-        mx = v[1];
-      }
-      if (nonfinite || !isfinite(md)) {
-        // Inf/NaN correction: no update, the step is not counted, next stage
-        if (cx.tid == 0) {
-          if (cx.cta == 0 && S.nstages >= 1 && S.nstages <= MSIR_MAX_STAGES)
-            a.rep->stage[S.nstages - 1].nonfinite = 1;
-          if (S.alg == MSIR_ALG_GMRES) {
-            S.phase = PH_NEED_ESC;
-          } else {
-            S.alg += 1;
-            S.it = 0;
-            S.rho_max = 0.0;
-            S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
-            rep_new_stage(a, S);
-          }
-        }
-        __syncthreads();
-        if (S.phase == PH_NEED_ESC) break;
-        continue;
-      }
-      const double s_old = s, xnorm_old = mx;
-      FOR_MY_ROWS(cx, i) a.x[i] = a.xn[i];
-      if (!(ok = grid_barrier(a.bar, a.err, cx.G))) break;
-      double ferr = 0.0;
-      if (!(ok = residual<A0>(cx, a, a.x, ur, s, xnorm, &ferr))) break;
-      nbe = s / (a.normA * xnorm + a.normb);
-      const bool better = nbe < S.best_nbe;
-      // every thread has read S before thread 0 updates it (shared memory)
-      __syncthreads();
-      if (better) FOR_MY_ROWS(cx, i) a.xbest[i] = a.x[i];
-      if (cx.tid == 0) {
-        if (better) S.best_nbe = nbe;
-        S.it += 1;
-        S.total_steps += 1;
-        if (kg >= 0) S.total_gmres += kg;
-        if (cx.cta == 0 && S.nstages >= 1 && S.nstages <= MSIR_MAX_STAGES) {
-          msir_stage& g = a.rep->stage[S.nstages - 1];
-          if (kg >= 0 && g.steps < MSIR_MAX_STEPS) g.gmres_iters[g.steps] = kg;
-          g.steps += 1;
-        }
-        int rs = 0;
-        s_act = ctl_step(S, a, s_old, md, xnorm_old, nbe, ferr, kg, &rs);
-        s_reset = rs;
-        s_alg = S.alg;
-        S.nbe = nbe;
-      }
-      __syncthreads();
-      // decisions below use s_act/s_reset/s_alg: thread 0 changes S.alg
-      // inside this branch while other warps may not have reached it yet
-      if (s_act == 1) {
-        if (cx.tid == 0) { S.cged = 1; S.status = MSIR_OK; }
-        break;
-      }
-      if (s_act == 2) {
-        const bool reset = s_reset != 0;
-        if (reset) FOR_MY_ROWS(cx, i) a.x[i] = a.x0[i];
-        if (s_alg == MSIR_ALG_GMRES) {
-          if (cx.tid == 0) S.phase = PH_NEED_ESC;
-          __syncthreads();
-          break;
-        }
-        if (cx.tid == 0) {
-          S.alg += 1;
-          S.it = 0;
-          S.rho_max = 0.0;
-          S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
-          rep_new_stage(a, S);
-        }
-        __syncthreads();
-        if (reset) {
-          if (!(ok = grid_barrier(a.bar, a.err, cx.G))) break;
-          if (!(ok = residual<A0>(cx, a, a.x, ur, s, xnorm))) break;
-          nbe = s / (a.normA * xnorm + a.normb);
-          const bool b2 = nbe < S.best_nbe;
-          if (b2) FOR_MY_ROWS(cx, i) a.xbest[i] = a.x[i];
-          __syncthreads();
-          if (cx.tid == 0 && b2) S.best_nbe = nbe;
-          __syncthreads();
-        }
-      }
-    }
-    if (cx.tid == 0) {
-      S.s = s;
-      S.nbe = nbe;
-      if (S.phase != PH_NEED_ESC) S.phase = PH_DONE;
-    }
-    __syncthreads();
-    if (ok && S.phase == PH_DONE && !S.cged) {
-      // not converged: return the iterate of smallest nbe
-      FOR_MY_ROWS(cx, i) a.x[i] = a.xbest[i];
-      if (cx.tid == 0) { S.status = MSIR_NOT_CONVERGED; S.nbe = S.best_nbe; }
-    }
+    ok = refine_msir<A0, F>(cx, a, S, gsm, s_act, s_reset, s_alg);
   }
-finish:
   __syncthreads();
   if (!ok && cx.tid == 0) { S.phase = PH_ERROR; S.status = MSIR_ERR_TIMEOUT; }
   if (cx.tid == 0) {

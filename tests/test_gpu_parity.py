@@ -331,20 +331,102 @@ def test_multi_rhs_n8192_sixteen_columns(ctx, M):
         assert [g[:5] for g in stages_of(reps[j])] == [g[:5] for g in stages_of(rj[0])]
 
 
-def test_batched_equals_single_solves(ctx, M):
-    systems = batched_systems(12, seed=0)
-    As, bs, specs = [], [], []
-    for (n, kappa, seed) in systems:
+@pytest.mark.parametrize("uf", [OF.FP32, OF.FP64, OF.FP16, OF.BF16])
+def test_batched_lu_is_bit_exact(ctx, M, uf):
+    """msir_factor_batched (one thread block per system, one launch) against
+    the oracle's blocked LU with the same blocking, element for element and
+    pivot for pivot; bf16 / fp16 with the outer update as the fp32 chain
+    (outer_tc=False), the batched engine's model.  Sizes span one panel, a
+    ragged panel, one outer block, several outer blocks with ragged tails
+    and the engine's maximum; kappa up to 1e8 and a graded system."""
+    sizes = [1, 2, 31, 64, 65, 100, 129, 257, 512]
+    As, A32s = [], []
+    for i, n in enumerate(sizes):
+        A, _, _ = randsvd_system(n, 1e2 if n < 4 else [1e3, 1e6, 1e8][i % 3], 70 + i, graded=(i == 5))
+        A32 = OF.fl(A, OF.FP32).astype(np.float64) if uf != OF.FP64 else A
+        A32s.append(A32)
+        As.append(to_dev(A32))
+    out = ctx.factor_batched(As, OF.NAMES[uf])
+    nb = 16 if uf == OF.FP64 else 32
+    for A32, (F, ipiv, info, nonfinite) in zip(A32s, out):
+        Fo, ipo, info_o = OL.lu_factor(A32.astype(np.float32) if uf != OF.FP64 else A32, uf, nb, 64,
+                                       outer_tc=False)
+        assert info == info_o == 0 and nonfinite == 0
+        assert np.array_equal(ipiv.cpu().numpy(), ipo)
+        assert np.array_equal(F.cpu().numpy(), Fo)
+
+
+def _batch_cases():
+    """Small systems of every triple, sizes and conditioning: some end in
+    SIR, some go through SGMRES-IR / GMRES-IR and escalate u_f."""
+    cases = []
+    for i, (n, kappa, spec) in enumerate([(40, 1e2, HSD), (100, 1e5, HSD), (129, 1e3, BSD), (300, 1e6, HSD),
+                                         (512, 1e4, HSD), (200, 1e9, SDQ), (96, 1e12, SDQ),
+                                         (150, 1e8, HDQ), (257, 1e2, BSD), (64, 1e7, HSD)]):
+        cases.append((n, kappa, spec, 500 + i))
+    return cases
+
+
+def test_batched_engine_matches_the_oracle(ctx, M):
+    """msir_solve_batched on systems of n <= 512 (all of them in the batched
+    engine's one launch per working precision) against the oracle run on
+    each system with the engine's LU model (outer_tc=False): the same stage
+    sequence and precisions, steps within +-1, GMRES iterations within 10 %,
+    same cged, nbe <= 2 u0 when converged, forward error within 2x the
+    oracle's + 2 u0.  And the same stage kinds and convergence as the
+    system solved alone."""
+    cases = _batch_cases()
+    As, bs, specs, hosts = [], [], [], []
+    for (n, kappa, spec, seed) in cases:
         A, B, _ = randsvd_system(n, kappa, seed)
+        hosts.append((A, B[:, 0].copy()))
         As.append(to_dev(A))
         bs.append(to_dev(B[:, 0].copy()))
-        specs.append(HSD)
+        specs.append(spec)
     xs, reps, st = ctx.solve_batched(As, bs, specs)
     assert st in (M.OK, M.NOT_CONVERGED)
-    for A, b, x, r in zip(As, bs, xs, reps):
-        x1, r1, s1 = ctx.solve(A, b, HSD)
-        assert r["steps"] == r1[0]["steps"]
-        same_result(A.cpu().numpy(), b.cpu().numpy(), OF.FP32, x.cpu().numpy(), r, x1.cpu().numpy(), r1[0])
+    assert sum(r["n_launches"] for r in reps) == 2  # one launch per working precision
+    for (A, b), x, r, spec in zip(hosts, xs, reps, specs):
+        trip = _trip(M, spec)
+        u0 = trip[1]
+        params = OM.Params(nb=r["nb"], nbo=r["nbo"], outer_tc=False)
+        ref = OM.msir(A, b, trip, params)
+        print(f"n={A.shape[0]} {spec}: engine '{r['steps']}' oracle '{OM.stage_string(ref.stages)}'")
+        assert_stage_parity(stages_of(r), stages_oracle(ref))
+        assert bool(r["cged"]) == bool(ref.cged)
+        uu = OF.u_of(u0)
+        Au, bu = OF.fl(A, u0).astype(np.float64), OF.fl(b, u0).astype(np.float64)
+        xg = x.cpu().numpy()
+        if ref.cged:
+            assert r["nbe"] <= 2 * uu and OX.nbe(Au, bu, xg) <= 2 * uu
+        xr = OX.x_ref(Au, bu)
+        assert OX.ferr(xg, xr) <= 2 * OX.ferr(ref.x, xr) + 2 * uu
+        x1, r1, _ = ctx.solve(to_dev(A), to_dev(b), spec)
+        assert [g[:4] for g in stages_of(r)] == [g[:4] for g in stages_of(r1[0])]
+        assert bool(r["cged"]) == bool(r1[0]["cged"])
+
+
+def test_batched_engine_and_slots_in_one_call(ctx, M):
+    """A batch mixing engine systems (n <= 512) with larger ones (the
+    concurrent slots) returns every result in its place: each converges to
+    nbe <= 2 u0 with the same stage kinds as solving it alone."""
+    cases = [(600, 1e3, HSD, 1), (100, 1e3, HSD, 2), (700, 1e6, SDQ, 3), (300, 1e4, HSD, 4), (50, 1e2, SDQ, 5)]
+    As, bs, specs, hosts = [], [], [], []
+    for (n, kappa, spec, seed) in cases:
+        A, B, _ = randsvd_system(n, kappa, 600 + seed)
+        hosts.append((A, B[:, 0].copy()))
+        As.append(to_dev(A))
+        bs.append(to_dev(B[:, 0].copy()))
+        specs.append(spec)
+    xs, reps, st = ctx.solve_batched(As, bs, specs)
+    assert st == M.OK
+    for (A, b), x, r, spec in zip(hosts, xs, reps, specs):
+        u0 = _trip(M, spec)[1]
+        uu = OF.u_of(u0)
+        Au, bu = OF.fl(A, u0).astype(np.float64), OF.fl(b, u0).astype(np.float64)
+        assert r["cged"] and OX.nbe(Au, bu, x.cpu().numpy()) <= 2 * uu
+        x1, r1, _ = ctx.solve(to_dev(A), to_dev(b), spec)
+        assert [g[:4] for g in stages_of(r)] == [g[:4] for g in stages_of(r1[0])]
 
 
 def test_batched_multiblock_ctas_through_stage_switches(ctx, M):

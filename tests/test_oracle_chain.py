@@ -91,13 +91,14 @@ def _q(x):
     return Fraction(float(x))
 
 
-def _lu_exact_model(A, fmt, nb, nbo):
+def _lu_exact_model(A, fmt, nb, nbo, outer_tc=True):
     """The blocked LU of oracle.lu written with Python scalars and exact
     rationals, rounding at the stated points only: panel and substitution
     in T with rounded products and differences; updates inside the outer
     block as fma chains in T; the outer update as an fma chain in T for
     fp32/fp64 and as one exact sum rounded to fp32, then to u_f, for
-    bf16/fp16.  Element loops, no numpy arithmetic."""
+    bf16/fp16 (outer_tc=False: the fp32 fma chain for those too).  Element
+    loops, no numpy arithmetic."""
     f = OF.NAMES[fmt]
     t = "fp64" if fmt == OF.FP64 else "fp32"
     n = A.shape[0]
@@ -159,7 +160,7 @@ def _lu_exact_model(A, fmt, nb, nbo):
         new = {}
         for i in range(k + W, n):
             for c in range(k + W, n):
-                if fmt in (OF.FP16, OF.BF16):
+                if fmt in (OF.FP16, OF.BF16) and outer_tc:
                     s = sum(_q(F[i][m]) * _q(F[m][c]) for m in range(k, k + W))
                     new[i, c] = round_q(_q(round_q(_q(F[i][c]) - s, "fp32")), f)
                 else:
@@ -181,3 +182,34 @@ def test_blocked_lu_rounding_points_match_exact_model(fmt, nb, nbo):
     assert info == 0
     assert np.array_equal(ipiv, ipe)
     assert np.array_equal(Fm, Fe)
+
+
+@pytest.mark.parametrize("fmt", [OF.FP16, OF.BF16])
+@pytest.mark.parametrize("nb,nbo", [(2, 4), (3, 6)])
+def test_blocked_lu_without_tensor_cores_matches_exact_model(fmt, nb, nbo):
+    """outer_tc=False (the batched engine's bf16 / fp16 LU): the outer update
+    is the fp32 fma chain at every rounding point."""
+    n = 9
+    for seed in range(3):
+        rng = np.random.default_rng(40 + fmt + nb + 7 * seed)
+        A = (rng.standard_normal((n, n)) * 2.0 ** rng.integers(-3, 4, (n, n))).astype(np.float32)
+        Fm, ipiv, info = OL.lu_factor(A, fmt, nb, nbo, outer_tc=False)
+        Fe, ipe = _lu_exact_model(A, fmt, nb, nbo, outer_tc=False)
+        assert info == 0
+        assert np.array_equal(ipiv, ipe)
+        assert np.array_equal(Fm, Fe)
+
+
+@pytest.mark.parametrize("fmt", [OF.FP16, OF.BF16])
+def test_outer_update_models_differ_where_fp32_rounds(fmt):
+    """C - (2^8 2^7 + 2^-10 1 - 2^8 2^7) with C = 0: the exact sum is 2^-10;
+    the fp32 chain loses 2^-10 against 2^15 (half an ulp is 2^-9) and gives
+    0.  The tensor-core model keeps it, the chain model does not."""
+    F = np.zeros((4, 4))
+    F[3, 0:3] = [2.0 ** 8, 2.0 ** -10, -(2.0 ** 8)]
+    F[0:3, 3] = [2.0 ** 7, 1.0, 2.0 ** 7]
+    Ft, Fc = F.copy(), F.copy()
+    OL._update(Ft, 0, 3, 3, 4, fmt, tensor_core=True)
+    OL._update(Fc, 0, 3, 3, 4, fmt, tensor_core=False)
+    assert Ft[3, 3] == -(2.0 ** -10)
+    assert Fc[3, 3] == 0.0
