@@ -306,6 +306,41 @@ def roofline_line(ref_bytes, ref_fp64, ref_alg, hbm_ach, fp64_ach, alg_ach, hbm_
     return top
 
 
+def fp32_peak():
+    """The fp32 fma rate measured on this GPU (msir_probe_fma_rate)."""
+    import paper_2107_06200_gb300 as M
+    best = 0.0
+    for _ in range(3):
+        tf, _sec = M.probe_fma_rate(0, M.FP32, 1 << 14)
+        best = max(best, tf)
+    return best
+
+
+def engine_flops(rep, n):
+    """fp32-pipe work of one system in the batched engine: every bf16 / fp16
+    / fp32 factorisation (2/3 n^3 fused multiply-adds in fp32, the squeezed
+    retry included) and the refinement's algorithmic flops; an fp64
+    factorisation counts on the fp64 pipe and is left out here."""
+    nf = max(1, rep["n_factorizations"])
+    f64 = 1 if any(s["uf"] == "fp64" for s in rep["stages"]) else 0
+    return (2.0 / 3.0) * n ** 3 * max(0, nf - f64) + refine_algorithmic_flops(rep, n)
+
+
+def engine_roofline(reps, ns, dur_s):
+    """The batched engine's one launch per step (batched_solve_kernel): its
+    block LUs and compensated sums run on the fp32 pipe, so the bound is the
+    measured fp32 fma rate; the kernel's duration is the step's (the call's
+    host work is microseconds)."""
+    work = sum(engine_flops(r, n) for r, n in zip(reps, ns))
+    pk = fp32_peak()
+    ach = work / dur_s / 1e12
+    return {"bound": "alu", "pipe": "fp32", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+            "peak_source": "measured (msir_probe_fma_rate, fp32 fma chains on every SM)",
+            "kernel": "batched_solve_kernel (batched engine, one launch per step)",
+            "work": "2/3 n^3 per fp32-pipe factorisation + 4 n^2 per GMRES iteration or step + 8 n k for CGS2",
+            "traffic": None, "traffic_unit": "bytes per launch (ncu)", "concurrency": 1.0}
+
+
 def run_cpu_baseline(units, max_seconds=25.0, n_sample=1024):
     """The oracle as it stands on the host cores, on a bounded sample of the
     workload: its (kappa, triple) systems at n = n_sample (the oracle's LU
@@ -616,6 +651,13 @@ def main():
     big = max(u[0] for u in units) >= 4096
     systems = build_systems(units, device=str(dev) if big else None)
     ctx = M.Context(local)
+    tuned = None
+    if mode == "batched" and max(s_["n"] for s_ in systems) <= 512:
+        # the batched engine's tile shapes (LU blocking per u_f and size
+        # bucket) from the library's autotuner, untimed
+        tab = ctx.autotune_batched(samples=152)
+        tuned = {f"{uf} n<={64 << b}": f"nb={v[0]} nbo={v[1]}" for (uf, b), v in tab.items()
+                 if uf in {sp.split(",")[0] for sp in (s_["spec"] for s_ in systems)} or uf == "fp32"}
     As = [torch.from_numpy(s_["A"]).to(dev) for s_ in systems]
     bs = [torch.from_numpy(np.ascontiguousarray(s_["b"])).to(dev) for s_ in systems]
     specs = [s_["spec"] for s_ in systems]
@@ -682,7 +724,12 @@ def main():
     ref_fp64 = sum(refine_fp64_flops(r, n) for r, n in zip(last, rep_n))
     ref_alg = sum(refine_algorithmic_flops(r, n) for r, n in zip(last, rep_n))
     peak, peak_kind = peaks()
-    dur_s = (ref_ms / ref_launch) * 1e-3 if ref_ms > 0 else float("inf")
+    engine = ref_launch == 0 and mode == "batched"  # every system in the batched engine's one launch
+    if engine:
+        ref_launch = 1
+        dur_s = ms_per_step * 1e-3
+    else:
+        dur_s = (ref_ms / ref_launch) * 1e-3 if ref_ms > 0 else float("inf")
     hbm_ach = (ref_bytes / ref_launch) / dur_s / 1e9
     fp64_ach = (ref_fp64 / ref_launch) / dur_s / 1e12
     alg_ach = (ref_alg / ref_launch) / dur_s / 1e12
@@ -789,7 +836,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f16+bf16+f32+f64+dd",
             "data": DATA,
-            "config": bench_config(name, world, mode),
+            "config": bench_config(name, world, mode) | ({"tile_shapes": "msir_autotune_batched (untimed, before the "
+                                                           "warm-up): " + ", ".join(f"{k}: {v}" for k, v in tuned.items())}
+                                                          if tuned else {}),
             "latency_ms": {"p50": p50, "p99": p99, "samples": len(lat)},
             "all_converged_nbe_le_2u0": nbe_ok,
             "systems": per_system if len(per_system) <= 64 else
@@ -804,8 +853,9 @@ def main():
                     "d2h_bytes_per_step": d2h, "steps": e2e_steps,
                     "api": "msir_solve_host (host buffers, copies inside the call)"
                     if mode != "batched" else "pinned host copies + msir_solve_batched"},
-            "roofline": roofline_line(ref_bytes, ref_fp64, ref_alg, hbm_ach, fp64_ach, alg_ach, peak,
-                                      peak_kind, fp64_pk, concurrency, name),
+            "roofline": (engine_roofline(last, rep_n, dur_s) if engine else
+                         roofline_line(ref_bytes, ref_fp64, ref_alg, hbm_ach, fp64_ach, alg_ach, peak,
+                                       peak_kind, fp64_pk, concurrency, name)),
             "time_split_ms": {"factor": fac_ms, "refine": ref_ms},
             "cpu_baseline": cpu,
             "cost_aware_kmax": cost_aware,

@@ -286,6 +286,24 @@ msir_status msir_factor_batched(msir_ctx* ctx, int count, const int* n, const do
                                 int nb, int nbo, double* const* F_dev, int* const* ipiv_dev,
                                 int* const* flags_dev);
 
+/* Autotuner of the batched engine's tile shapes: the LU blocking (nb, nbo)
+ * that msir_factor_batched and the engine's factorisations use when
+ * msir_params.nb / nbo are <= 0.  For u_f in {bf16, fp16, fp32, fp64} and
+ * n in {64, 128, 256, 512} it times msir_factor_batched (CUDA events, best
+ * of two after a warm-up) on `samples` seeded random matrices for each
+ * candidate blocking, nb in {16, 32} (fp64: {8, 16}) x nbo in {32, 64},
+ * and keeps the fastest for systems of that size bucket (n <= 64, 128, 256,
+ * 512).  With cache_path non-NULL the table is written there, one line per
+ * entry keyed by the device name, u_f and the bucket; samples = 0 instead
+ * only reads this device's entries from cache_path (MSIR_ERR_INVALID if
+ * there are none).  nb_out, nbo_out (16 ints each) and ms_out (16 doubles;
+ * 0 when read from a file), may be NULL: the table by [u_f - 1][bucket].
+ * The blocking changes the LU's rounding points (the reports state the
+ * blocking used).  Blocks until done; device memory about
+ * 2 samples * 512^2 * 8 bytes. */
+msir_status msir_autotune_batched(msir_ctx* ctx, int samples, const char* cache_path, int* nb_out, int* nbo_out,
+                                  double* ms_out);
+
 /* Continuous-batching solve server on the context's device.
  * hbm_budget_bytes: device memory the server may hold (0 = 90% of the free
  * memory).  max_slots: requests in flight on the device at once.  A worker

@@ -281,6 +281,16 @@ class Context:
                     "solve_batched")
         return xs, [report_to_dict(reps[i]) for i in range(cnt)], st
 
+    def autotune_batched(self, samples=152, cache_path=None):
+        """msir_autotune_batched: returns {(u_f name, bucket): (nb, nbo, ms)}
+        (buckets 0..3 for n <= 64, 128, 256, 512); samples=0 reads cache_path."""
+        nb = (ctypes.c_int * 16)()
+        nbo = (ctypes.c_int * 16)()
+        ms = (ctypes.c_double * 16)()
+        path = cache_path.encode() if cache_path else None
+        _check(_L.msir_autotune_batched(self.h, samples, path, nb, nbo, ms), "autotune_batched")
+        return {(PREC_NAMES[1 + i // 4], i % 4): (nb[i], nbo[i], ms[i]) for i in range(16)}
+
     def factor_batched(self, As, fmt, nb=0, nbo=0):
         """msir_factor_batched: As, a list of (n_i x n_i) fp64 torch cuda
         tensors; fmt, the u_f name or code.  Returns a list of (F (fp64 row-

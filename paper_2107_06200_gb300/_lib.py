@@ -27,6 +27,7 @@ EXPORTED = [
     "msir_solve_batched", "msir_server_create", "msir_server_submit", "msir_server_poll",
     "msir_server_destroy", "msir_server_set_backlog_limit", "msir_status_string", "msir_residual_noalloc", "msir_probe_fma_rate",
     "msir_probe_wait_timeout", "msir_probe_widen_check", "msir_factor_batched",
+    "msir_autotune_batched",
 ]
 
 
@@ -97,6 +98,7 @@ def load(path=LIB_PATH):
         "msir_probe_widen_check": [I, ctypes.POINTER(ctypes.c_ulonglong), ctypes.POINTER(ctypes.c_ulonglong)],
         "msir_factor_batched": [P, I, pI, ctypes.POINTER(P), I, I, I, ctypes.POINTER(P), ctypes.POINTER(P),
                                 ctypes.POINTER(P)],
+        "msir_autotune_batched": [P, I, ctypes.c_char_p, pI, pI, pD],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

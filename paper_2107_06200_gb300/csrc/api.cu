@@ -27,6 +27,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -153,6 +154,9 @@ struct msir_ctx {
   int num_sms = 0;
   int max_dyn_smem = 0;
   std::vector<Slot*> pool;  // slots kept across calls (streams, pinned buffers, workspaces)
+  // the batched engine's LU blocking by [u_f - 1][size bucket] (0: default),
+  // from msir_autotune_batched
+  int tune_nb[4][4] = {}, tune_nbo[4][4] = {};
 };
 
 struct Level {  // one factorisation of the current matrix
@@ -1719,6 +1723,8 @@ static msir_status run_batch_engine(msir_ctx* ctx, const std::vector<int>& idx, 
     B.allow_escalation = p.allow_escalation;
     B.nb = p.nb;
     B.nbo = p.nbo;
+    memcpy(B.tune_nb, ctx->tune_nb, sizeof(B.tune_nb));
+    memcpy(B.tune_nbo, ctx->tune_nbo, sizeof(B.tune_nbo));
     B.mu_half = std::ldexp(1.0, (int)std::floor(std::log2(0.1 * xmax_of(MSIR_FP16))));
     B.mu_bf16 = std::ldexp(1.0, (int)std::floor(std::log2(0.1 * xmax_of(MSIR_BF16))));
     B.mu_single = std::ldexp(1.0, (int)std::floor(std::log2(0.1 * xmax_of(MSIR_FP32))));
@@ -1791,6 +1797,130 @@ msir_status msir_factor_batched(msir_ctx* ctx, int count, const int* n, const do
   if (d_tasks) cudaFreeAsync(d_tasks, st);
   cudaStreamSynchronize(st);
   return r;
+}
+
+// ------------------------------------------------ the engine's autotuner
+
+static const char* kTuneHeader = "msir batched LU blocking v1";
+
+static bool tune_load(msir_ctx* ctx, const char* path, const char* dev) {
+  FILE* f = fopen(path, "r");
+  if (!f) return false;
+  char line[512];
+  bool any = false;
+  if (!fgets(line, sizeof line, f) || strncmp(line, kTuneHeader, strlen(kTuneHeader)) != 0) {
+    fclose(f);
+    return false;
+  }
+  while (fgets(line, sizeof line, f)) {
+    char name[256];
+    int fmt = 0, bucket = -1, nb = 0, nbo = 0;
+    double ms = 0;
+    if (sscanf(line, "%255[^|]|%d|%d|%d|%d|%lf", name, &fmt, &bucket, &nb, &nbo, &ms) != 6) continue;
+    if (strcmp(name, dev) != 0 || fmt < MSIR_BF16 || fmt > MSIR_FP64 || bucket < 0 || bucket > 3) continue;
+    if (nb < 1 || nb > (fmt == MSIR_FP64 ? 16 : 32) || nbo < nb || nbo > 64 || nbo % nb) continue;
+    ctx->tune_nb[fmt - 1][bucket] = nb;
+    ctx->tune_nbo[fmt - 1][bucket] = nbo;
+    any = true;
+  }
+  fclose(f);
+  return any;
+}
+
+msir_status msir_autotune_batched(msir_ctx* ctx, int samples, const char* cache_path, int* nb_out, int* nbo_out,
+                                  double* ms_out) {
+  if (!ctx || samples < 0 || samples > 4096 || (samples == 0 && !cache_path)) return MSIR_ERR_INVALID;
+  CK(cudaSetDevice(ctx->device));
+  cudaDeviceProp prop;
+  CK(cudaGetDeviceProperties(&prop, ctx->device));
+  std::string dev(prop.name);
+  for (char& c : dev)
+    if (c == '|' || c == '\n') c = ' ';
+  double best_ms[4][4] = {};
+  if (samples == 0) {
+    if (!tune_load(ctx, cache_path, dev.c_str())) return MSIR_ERR_INVALID;
+  } else {
+    cudaStream_t st = ctx->stream;
+    const int nmax = kBatchMaxN;
+    double *A = nullptr, *F = nullptr;
+    int *ipiv = nullptr, *flags = nullptr;
+    BatchFactorTask* d_tasks = nullptr;
+    char* ws = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int grid = std::max(1, std::min(samples, ctx->num_sms));
+    const size_t stride = batched_factor_ws_bytes(MSIR_FP64);
+    msir_status r = MSIR_OK;
+    auto alloc = [&](void** p, size_t b) {
+      if (r == MSIR_OK) r = cuda_status(cudaMallocAsync(p, b, st));
+    };
+    alloc((void**)&A, sizeof(double) * samples * nmax * nmax);
+    alloc((void**)&F, sizeof(double) * samples * nmax * nmax);
+    alloc((void**)&ipiv, sizeof(int) * samples * nmax);
+    alloc((void**)&flags, sizeof(int) * samples * 2);
+    alloc((void**)&d_tasks, sizeof(BatchFactorTask) * samples);
+    alloc((void**)&ws, stride * grid);
+    if (r == MSIR_OK) r = cuda_status(cudaEventCreate(&e0));
+    if (r == MSIR_OK) r = cuda_status(cudaEventCreate(&e1));
+    std::vector<BatchFactorTask> tasks(samples);
+    for (int fmt = MSIR_BF16; fmt <= MSIR_FP64 && r == MSIR_OK; ++fmt) {
+      const int cand[4][2] = {{fmt == MSIR_FP64 ? 8 : 16, 32}, {fmt == MSIR_FP64 ? 8 : 16, 64},
+                              {fmt == MSIR_FP64 ? 16 : 32, 32}, {fmt == MSIR_FP64 ? 16 : 32, 64}};
+      for (int b = 0; b < 4 && r == MSIR_OK; ++b) {
+        const int n = 64 << b;
+        r = cuda_status(launch_fill_random(A, (size_t)samples * n * n, 7u * fmt + b, st));
+        for (int i = 0; i < samples; ++i)
+          tasks[i] = BatchFactorTask{A + (size_t)i * n * n, n, F + (size_t)i * n * n, ipiv + (size_t)i * nmax,
+                                     flags + 2 * i};
+        if (r == MSIR_OK)
+          r = cuda_status(cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(BatchFactorTask) * samples,
+                                          cudaMemcpyHostToDevice, st));
+        double best = 1e30;
+        int bnb = 0, bnbo = 0;
+        for (int c = 0; c < 4 && r == MSIR_OK; ++c) {
+          float tmin = 1e30f;
+          for (int rep = 0; rep < 3 && r == MSIR_OK; ++rep) {  // the first is a warm-up
+            cudaEventRecord(e0, st);
+            r = cuda_status(launch_batched_factor(fmt, d_tasks, samples, ws, stride, cand[c][0], cand[c][1], grid, st));
+            cudaEventRecord(e1, st);
+            if (r == MSIR_OK) r = cuda_status(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tmin = std::min(tmin, ms);
+          }
+          if (tmin < best) {
+            best = tmin;
+            bnb = cand[c][0];
+            bnbo = cand[c][1];
+          }
+        }
+        ctx->tune_nb[fmt - 1][b] = bnb;
+        ctx->tune_nbo[fmt - 1][b] = bnbo;
+        best_ms[fmt - 1][b] = best;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (void* p : {(void*)A, (void*)F, (void*)ipiv, (void*)flags, (void*)d_tasks, (void*)ws})
+      if (p) cudaFreeAsync(p, st);
+    cudaStreamSynchronize(st);
+    if (r != MSIR_OK) return r;
+    if (cache_path) {
+      FILE* f = fopen(cache_path, "w");
+      if (!f) return MSIR_ERR_INVALID;
+      fprintf(f, "%s\n", kTuneHeader);
+      for (int fmt = MSIR_BF16; fmt <= MSIR_FP64; ++fmt)
+        for (int b = 0; b < 4; ++b)
+          fprintf(f, "%s|%d|%d|%d|%d|%.6f\n", dev.c_str(), fmt, b, ctx->tune_nb[fmt - 1][b],
+                  ctx->tune_nbo[fmt - 1][b], best_ms[fmt - 1][b]);
+      fclose(f);
+    }
+  }
+  for (int i = 0; i < 16; ++i) {
+    if (nb_out) nb_out[i] = ctx->tune_nb[i / 4][i % 4];
+    if (nbo_out) nbo_out[i] = ctx->tune_nbo[i / 4][i % 4];
+    if (ms_out) ms_out[i] = best_ms[i / 4][i % 4];
+  }
+  return MSIR_OK;
 }
 
 // MSIR_BATCH_ENGINE=0 sends every system of msir_solve_batched through the

@@ -36,6 +36,24 @@ cudaError_t launch_batched(int u0, const BatchArgs& args, int grid, cudaStream_t
   return cudaLaunchKernel(fn, dim3(grid), dim3(kBatchThreads), params, smem, st);
 }
 
+// a 32-bit integer hash of (index, seed) mapped to [-1, 1)
+__global__ void fill_random_kernel(double* A, size_t count, unsigned seed) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    unsigned h = (unsigned)i * 2654435761u ^ (unsigned)(i >> 32) * 40503u ^ seed * 2246822519u;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    h *= 3266489917u;
+    h ^= h >> 16;
+    A[i] = (double)h * (2.0 / 4294967296.0) - 1.0;
+  }
+}
+
+cudaError_t launch_fill_random(double* A, size_t count, unsigned seed, cudaStream_t st) {
+  fill_random_kernel<<<1024, 256, 0, st>>>(A, count, seed);
+  return cudaGetLastError();
+}
+
 size_t batched_factor_ws_bytes(int fmt) {
   const size_t es = fmt == MSIR_FP64 ? 8 : (fmt == MSIR_FP32 ? 4 : 2);
   return ((size_t)kBatchMaxN * kBatchMaxN * es + (size_t)kBatchMaxN * 4 + 255) / 256 * 256;

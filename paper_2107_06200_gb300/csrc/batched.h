@@ -42,9 +42,16 @@ struct BatchArgs {
   // Algorithm 4's parameters, one set for the batch
   int i_max;
   double rho_thresh, kmax_frac, tau, gamma;
-  int conv, allow_escalation, nb, nbo;  // nb, nbo <= 0: the defaults
+  int conv, allow_escalation, nb, nbo;  // nb, nbo > 0: this blocking for every LU
   double mu_half, mu_bf16, mu_single;   // squeezing mu = 2^floor(log2(0.1 x_max)) per u_f
+  // nb, nbo <= 0: the blocking of an LU in u_f = fmt of a system of n rows
+  // is tune_nb/nbo[fmt - 1][bucket], bucket = 0, 1, 2, 3 for n <= 64, 128,
+  // 256, 512 (0 there: the defaults 32 (fp64 16) and 64)
+  int tune_nb[4][4], tune_nbo[4][4];
 };
+
+// size bucket of the tuning table
+__host__ __device__ inline int batch_bucket(int n) { return n <= 64 ? 0 : (n <= 128 ? 1 : (n <= 256 ? 2 : 3)); }
 
 // Smallest and largest n the engine takes (one block factors and refines
 // the whole system); systems of other sizes go through the slots.
@@ -68,6 +75,8 @@ struct BatchFactorTask {
 };
 cudaError_t launch_batched_factor(int fmt, const BatchFactorTask* tasks, int count, char* ws,
                                   size_t ws_stride, int nb, int nbo, int grid, cudaStream_t st);
+// seeded uniform values in [-1, 1) (the autotuner's matrices)
+cudaError_t launch_fill_random(double* A, size_t count, unsigned seed, cudaStream_t st);
 size_t batched_factor_ws_bytes(int fmt);
 
 }  // namespace msir

@@ -279,8 +279,9 @@ __global__ void __launch_bounds__(kBatchThreads, 1) batched_solve_kernel(BatchAr
     double t_factor = 0.0, t_refine = 0.0;
     while (true) {
       const int l = level_of(fmt);
-      int nb = B.nb > 0 ? B.nb : (fmt == MSIR_FP64 ? 16 : 32);
-      int nbo = B.nbo > 0 ? B.nbo : 64;
+      const int tb = B.tune_nb[fmt - 1][batch_bucket(n)], tbo = B.tune_nbo[fmt - 1][batch_bucket(n)];
+      int nb = B.nb > 0 ? B.nb : (tb > 0 ? tb : (fmt == MSIR_FP64 ? 16 : 32));
+      int nbo = B.nbo > 0 ? B.nbo : (tbo > 0 ? tbo : 64);
       if (fmt == MSIR_FP64 && nb > 16) nb = 16;
       if (nbo % nb) nbo = nb * ((nbo + nb - 1) / nb);
       if (nbo > 64) nbo = 64;

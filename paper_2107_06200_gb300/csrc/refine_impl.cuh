@@ -1777,8 +1777,9 @@ __device__ bool gmres(Cx& cx, const RefineArgs& a, double s, int ur, int u, int 
 
 // -------------------------------------------------------------- kernel
 
-static __device__ void rep_new_stage(const RefineArgs& a, RefState& S) {
-  if (blockIdx.x == 0 && threadIdx.x == 0 && S.nstages < MSIR_MAX_STAGES) {
+// (cta: the block's index in the solve's grid; block 0 writes the report)
+static __device__ void rep_new_stage(const RefineArgs& a, RefState& S, int cta) {
+  if (cta == 0 && threadIdx.x == 0 && S.nstages < MSIR_MAX_STAGES) {
     msir_stage& g = a.rep->stage[S.nstages];
     g.uf = S.uf;
     g.u = S.u;
@@ -1839,7 +1840,7 @@ __device__ bool refine_msir(Cx& cx, const RefineArgs& a, RefState& S, unsigned c
       FOR_MY_ROWS(cx, i) { a.x[i] = 0.0; a.xbest[i] = 0.0; }
       if (cx.tid == 0) { S.cged = 1; S.status = MSIR_OK; S.phase = PH_DONE; S.nbe = 0.0; S.s = 0.0; }
       __syncthreads();
-      return false;
+      return true;  // b = 0: x = 0, converged
     }
     // x0 = fl_u(fl_u(||b||) M_f^{-1} fl_u(b / ||b||)) with the u_f model
     for (int b = cx.cta; b < cx.nblk; b += cx.G)
@@ -1881,7 +1882,7 @@ __device__ bool refine_msir(Cx& cx, const RefineArgs& a, RefState& S, unsigned c
       S.rho_max = 0.0;
       S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
       S.phase = PH_ESCALATED + 10;  // running
-      rep_new_stage(a, S);
+      rep_new_stage(a, S, cx.cta);
     }
     __syncthreads();
   } else if (S.phase == PH_ESCALATED) {
@@ -1895,7 +1896,7 @@ __device__ bool refine_msir(Cx& cx, const RefineArgs& a, RefState& S, unsigned c
       S.rho_max = 0.0;
       S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
       S.phase = PH_ESCALATED + 10;
-      rep_new_stage(a, S);
+      rep_new_stage(a, S, cx.cta);
     }
     __syncthreads();
     if (nbe <= S.best_nbe) FOR_MY_ROWS(cx, i) a.xbest[i] = a.x[i];
@@ -1963,7 +1964,7 @@ __device__ bool refine_msir(Cx& cx, const RefineArgs& a, RefState& S, unsigned c
           S.it = 0;
           S.rho_max = 0.0;
           S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
-          rep_new_stage(a, S);
+          rep_new_stage(a, S, cx.cta);
         }
       }
       __syncthreads();
@@ -2016,7 +2017,7 @@ __device__ bool refine_msir(Cx& cx, const RefineArgs& a, RefState& S, unsigned c
         S.it = 0;
         S.rho_max = 0.0;
         S.delta_prev = __longlong_as_double(0x7ff0000000000000ll);
-        rep_new_stage(a, S);
+        rep_new_stage(a, S, cx.cta);
       }
       __syncthreads();
       if (reset) {

@@ -80,3 +80,19 @@ def test_refine_bytes_per_step_and_per_iteration():
     # u = fp64 (A_u in fp64), fp32 factors, dd residual
     rep = {"stages": [_st("GMRES-IR", "fp32", "fp64", "dd", 1, [1])]}
     assert bench.refine_bytes(rep, n) == (n * n * 8 + n * n * 4) + (n * n * 8 + n * n * 4 + 4.0 * n * 8)
+
+
+def test_engine_flops_count_fp32_pipe_factorisations():
+    """The batched engine's work: 2/3 n^3 per factorisation on the fp32 pipe
+    (fp16 then fp32 here; an fp64 one is left out) plus the refinement's
+    algorithmic flops."""
+    import bench
+    n = 100
+    st = [{"uf": "fp16", "alg": "SIR", "steps": 2, "gmres_iters": [0] * 48},
+          {"uf": "fp32", "alg": "SIR", "steps": 3, "gmres_iters": [0] * 48}]
+    rep = {"n_factorizations": 2, "stages": st, "total_steps": 5, "total_gmres_iters": 0}
+    base = bench.refine_algorithmic_flops(rep, n)
+    assert bench.engine_flops(rep, n) == pytest.approx(2 * (2.0 / 3.0) * n ** 3 + base)
+    rep64 = {"n_factorizations": 2, "stages": st[:1] + [dict(st[1], uf="fp64")], "total_steps": 5,
+             "total_gmres_iters": 0}
+    assert bench.engine_flops(rep64, n) == pytest.approx((2.0 / 3.0) * n ** 3 + bench.refine_algorithmic_flops(rep64, n))

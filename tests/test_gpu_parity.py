@@ -406,6 +406,32 @@ def test_batched_engine_matches_the_oracle(ctx, M):
         assert bool(r["cged"]) == bool(r1[0]["cged"])
 
 
+def test_batched_autotuner_table_cache_and_use(ctx, M, tmp_path):
+    """msir_autotune_batched: every (u_f, size bucket) gets one of its
+    candidate blockings and a measured time; the table written to the cache
+    file reads back the same on a new context; a batch solved with the tuned
+    table reports that blocking and still matches the oracle run with it."""
+    path = str(tmp_path / "tune.txt")
+    tab = ctx.autotune_batched(samples=16, cache_path=path)
+    for (uf, bucket), (nb, nbo, ms) in tab.items():
+        assert (nb in (8, 16)) if uf == "fp64" else (nb in (16, 32))
+        assert nbo in (32, 64) and ms > 0
+    ctx2 = M.Context(0)
+    try:
+        tab2 = ctx2.autotune_batched(samples=0, cache_path=path)
+        assert {k: v[:2] for k, v in tab2.items()} == {k: v[:2] for k, v in tab.items()}
+        A, B, _ = randsvd_system(200, 1e3, 77)  # one factorisation (no escalation)
+        xs, reps, st = ctx2.solve_batched([to_dev(A)], [to_dev(B[:, 0].copy())], HSD)
+        r = reps[0]
+        assert r["n_factorizations"] == 1
+        assert (r["nb"], r["nbo"]) == tab[("fp16", 2)][:2]
+        params = OM.Params(nb=r["nb"], nbo=r["nbo"], outer_tc=False)
+        ref = OM.msir(A, B[:, 0], _trip(M, HSD), params)
+        assert_stage_parity(stages_of(r), stages_oracle(ref))
+    finally:
+        ctx2.close()
+
+
 def test_batched_engine_and_slots_in_one_call(ctx, M):
     """A batch mixing engine systems (n <= 512) with larger ones (the
     concurrent slots) returns every result in its place: each converges to
