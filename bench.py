@@ -225,7 +225,7 @@ def refine_bytes(rep, n):
 # launch of this bench's default workload, from one ncu launch-list capture
 # of the same command (3.54 TB over 12 refinement launches, four per step)
 # with the refinement kernel as it stands; None for other workloads.
-REFINE_DRAM_BYTES_PER_LAUNCH = {"c3_n8192_k1e3": 2.95e11}
+REFINE_DRAM_BYTES_PER_LAUNCH = {}  # none captured for the current refinement kernel on a bench workload
 
 
 def refine_fp64_flops(rep, n):
@@ -550,6 +550,25 @@ def run_profile_case(name):
     import torch
     import paper_2107_06200_gb300 as M
     from synth import randsvd_system
+    if name == "batched_engine_64":
+        # the batched engine on the first 64 systems of n <= 256 of the
+        # 4096-system workload (workspaces of ~4 MB per block): two launches
+        from synth import batched_systems
+        sel = [s for s in batched_systems(4096, seed=0) if s[0] <= 256][:64]
+        dev = torch.device("cuda", 0)
+        ctx = M.Context(0)
+        As, bs = [], []
+        for (n, kappa, seed) in sel:
+            A, B, _ = randsvd_system(n, kappa, seed)
+            As.append(torch.from_numpy(A).to(dev))
+            bs.append(torch.from_numpy(B[:, 0].copy()).to(dev))
+        for _ in range(2):
+            xs, reps, st = ctx.solve_batched(As, bs, "fp16,fp32,fp64")
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": name, "status": st, "systems": len(sel),
+                          "converged": sum(bool(r["cged"]) for r in reps)}))
+        ctx.close()
+        return
     n, kappa, spec, graded, reps, kf = PROFILE_CASES[name]
     A, B, _ = randsvd_system(n, kappa, 0, graded=graded, device="cuda:0" if n >= 4096 else None)
     dev = torch.device("cuda", 0)
@@ -576,7 +595,7 @@ def main():
     ap.add_argument("--no-gemv", action="store_true", help="skip the operator bandwidth measurement")
     ap.add_argument("--no-cost-aware", action="store_true",
                     help="skip the extra pass with the cost-aware k_max")
-    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES),
+    ap.add_argument("--profile-case", default=None, choices=sorted(PROFILE_CASES) + ["batched_engine_64"],
                     help="run one untimed solve of a named small case (for ncu captures) and exit")
     ap.add_argument("--sequential", action="store_true",
                     help="solve the systems one after another with msir_solve instead of msir_solve_batched")
@@ -656,7 +675,8 @@ def main():
         # the batched engine's tile shapes (LU blocking per u_f and size
         # bucket) from the library's autotuner, untimed
         tab = ctx.autotune_batched(samples=152)
-        tuned = {f"{uf} n<={64 << b}": f"nb={v[0]} nbo={v[1]}" for (uf, b), v in tab.items()
+        tuned = {f"{uf} n<={64 << b}": f"nb={v[0]} nbo={v[1]} ({v[2]:.3f} ms for 152 LUs of n={64 << b})"
+                 for (uf, b), v in tab.items()
                  if uf in {sp.split(",")[0] for sp in (s_["spec"] for s_ in systems)} or uf == "fp32"}
     As = [torch.from_numpy(s_["A"]).to(dev) for s_ in systems]
     bs = [torch.from_numpy(np.ascontiguousarray(s_["b"])).to(dev) for s_ in systems]

@@ -309,9 +309,10 @@ msir_status msir_autotune_batched(msir_ctx* ctx, int samples, const char* cache_
  * memory).  max_slots: requests in flight on the device at once.  A worker
  * thread admits queued requests into free slots, each on its own stream:
  * a request is admitted when the device memory it needs (its workspace and
- * its A, b, x in the slot) fits the budget; requests are taken in arrival
- * order, and one that does not fit may be passed by later requests that do,
- * at most 8 times, after which it waits for memory to free up.  Slots keep
+ * its A, b, x in the slot) fits the budget.  Among the waiting requests
+ * that fit, the one with the fewest rows (the least work) goes first; once
+ * the request at the head of the queue (the oldest) has been passed 8
+ * times it goes next, waiting for memory to free up if it must.  Slots keep
  * their workspaces between requests and give them back only when a request
  * would not fit otherwise. */
 msir_status msir_server_create(msir_ctx* ctx, size_t hbm_budget_bytes, int max_slots,
@@ -332,9 +333,9 @@ msir_status msir_server_submit(msir_server* s, int n, const double* A_host, int 
 
 /* Admission by expected waiting time (the paper has no counterpart; a
  * serving policy).  With max_backlog_ms > 0, a submission is refused with
- * MSIR_ERR_BUSY when the queued requests' work, sum of n^3, divided by the
- * server's recent completion rate (n^3 per ms over its last 32 completed
- * requests) exceeds max_backlog_ms.  Until 4 requests have completed there
+ * MSIR_ERR_BUSY when the queued and running requests' work, sum of n^3,
+ * divided by the server's recent completion rate (n^3 per ms over its last
+ * 32 completed requests) exceeds max_backlog_ms.  Until 4 requests have completed there
  * is no rate and only the host-memory limit applies.  0 (the default)
  * removes the limit.  MSIR_ERR_INVALID for a negative or non-finite value. */
 msir_status msir_server_set_backlog_limit(msir_server* s, double max_backlog_ms);

@@ -2056,7 +2056,8 @@ struct msir_server {
   std::vector<ServerSlot> slots;
   // admission by expected waiting time (msir_server_set_backlog_limit)
   double max_backlog_ms = 0.0;
-  double queued_work = 0.0;  // sum of n^3 over queued requests
+  double queued_work = 0.0;   // sum of n^3 over queued requests
+  double running_work = 0.0;  // sum of n^3 over admitted, unfinished requests
   std::deque<std::pair<double, double>> done_log;  // (completion time in ms, n^3), last kRateWindow
 };
 
@@ -2069,15 +2070,17 @@ static double steady_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// Expected waiting time of the queue in ms (work over the measured rate), or
-// -1 while fewer than 4 requests have completed.  Caller holds S->mu.
+// Expected waiting time of a new request in ms: the queued and running
+// requests' work over the measured rate (running work counted whole: an
+// upper bound), or -1 while fewer than 4 requests have completed.  Caller
+// holds S->mu.
 static double server_backlog_ms(const msir_server* S) {
   if (S->done_log.size() < 4) return -1.0;
   double w = 0.0;
   for (size_t i = 1; i < S->done_log.size(); ++i) w += S->done_log[i].second;
   const double span = S->done_log.back().first - S->done_log.front().first;
   if (!(span > 0.0) || !(w > 0.0)) return -1.0;
-  return S->queued_work / (w / span);
+  return (S->queued_work + S->running_work) / (w / span);
 }
 
 static size_t request_footprint(int n, const msir_params& p, int u) {
@@ -2154,18 +2157,25 @@ static void server_loop(msir_server* S) {
         Request* pick = nullptr;
         size_t delta = 0;
         for (int attempt = 0; attempt < 2 && !pick; ++attempt) {
+          // the smallest waiting request that fits (fewest rows: least work),
+          // unless the head of the queue has been passed kMaxBypass times
+          const bool head_turn = S->queue.front()->bypassed >= kMaxBypass;
+          auto pick_it = S->queue.end();
           for (auto it = S->queue.begin(); it != S->queue.end(); ++it) {
             Request* q = *it;
             const size_t d = admit_delta(ss, q->footprint);
             const bool fits = S->in_use + d <= S->budget || S->in_use == 0;
-            if (fits) {
+            if (fits && (!pick || q->job.n < pick->job.n)) {
               pick = q;
+              pick_it = it;
               delta = d;
-              S->queue.erase(it);
-              S->queued_work -= request_work(q->job.n);
-              break;
             }
-            if (it == S->queue.begin() && q->bypassed >= kMaxBypass) break;  // the head's turn
+            if (head_turn) break;  // only the head may go (or nothing, until memory frees up)
+          }
+          if (pick) {
+            S->queue.erase(pick_it);
+            S->queued_work -= request_work(pick->job.n);
+            S->running_work += request_work(pick->job.n);
           }
           if (pick || attempt > 0) break;
           // nothing fits: idle slots give back what they keep, then retry
@@ -2233,6 +2243,7 @@ static void server_loop(msir_server* S) {
         q->job.t_done = std::chrono::steady_clock::now();
         q->state = 2;
         ss.req = nullptr;
+        S->running_work -= request_work(q->job.n);
         S->done_log.emplace_back(steady_ms(), request_work(q->job.n));
         if (S->done_log.size() > kRateWindow) S->done_log.pop_front();
       }

@@ -58,12 +58,17 @@ __device__ __forceinline__ F lu_store(LuT<F> v) {
   else return from_t<F>(v);
 }
 
-// bytes of shared memory cta_lu needs for panels of width nb (row stride
-// nb + 1) over up to kCtaLuMax rows; the substitution and update tiles fit
-// in the same space
+// bytes of shared memory cta_lu needs: the largest of its three uses of
+// the same space, a panel of width nb (row stride nb + 1) over up to
+// kCtaLuMax rows, the substitution's L11 and column chunk (two 64 x 65
+// tiles) and the update's L21 and U12 tiles (32 x 65 and 64 x 33)
 template <typename F>
 constexpr size_t cta_lu_smem(int nb) {
-  return (size_t)kCtaLuMax * (nb + 1) * sizeof(LuT<F>);
+  const size_t panel = (size_t)kCtaLuMax * (nb + 1);
+  const size_t trsm = (size_t)2 * 64 * 65;
+  const size_t upd = (size_t)32 * 65 + 64 * 33;
+  const size_t m = panel > trsm ? panel : trsm;
+  return (m > upd ? m : upd) * sizeof(LuT<F>);
 }
 
 // Argmax of |P[r][j]| over rows r in [j, m) (NaN counts as -1, ties go to

@@ -603,6 +603,10 @@ __device__ __forceinline__ unsigned inbox_tag(unsigned epoch, int round) {
   return ((epoch << 8) | ((unsigned)round & 0xffu)) & 0x7fffffffu;
 }
 
+// Offset of the second probe of a substitution hand-off (about half the
+// round trip of an L2 load on GB300).
+constexpr unsigned kPollStaggerNs = 250;
+
 // Payload words of one block held by one lane: values lane and lane + 32.
 template <int W>
 struct LLRaw {
@@ -638,7 +642,26 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
   constexpr int W = ACC::kW;
   unsigned long long t0 = 0;
   unsigned spins = 0;
+  // Not there yet: two probes of the words in flight, the second issued
+  // about half a load round trip after the first and each re-issued as soon
+  // as it returns, so the words are seen within half a round trip of their
+  // arrival instead of a whole one.
+  LLRaw<W> b;
+  bool two = false;
   while (!ll_ready<W>(r, epoch)) {
+    if (!two) {
+      ll_issue<W>(blk, lane, r);
+      __nanosleep(kPollStaggerNs);
+      ll_issue<W>(blk, lane, b);
+      two = true;
+      if (ll_ready<W>(r, epoch)) break;
+    }
+    ll_issue<W>(blk, lane, r);
+    if (ll_ready<W>(b, epoch)) {
+      r = b;
+      break;
+    }
+    ll_issue<W>(blk, lane, b);
     if ((++spins & 255u) == 0u) {
       int bad = 0;
       if (lane == 0) {
@@ -667,7 +690,6 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
       }
       if (bad) return false;
     }
-    ll_issue<W>(blk, lane, r);
   }
   __syncwarp();  // the previous block's staged values have been consumed
 #pragma unroll
