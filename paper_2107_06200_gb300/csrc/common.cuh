@@ -258,10 +258,6 @@ __device__ __forceinline__ void record_timeout(int* err, int site, int v0, int v
 __device__ __forceinline__ bool grid_barrier_for(unsigned* count, int* err, unsigned G,
                                                  unsigned long long limit_ns) {
   __shared__ int s_ok;
-  if (G == 1) {  // a grid of one block (the batched engine): a block barrier orders its memory
-    __syncthreads();
-    return true;
-  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;

@@ -603,10 +603,6 @@ __device__ __forceinline__ unsigned inbox_tag(unsigned epoch, int round) {
   return ((epoch << 8) | ((unsigned)round & 0xffu)) & 0x7fffffffu;
 }
 
-// Offset of the second probe of a substitution hand-off (about half the
-// round trip of an L2 load on GB300).
-constexpr unsigned kPollStaggerNs = 250;
-
 // Payload words of one block held by one lane: values lane and lane + 32.
 template <int W>
 struct LLRaw {
@@ -642,26 +638,7 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
   constexpr int W = ACC::kW;
   unsigned long long t0 = 0;
   unsigned spins = 0;
-  // Not there yet: two probes of the words in flight, the second issued
-  // about half a load round trip after the first and each re-issued as soon
-  // as it returns, so the words are seen within half a round trip of their
-  // arrival instead of a whole one.
-  LLRaw<W> b;
-  bool two = false;
   while (!ll_ready<W>(r, epoch)) {
-    if (!two) {
-      ll_issue<W>(blk, lane, r);
-      __nanosleep(kPollStaggerNs);
-      ll_issue<W>(blk, lane, b);
-      two = true;
-      if (ll_ready<W>(r, epoch)) break;
-    }
-    ll_issue<W>(blk, lane, r);
-    if (ll_ready<W>(b, epoch)) {
-      r = b;
-      break;
-    }
-    ll_issue<W>(blk, lane, b);
     if ((++spins & 255u) == 0u) {
       int bad = 0;
       if (lane == 0) {
@@ -690,6 +667,7 @@ __device__ __forceinline__ bool ll_complete(const unsigned long long* blk, unsig
       }
       if (bad) return false;
     }
+    ll_issue<W>(blk, lane, r);
   }
   __syncwarp();  // the previous block's staged values have been consumed
 #pragma unroll
@@ -1851,7 +1829,7 @@ static __device__ int ctl_step(RefState& S, const RefineArgs& a, double s, doubl
 // one CTA alone (cx.G = 1) in the batched engine.  S, s_act, s_reset and
 // s_alg live in shared memory.  Returns false if a device wait failed.
 template <typename A0, typename F>
-__device__ bool refine_msir(Cx& cx, const RefineArgs& a, RefState& S, unsigned char* gsm, int& s_act,
+__device__ __forceinline__ bool refine_msir(Cx& cx, const RefineArgs& a, RefState& S, unsigned char* gsm, int& s_act,
                             int& s_reset, int& s_alg) {
   bool ok = true;
   const int ff = factor_fmt<F>(a);
