@@ -269,6 +269,16 @@ msir_status msir_solve_batched(msir_ctx* ctx, int count, const int* n,
                                double* const* x_dev, const msir_triple* t,
                                const msir_params* params, msir_report* reps);
 
+/* msir_solve_batched with host buffers: A_host[i] (n[i] x n[i], column-
+ * major, lda = n[i]), b_host[i] and x_host[i] (n[i] doubles) are host
+ * memory (pinned memory copies fastest).  The call copies A and b into one
+ * device allocation on the context stream, solves as msir_solve_batched
+ * and copies every x back before it returns.  Errors as msir_solve_batched,
+ * and MSIR_ERR_NOMEM if the device copy cannot be allocated. */
+msir_status msir_solve_batched_host(msir_ctx* ctx, int count, const int* n, const double* const* A_host,
+                                    const double* const* b_host, double* const* x_host, const msir_triple* t,
+                                    const msir_params* params, msir_report* reps);
+
 /* Batched LU, the factorisation of the batched engine (Algorithm 4's first
  * step for many small systems in one launch; Sec. 1).  System i:
  * A_dev[i] is n[i] x n[i] fp64 column-major (lda = n[i]), 1 <= n[i] <= 512;

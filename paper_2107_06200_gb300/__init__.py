@@ -281,6 +281,33 @@ class Context:
                     "solve_batched")
         return xs, [report_to_dict(reps[i]) for i in range(cnt)], st
 
+    def solve_batched_host(self, As, bs, specs, params=None):
+        """msir_solve_batched_host: lists of host arrays (numpy, or pinned torch
+        CPU tensors) A_i (n_i x n_i) and b_i; the C call copies them to the
+        device and the solutions back.  Returns (xs (numpy), reports, status)."""
+        cnt = len(As)
+
+        def host(a, colmajor):
+            if hasattr(a, "numpy"):  # a torch CPU tensor (e.g. pinned): keep its memory
+                a = a.numpy()
+            a = np.asarray(a, dtype=np.float64)
+            return np.asfortranarray(a) if colmajor else np.ascontiguousarray(a)
+        Ah = [host(A, True) for A in As]
+        bh = [host(b, False) for b in bs]
+        xs = [np.empty(b.shape[0]) for b in bh]
+        ns = (ctypes.c_int * cnt)(*[A.shape[0] for A in Ah])
+        Ap = (ctypes.c_void_p * cnt)(*[A.ctypes.data for A in Ah])
+        bp = (ctypes.c_void_p * cnt)(*[b.ctypes.data for b in bh])
+        xp = (ctypes.c_void_p * cnt)(*[x.ctypes.data for x in xs])
+        if isinstance(specs, (str, Triple)):
+            specs = [specs] * cnt
+        tp = (Triple * cnt)(*[triple(s) for s in specs])
+        reps = (Report * cnt)()
+        p = params or params_default()
+        st = _check(_L.msir_solve_batched_host(self.h, cnt, ns, Ap, bp, xp, tp, ctypes.byref(p), reps),
+                    "solve_batched_host")
+        return xs, [report_to_dict(reps[i]) for i in range(cnt)], st
+
     def autotune_batched(self, samples=152, cache_path=None):
         """msir_autotune_batched: returns {(u_f name, bucket): (nb, nbo, ms)}
         (buckets 0..3 for n <= 64, 128, 256, 512); samples=0 reads cache_path."""

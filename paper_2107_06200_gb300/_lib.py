@@ -27,7 +27,7 @@ EXPORTED = [
     "msir_solve_batched", "msir_server_create", "msir_server_submit", "msir_server_poll",
     "msir_server_destroy", "msir_server_set_backlog_limit", "msir_status_string", "msir_residual_noalloc", "msir_probe_fma_rate",
     "msir_probe_wait_timeout", "msir_probe_widen_check", "msir_factor_batched",
-    "msir_autotune_batched",
+    "msir_autotune_batched", "msir_solve_batched_host",
 ]
 
 
@@ -99,6 +99,8 @@ def load(path=LIB_PATH):
         "msir_factor_batched": [P, I, pI, ctypes.POINTER(P), I, I, I, ctypes.POINTER(P), ctypes.POINTER(P),
                                 ctypes.POINTER(P)],
         "msir_autotune_batched": [P, I, ctypes.c_char_p, pI, pI, pD],
+        "msir_solve_batched_host": [P, I, pI, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.POINTER(P),
+                                    ctypes.POINTER(Triple), ctypes.POINTER(Params), ctypes.POINTER(Report)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)

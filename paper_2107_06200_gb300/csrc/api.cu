@@ -1766,6 +1766,54 @@ static msir_status run_batch_engine(msir_ctx* ctx, const std::vector<int>& idx, 
   return MSIR_OK;
 }
 
+msir_status msir_solve_batched_host(msir_ctx* ctx, int count, const int* n, const double* const* A_host,
+                                    const double* const* b_host, double* const* x_host, const msir_triple* t,
+                                    const msir_params* params, msir_report* reps) {
+  if (!ctx || count < 0 || (count > 0 && (!n || !A_host || !b_host || !x_host || !t))) return MSIR_ERR_INVALID;
+  for (int i = 0; i < count; ++i)
+    if (n[i] <= 0 || !A_host[i] || !b_host[i] || !x_host[i]) return MSIR_ERR_INVALID;
+  if (count == 0) return MSIR_OK;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t st = ctx->stream;
+  std::vector<size_t> offA(count), offb(count), offx(count);
+  size_t total = 0;
+  for (int i = 0; i < count; ++i) {
+    offA[i] = total;
+    total += round_up((size_t)n[i] * n[i] * 8, 256);
+    offb[i] = total;
+    total += round_up((size_t)n[i] * 8, 256);
+    offx[i] = total;
+    total += round_up((size_t)n[i] * 8, 256);
+  }
+  char* buf = nullptr;
+  if (cudaMallocAsync((void**)&buf, total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return MSIR_ERR_NOMEM;
+  }
+  std::vector<const double*> dA(count), db(count);
+  std::vector<double*> dx(count);
+  msir_status r = MSIR_OK;
+  for (int i = 0; i < count && r == MSIR_OK; ++i) {
+    dA[i] = (const double*)(buf + offA[i]);
+    db[i] = (const double*)(buf + offb[i]);
+    dx[i] = (double*)(buf + offx[i]);
+    r = cuda_status(cudaMemcpyAsync((void*)dA[i], A_host[i], (size_t)n[i] * n[i] * 8, cudaMemcpyHostToDevice, st));
+    if (r == MSIR_OK)
+      r = cuda_status(cudaMemcpyAsync((void*)db[i], b_host[i], (size_t)n[i] * 8, cudaMemcpyHostToDevice, st));
+  }
+  msir_status rs = r;
+  if (r == MSIR_OK) rs = msir_solve_batched(ctx, count, n, dA.data(), db.data(), dx.data(), t, params, reps);
+  if (rs >= 0) {
+    for (int i = 0; i < count && r == MSIR_OK; ++i)
+      r = cuda_status(cudaMemcpyAsync(x_host[i], dx[i], (size_t)n[i] * 8, cudaMemcpyDeviceToHost, st));
+    if (r == MSIR_OK) r = cuda_status(cudaStreamSynchronize(st));
+  }
+  cudaFreeAsync(buf, st);
+  cudaStreamSynchronize(st);
+  if (r != MSIR_OK) return r;
+  return rs;
+}
+
 msir_status msir_factor_batched(msir_ctx* ctx, int count, const int* n, const double* const* A_dev, int fmt,
                                 int nb, int nbo, double* const* F_dev, int* const* ipiv_dev,
                                 int* const* flags_dev) {

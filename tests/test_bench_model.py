@@ -96,3 +96,15 @@ def test_engine_flops_count_fp32_pipe_factorisations():
     rep64 = {"n_factorizations": 2, "stages": st[:1] + [dict(st[1], uf="fp64")], "total_steps": 5,
              "total_gmres_iters": 0}
     assert bench.engine_flops(rep64, n) == pytest.approx((2.0 / 3.0) * n ** 3 + bench.refine_algorithmic_flops(rep64, n))
+
+
+def test_engine_fp64_flops_count_inverses_and_scaled_blocks():
+    """Per factorisation: 2 ceil(n/64) inverse blocks of 64^3/6 terms at 11
+    fp64 operations, and 128 n^2 flops for the scaled blocks; plus the
+    refinement's fp64 work."""
+    import bench
+    n = 130
+    st = [{"uf": "fp16", "alg": "SIR", "u": "fp32", "ur": "fp64", "steps": 3, "gmres_iters": [0] * 48}]
+    rep = {"n_factorizations": 1, "stages": st, "total_steps": 3, "total_gmres_iters": 0}
+    per = 2 * 3 * (64 ** 3 / 6.0) * 11.0 + 2.0 * 64 * n * n
+    assert bench.engine_fp64_flops(rep, n) == pytest.approx(per + bench.refine_fp64_flops(rep, n))

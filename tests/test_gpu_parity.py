@@ -432,6 +432,26 @@ def test_batched_autotuner_table_cache_and_use(ctx, M, tmp_path):
         ctx2.close()
 
 
+def test_batched_host_buffers_equal_device_buffers(ctx, M):
+    """msir_solve_batched_host (host A, b, x; the copies inside the call)
+    gives bit for bit the solutions and the stage reports of
+    msir_solve_batched on device copies of the same systems (engine and
+    slots)."""
+    cases = [(90, 1e3, HSD, 1), (300, 1e5, HSD, 2), (600, 1e3, SDQ, 3)]
+    As, bs, specs = [], [], []
+    for (n, kappa, spec, seed) in cases:
+        A, B, _ = randsvd_system(n, kappa, 700 + seed)
+        As.append(A)
+        bs.append(B[:, 0].copy())
+        specs.append(spec)
+    xh, rh, sth = ctx.solve_batched_host(As, bs, specs)
+    xd, rd, std = ctx.solve_batched([to_dev(A) for A in As], [to_dev(b) for b in bs], specs)
+    assert sth == std
+    for a, b, r1, r2 in zip(xh, xd, rh, rd):
+        assert np.array_equal(a, b.cpu().numpy())
+        assert r1["steps"] == r2["steps"] and r1["cged"] == r2["cged"]
+
+
 def test_batched_engine_and_slots_in_one_call(ctx, M):
     """A batch mixing engine systems (n <= 512) with larger ones (the
     concurrent slots) returns every result in its place: each converges to
