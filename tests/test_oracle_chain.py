@@ -213,3 +213,22 @@ def test_outer_update_models_differ_where_fp32_rounds(fmt):
     OL._update(Fc, 0, 3, 3, 4, fmt, tensor_core=False)
     assert Ft[3, 3] == -(2.0 ** -10)
     assert Fc[3, 3] == 0.0
+
+
+@pytest.mark.parametrize("fmt,e", [(OF.FP16, 11), (OF.BF16, 8)])
+def test_tensor_core_update_rounds_twice(fmt, e):
+    """The tensor-core outer update rounds the exact sum to fp32 and then to
+    u_f.  C = 1, L21 U12 = -(2^-e + 2^-40) puts C - L21 U12 just above the
+    midpoint 1 + 2^-e between 1 and the next u_f value: one rounding gives
+    1 + 2^(1-e), but fp32 drops the 2^-40 and the tie then goes to the even
+    neighbour 1.  A single rounding, or a missing fp32 step, fails this."""
+    F = np.zeros((3, 3))
+    F[2, 0:2] = [2.0 ** -e, 2.0 ** -20]
+    F[0:2, 2] = [-1.0, -(2.0 ** -20)]
+    F[2, 2] = 1.0
+    exact = Fraction(1) + Fraction(1, 2 ** e) + Fraction(1, 2 ** 40)
+    # one rounding to u_f (spacing 2^(1-e) on [1, 2)) would go up: exact is
+    # past the midpoint 1 + 2^-e
+    assert Fraction(1) + Fraction(1, 2 ** e) < exact < Fraction(1) + Fraction(2, 2 ** e)
+    OL._update(F, 0, 2, 2, 3, fmt, tensor_core=True)
+    assert F[2, 2] == 1.0

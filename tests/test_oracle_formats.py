@@ -160,3 +160,20 @@ def test_dd_pairwise_sum_accuracy():
     got = Fraction(float(s[0])) + Fraction(float(s[1]))
     bound = Fraction(2) ** -100 * sum(abs(Fraction(float(a)) * Fraction(float(b))) for a, b in zip(x, y))
     assert abs(got - exact) <= bound
+
+
+@pytest.mark.parametrize("fmt,e", [(F.FP16, 11), (F.BF16, 8)])
+def test_16bit_rounding_of_fp64_goes_through_fp32(fmt, e):
+    """fl_f(x) of an fp64 x is fl_f(fl_32(x)): the 16-bit values of the method
+    come from fp32 arithmetic on both sides, and the fp64 -> 16-bit rounding of
+    A_f at u0 = fp64 takes the same route.  x = 1 + 2^-e + 2^-40 lies just
+    above the midpoint between 1 and the next u_f value, so one rounding would
+    give 1 + 2^(1-e); fp32 lands on the midpoint and the tie goes to 1.  Below
+    the midpoint both routes agree."""
+    x = 1.0 + 2.0 ** -e + 2.0 ** -40
+    assert round_q(Fraction(x), "fp16" if fmt == F.FP16 else "bf16") == 1.0 + 2.0 ** (1 - e)
+    assert float(F.fl(np.array([x]), fmt)[0]) == 1.0
+    y = 1.0 + 2.0 ** -e - 2.0 ** -40
+    assert float(F.fl(np.array([y]), fmt)[0]) == 1.0
+    z = 1.0 + 2.0 ** -e + 2.0 ** -20  # kept by fp32: both routes go up
+    assert float(F.fl(np.array([z]), fmt)[0]) == 1.0 + 2.0 ** (1 - e)
