@@ -96,7 +96,9 @@ typedef enum {
  * double, Sec. 3), gamma = sqrt(n) (Algorithm 4). */
 typedef struct {
   int i_max;            /* maximum steps of each variant (Sec. 2.1)          */
-  double rho_thresh;    /* ratio threshold of successive corrections          */
+  double rho_thresh;    /* ratio threshold of successive corrections; 0.5 is
+                           Sec. 2.1.1's cautious setting, 0.9 its aggressive
+                           one (more steps per stage on hard problems)       */
   double kmax_frac;     /* k_max = kmax_frac * n GMRES iterations per step;
                            < 0: cost-aware k_max, at most |kmax_frac| * n: a
                            GMRES stage stops once its iterations have cost

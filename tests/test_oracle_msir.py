@@ -47,6 +47,37 @@ def test_ratio_exactly_at_threshold_switches():
     assert v == 0.5 and a == "switch"
 
 
+def test_aggressive_threshold_keeps_a_slow_stage_going():
+    """Sec. 2.1.1: the aggressive setting rho_thresh = 0.9 against the cautious
+    0.5.  A ratio of 0.6 switches the cautious controller and not the
+    aggressive one; 0.9 itself switches both ways of reading the test."""
+    for rho, expect in ((0.5, "switch"), (0.9, "continue")):
+        c = _ctl(rho_thresh=rho)
+        c.step(1.0, 1e-1, 1.0, F.FP32, 1e-3)
+        a, reset, z, v, phi = c.step(1.0, 0.6e-1, 1.0, F.FP32, 1e-3)
+        assert v == pytest.approx(0.6) and a == expect
+    c = _ctl(rho_thresh=0.9)
+    c.step(1.0, 2.0 ** -4, 1.0, F.FP32, 1e-3)
+    a, reset, z, v, phi = c.step(1.0, 0.9 * 2.0 ** -4, 1.0, F.FP32, 1e-3)
+    assert v == pytest.approx(0.9) and a == "switch"
+
+
+def test_aggressive_mode_takes_more_sir_steps_and_converges():
+    """Sec. 2.1.1: the aggressive setting spends more steps in a stage on the
+    harder problems.  At kappa = 3e4, (half, single, double), the cautious run
+    leaves SIR after two steps and needs SGMRES-IR, GMRES-IR and an fp32
+    refactorisation; the aggressive run stays in SIR to i_max and finishes in
+    SGMRES-IR on the fp16 factors."""
+    cautious, *_ = _run(100, 3e4, HSD, nb=32, rho_thresh=0.5)
+    aggressive, A_u, b_u, xr = _run(100, 3e4, HSD, nb=32, rho_thresh=0.9)
+    assert cautious.cged and aggressive.cged
+    assert aggressive.stages[0].steps > cautious.stages[0].steps
+    assert aggressive.stages[0].steps == 10  # i_max
+    assert len({st.uf for st in aggressive.stages}) == 1  # no refactorisation
+    assert len({st.uf for st in cautious.stages}) == 2
+    assert X.nbe(A_u, b_u, aggressive.x) <= 2 * F.u_of(F.FP32)
+
+
 def test_divergence_resets_x():
     c = _ctl()
     c.step(1.0, 1e-2, 1.0, F.FP32, 1e-3)
