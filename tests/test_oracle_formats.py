@@ -177,3 +177,23 @@ def test_16bit_rounding_of_fp64_goes_through_fp32(fmt, e):
     assert float(F.fl(np.array([y]), fmt)[0]) == 1.0
     z = 1.0 + 2.0 ** -e + 2.0 ** -20  # kept by fp32: both routes go up
     assert float(F.fl(np.array([z]), fmt)[0]) == 1.0 + 2.0 ** (1 - e)
+
+
+def test_dd_add_keeps_the_low_words_rounding_error():
+    """Cancelling high words leave the sum of the low words, whose own
+    rounding error (2^-114 here) must survive: 2^-60 + 2^-114 is a dd number,
+    so the accurate addition returns it exactly."""
+    a = (1.0, 2.0 ** -60)
+    b = (-1.0, 2.0 ** -114)
+    s = F.dd_add(a, b)
+    assert Fraction(s[0]) + Fraction(s[1]) == Fraction(1, 2 ** 60) + Fraction(1, 2 ** 114)
+
+
+def test_dd_div_third_quotient_term():
+    """a / b with nonzero low words: the third partial quotient brings the
+    error from about 2^-105 (two terms) to below 2^-110 relative."""
+    a = F.fast_two_sum(21.0, 21.0 * 2.0 ** -53 * (1 + 2.0 ** -20))
+    b = F.fast_two_sum(1.0, 2.0 ** -53 * (1 - 2.0 ** -21))
+    exact = (Fraction(a[0]) + Fraction(a[1])) / (Fraction(b[0]) + Fraction(b[1]))
+    q = F.dd_div(a, b)
+    assert abs(Fraction(q[0]) + Fraction(q[1]) - exact) <= exact * Fraction(1, 2 ** 110)

@@ -99,3 +99,14 @@ def test_fp16_overflow_shows_up_as_inf():
     Fm, _, _ = L.lu_factor(B, F.FP16, 2)
     # u_22 = -60000 - 60000 = -120000 overflows fp16
     assert np.isinf(Fm[1, 1])
+
+
+def test_default_blocking():
+    """Panels of 32 columns (16 when the panel is held in fp64) inside outer
+    blocks of 64, and of 128 from n = 4096 (fewer roundings of the trailing
+    matrix to u_f)."""
+    for fmt in (F.BF16, F.FP16, F.FP32):
+        assert L.default_blocking(fmt, 4095) == (32, 64)
+        assert L.default_blocking(fmt, 4096) == (32, 128)
+    assert L.default_blocking(F.FP64, 100) == (16, 64)
+    assert L.default_blocking(F.FP64, 16384) == (16, 128)

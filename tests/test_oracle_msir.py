@@ -78,6 +78,32 @@ def test_aggressive_mode_takes_more_sir_steps_and_converges():
     assert X.nbe(A_u, b_u, aggressive.x) <= 2 * F.u_of(F.FP32)
 
 
+def test_small_correction_is_relative_to_x():
+    """z = ||d|| ||r|| / ||x||: the same correction is small against a large
+    x (z <= u switches) and not against x of norm 1."""
+    c = _ctl()
+    a, reset, z, v, phi = c.step(1.0, 1e-3, 1e6, F.FP32, 1e-3)
+    assert z == pytest.approx(1e-9) and a == "switch"
+    c = _ctl()
+    a, reset, z, v, phi = c.step(1.0, 1e-3, 1.0, F.FP32, 1e-3)
+    assert z == pytest.approx(1e-3) and a == "continue"
+
+
+def test_convergence_threshold_is_gamma_u():
+    """Algorithm 4 stops when phi <= gamma u (gamma = sqrt(n) = 10 here):
+    phi = 5u converges, phi = 11u does not."""
+    u = F.u_of(F.FP32)
+    c = _ctl(n=100)
+    a = c.step(1.0, 5 * u, 1.0, F.FP32, nbe_new=u)[0]
+    assert a == "converged"
+    c = _ctl(n=100)
+    a = c.step(1.0, 11 * u, 1.0, F.FP32, nbe_new=u)[0]
+    assert a == "continue"
+    c = _ctl(n=100, gamma=1.0)
+    a = c.step(1.0, 5 * u, 1.0, F.FP32, nbe_new=u)[0]
+    assert a == "continue"
+
+
 def test_divergence_resets_x():
     c = _ctl()
     c.step(1.0, 1e-2, 1.0, F.FP32, 1e-3)
@@ -295,3 +321,76 @@ def test_true_mode_run_meets_its_criterion():
     comb = M.msir(A, b, HSD)
     # the exact test can only stop later than (or with) the computable one here
     assert sum(s.steps for s in res.stages) >= sum(s.steps for s in comb.stages) - 1
+
+
+def _instrumented_run(monkeypatch, n, kappa, triple, **kw):
+    """Run the oracle with its residual, controller and GMRES calls logged."""
+    from oracle import gmres as G
+    log = []
+    real_resid, real_step, real_gmres = M.res_mod.residual, M.Controller.step, G.gmres
+
+    def resid(A, b, x, fmt_r):
+        log.append(("resid", np.array(x, copy=True)))
+        return real_resid(A, b, x, fmt_r)
+
+    def step(self, *a, **k):
+        out = real_step(self, *a, **k)
+        log.append(("step", out[0], out[1]))
+        return out
+
+    def gm(fac, A, r, fmt_u, fmt_op, *a, **k):
+        log.append(("gmres", fmt_u, fmt_op))
+        return real_gmres(fac, A, r, fmt_u, fmt_op, *a, **k)
+
+    monkeypatch.setattr(M.res_mod, "residual", resid)
+    monkeypatch.setattr(M.Controller, "step", step)
+    monkeypatch.setattr(M.gmres_mod, "gmres", gm)
+    res, A_u, b_u, xr = _run(n, kappa, triple, **kw)
+    return res, log, A_u, b_u
+
+
+def test_a_reset_restarts_the_next_stage_from_x0(monkeypatch):
+    """Sec. 2.1.1: when a stage ends with phi above phi_0 the next stage
+    starts again from x_0.  At kappa = 1e8 (half, single, double) the run
+    switches three times with phi > phi_0; after each, the first residual
+    is that of x_0 (the first x whose residual the run takes)."""
+    res, log, *_ = _instrumented_run(monkeypatch, 60, 1e8, HSD, nb=16)
+    x0 = next(e[1] for e in log if e[0] == "resid")
+    resets = 0
+    for i, e in enumerate(log):
+        if e[0] == "step" and e[1] == "switch" and e[2]:
+            nxt = next(f for f in log[i + 1:] if f[0] == "resid")
+            assert np.array_equal(nxt[1], x0)
+            resets += 1
+    assert resets >= 1 and res.cged
+
+
+def test_gmres_ir_applies_the_operator_in_u_squared(monkeypatch):
+    """Algorithm 3 (SGMRES-IR) applies the preconditioned operator in u,
+    Algorithm 2 (GMRES-IR) in u^2: every GMRES call of an SGMRES-IR stage
+    has operator precision u and every call of a GMRES-IR stage u^2."""
+    res, log, *_ = _instrumented_run(monkeypatch, 66, 1e6, HSD, nb=16)
+    calls = [e[1:] for e in log if e[0] == "gmres"]
+    n_sg = sum(st.steps for st in res.stages if st.alg == M.SGMRES)
+    n_g = sum(st.steps for st in res.stages if st.alg == M.GMRES)
+    assert n_sg >= 1 and n_g >= 1
+    assert calls == [(F.FP32, F.FP32)] * n_sg + [(F.FP32, F.FP64)] * n_g
+
+
+def test_gmres_cap_is_the_ceiling_of_kmax():
+    """k_max = 0.1 n GMRES iterations per step, taken as ceil(0.1 n): at
+    n = 66 a GMRES step that does not reach tau stops after 7 iterations."""
+    res, *_ = _run(66, 1e6, HSD, nb=16)
+    its = [k for st in res.stages for k in st.gmres_iters]
+    assert its and max(its) == 7 and 7 in its
+
+
+def test_a_run_that_does_not_converge_returns_its_best_iterate():
+    """Without escalation the (half, single, double) run at kappa = 1e8
+    stops unconverged; it returns the iterate of smallest nbe, which is not
+    the last one here."""
+    res, A_u, b_u, xr = _run(66, 1e8, HSD, nb=16, allow_escalation=False)
+    assert not res.cged
+    nbes = [h["nbe"] for h in res.history if "nbe" in h]
+    assert res.nbe <= min(nbes) and res.nbe < nbes[-1]
+    assert X.nbe(A_u, b_u, res.x) == pytest.approx(res.nbe, rel=1e-6)

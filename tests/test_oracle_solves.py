@@ -276,12 +276,14 @@ def _sparse_block_factor(n, seed):
 
 
 @pytest.mark.parametrize("arith", [F.FP32, F.FP64])
-def test_block_substitution_exact_across_blocks(arith):
-    n = 150  # two full blocks and a ragged one
+@pytest.mark.parametrize("n", [150, 129, 65])
+def test_block_substitution_exact_across_blocks(arith, n):
+    # 150: two full blocks and a ragged one; 129, 65: a last block of one row
     Fm = _sparse_block_factor(n, 23)
     Lm = np.tril(Fm, -1) + np.eye(n)
     U = np.triu(Fm)
-    x_true = np.random.default_rng(24).integers(-3, 4, n).astype(float)
+    # no zero entries: every coupling between blocks reaches the result
+    x_true = np.random.default_rng(24).choice([-3.0, -2.0, -1.0, 1.0, 2.0, 3.0], n)
     y_true = U @ x_true
     c = Lm @ y_true
     y = T.lower_unit(Fm, c, arith, arith)
@@ -388,3 +390,24 @@ def test_scaled_blocks_against_exact_rationals():
                 assert abs(Fraction(float(M64[i, jc])) - e) <= Fraction(2) ** -46 * mag
                 got = Fraction(float(Mdd[0][i, jc])) + Fraction(float(Mdd[1][i, jc]))
                 assert abs(got - e) <= Fraction(2) ** -98 * mag
+
+
+@pytest.mark.parametrize("fmt_u,fmt_op", [(F.FP32, F.FP32), (F.FP32, F.FP64)])
+def test_operator_is_the_preconditioner_on_the_rounded_product(fmt_u, fmt_op):
+    """Algorithms 2-3 apply M^{-1} A v with A v formed in the operator
+    precision: with u = fp32, apply_operator(v) equals apply_precond on
+    fl_op(A v), A v the exact sum of the fp32 products rounded once."""
+    rng = np.random.default_rng(31)
+    n = 70
+    A, B, _ = randsvd_system(n, 1e3, 31)
+    A_u = F.fl(A, fmt_u).astype(np.float64)
+    Fm, ipiv, info = L.lu_factor(A_u.astype(np.float32), F.FP16)
+    fac = _fac_from(Fm, ipiv, F.FP16)
+    v = F.fl(rng.standard_normal(n), fmt_u).astype(np.float64)
+    Av = np.array([float(sum(Fraction(float(a)) * Fraction(float(b)) for a, b in zip(row, v))) for row in A_u])
+    if fmt_u == F.FP32 and fmt_op == F.FP32:
+        Av = F.fl(Av, F.FP32).astype(np.float64)
+        assert not np.array_equal(Av, A_u @ v)  # the rounding to fp32 is seen
+    got = G.apply_operator(fac, A_u, v, fmt_u, fmt_op)
+    want = G.apply_precond(fac, Av, fmt_u, fmt_op)
+    assert np.array_equal(got, want)
