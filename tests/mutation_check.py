@@ -59,6 +59,11 @@ MISTAKES = [
     ("oracle/lu.py", "nbo = 128 if n >= 4096 else 64", "nbo = 64"),
     ("oracle/lu.py", "            perm[j], perm[p] = perm[p], perm[j]", "            perm[j] = perm[p]"),
     ("oracle/lu.py", "        elif info == 0:\n            info = kk + j + 1", "        elif info == 0:\n            info = kk + j"),
+    ("oracle/chain.c", "acc[j] = fmaf(l, u[j], acc[j]);", "acc[j] = l * u[j] + acc[j];"),
+    ("oracle/chain.c", "for (long m = 0; m < K; ++m) {\n      const float l", "for (long m = K - 1; m >= 0; --m) {\n      const float l"),
+    ("oracle/chain.c", "for (long j = 0; j < N; ++j) c[j] = c[j] - acc[j];\n    free(acc);\n  }\n}\n\nvoid oracle_chain_update_f64",
+     "for (long j = 0; j < N; ++j) c[j] = c[j] + acc[j];\n    free(acc);\n  }\n}\n\nvoid oracle_chain_update_f64"),
+    ("oracle/chain.c", "acc[j] = fma(l, u[j], acc[j]);", "acc[j] = l * u[j] + acc[j];"),
     # formats and double-double
     ("oracle/formats.py", "e = (a - (s - bb)) + (b - bb)", "e = (a - (s - bb)) - (b - bb)"),
     ("oracle/formats.py", "bits + np.uint64(0x7FFF) + lsb", "bits + np.uint64(0x8000) + lsb"),
