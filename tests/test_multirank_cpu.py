@@ -28,7 +28,8 @@ def _rank_main(rank, world, port, q):
         ms = 100.0 + 50.0 * rank           # rank 1 is the slow one
         got = bench.max_over_ranks(ms, world, torch.device("cpu"))
         dist.barrier()
-        rate = bench.whole_job_rate(bench.flops_equiv(2000) * 14, world, got)
+        # the workload once per rank: the job's work is world times a rank's
+        rate = bench.whole_job_rate(bench.flops_equiv(2000) * 14 * world, got)
         q.put((rank, got, rate))
     finally:
         dist.destroy_process_group()
@@ -53,7 +54,7 @@ def test_max_over_ranks_and_weak_rate_with_two_gloo_ranks():
 def test_single_rank_is_identity():
     import bench
     assert bench.max_over_ranks(12.5, 1) == 12.5
-    assert bench.whole_job_rate(1e12, 1, 1000.0) == pytest.approx(1.0)
+    assert bench.whole_job_rate(1e12, 1000.0) == pytest.approx(1.0)
 
 
 def _lpt_rank(rank, world, port, costs, q):
