@@ -48,6 +48,13 @@ R11 x_0 = ||b_u|| * fl_u(M_f^{-1} fl_u(b_u / ||b_u||)) with the u_f
 R12 Update x_{i+1} = fl_u(x_i + fl_u(fl_u(||r_i||) d_{i+1})).
 R13 GMRES tolerance tau: 1e-6 when u = fp32, 1e-10 when u = fp64 (Sec. 3),
     unless given.
+
+Params.ratio_scaled (off by default, test use only) takes Algorithm 4's
+listing literally for the ratio test alone: v = ||d_{i+1}|| / ||d_i|| with
+d the solves of the normalised residuals (z and phi keep R2).  With it the
+oracle reproduces the MSIR columns the paper prints for its randsvd
+experiments (Sec. 3.1, Tables 5-10), where a variant usually stops after two
+steps; those printed columns are its pins.
 """
 
 import math
@@ -79,6 +86,7 @@ class Params:
     nbo: int = 0
     allow_escalation: bool = True
     outer_tc: bool = True     # bf16 / fp16 outer update on tensor cores (lu.lu_factor)
+    ratio_scaled: bool = False  # ratio test on the scaled corrections (module docstring)
 
 
 @dataclass
@@ -188,6 +196,7 @@ class Controller:
         self.it = 0
         self.rho_max = 0.0
         self.delta_prev = math.inf
+        self.dhat_prev = math.inf
         self.phi0 = None
         self.phi = math.inf
 
@@ -200,7 +209,10 @@ class Controller:
         with np.errstate(all="ignore"):
             z = delta / xnorm if xnorm > 0 else math.inf
             # IEEE division: 0/0 is NaN (two zero corrections in a row), x/0 is Inf
-            v = float(np.float64(delta) / np.float64(self.delta_prev)) if math.isfinite(self.delta_prev) else 0.0
+            if self.p.ratio_scaled:
+                v = float(np.float64(dnorm) / np.float64(self.dhat_prev)) if math.isfinite(self.dhat_prev) else 0.0
+            else:
+                v = float(np.float64(delta) / np.float64(self.delta_prev)) if math.isfinite(self.delta_prev) else 0.0
         # rho_max = maxNum(rho_max, v): a NaN ratio leaves it unchanged
         self.rho_max = self.rho_max if math.isnan(v) else max(self.rho_max, v)
         phi = z / (1.0 - self.rho_max) if self.rho_max < 1.0 else math.inf
@@ -208,6 +220,7 @@ class Controller:
         if self.phi0 is None:
             self.phi0 = phi
         self.delta_prev = delta
+        self.dhat_prev = dnorm
         uu = u_of(self.u0)
         thr = self.gamma * uu
         if self.p.conv == CONV_EST:
@@ -228,6 +241,7 @@ class Controller:
         """Move to the next stage.  Returns True when that means raising u_f."""
         esc = self.alg == GMRES
         self.alg = {SIR: SGMRES, SGMRES: GMRES, GMRES: SIR}[self.alg]
+        self.dhat_prev = math.inf
         self.it = 0
         self.rho_max = 0.0
         self.delta_prev = math.inf
