@@ -96,6 +96,41 @@ def flbf16(x):
     return out
 
 
+def chop(x, fmt):
+    """One IEEE round-to-nearest-even rounding of float64 values to ``fmt``,
+    with no fp32 step in between: the rounding of the paper's simulated low
+    precisions (Sec. 3 simulates half precision by rounding every result of
+    a double-precision operation to half).  Gradual underflow; overflow to
+    +-Inf.  Returns float64.
+
+    fp16: numpy's float64 -> float16 conversion (one correct rounding).
+    bf16 (8 significant bits, exponent range of fp32): in the normal range
+    the float64 significand is rounded to 8 bits with integer arithmetic on
+    its bit pattern; below 2^-126 the value is rounded to a multiple of the
+    subnormal spacing 2^-133."""
+    x = np.asarray(x, dtype=np.float64)
+    with np.errstate(all="ignore"):
+        if fmt == FP64:
+            return x.copy()
+        if fmt == FP32:
+            return x.astype(np.float32).astype(np.float64)
+        if fmt == FP16:
+            return x.astype(np.float16).astype(np.float64)
+        if fmt == BF16:
+            bits = np.ascontiguousarray(x).view(np.uint64)
+            drop = np.uint64(52 - 7)
+            lsb = (bits >> drop) & np.uint64(1)
+            half = np.uint64((1 << 44) - 1)
+            mask = ~np.uint64((1 << 45) - 1)
+            r = ((bits + half + lsb) & mask).view(np.float64).reshape(x.shape)
+            r = np.where(np.isfinite(x), r, x)
+            tiny = np.abs(x) < 2.0 ** -126
+            r = np.where(tiny, np.round(x * 2.0 ** 133) * 2.0 ** -133, r)
+            r = np.where(np.abs(r) > XMAX[BF16], np.copysign(np.inf, x), r)
+            return r
+    raise ValueError(f"no single-word rounding for format {fmt}")
+
+
 def fl(x, fmt):
     """Round x (float32/float64 values) to format ``fmt``.
 

@@ -50,7 +50,7 @@ with row j at step j.
 
 import numpy as np
 
-from .formats import FP64, FP16, BF16, fl, arith_dtype
+from .formats import FP64, FP16, BF16, chop, fl, arith_dtype
 from .native import chain_update
 
 
@@ -181,6 +181,33 @@ def lu_factor(A, fmt_f, nb=None, nbo=None, trace=None, outer_tc=True):
             _swap_cols(F, ipiv, k, W, k + W, n)
             _trsm(F, k, W, k + W, n, T, fmt_f)
             _update(F, k, W, k + W, n, fmt_f, tensor_core=outer_tc and fmt_f in (FP16, BF16))
+    return F, ipiv, info
+
+
+def lu_factor_chop(A, fmt_f):
+    """GEPP with every operation rounded once to u_f (``formats.chop``), the
+    factorisation of the paper's experiments, which simulate a precision by
+    rounding each result (Sec. 3): unblocked and right-looking; in column k
+    the pivot is the first row of largest magnitude, l_ik = fl(a_ik / a_kk)
+    and a_ij = fl(a_ij - fl(l_ik a_kj)).  Same outputs as lu_factor."""
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    F = chop(A, fmt_f)
+    ipiv = np.arange(n, dtype=np.int64)
+    info = 0
+    with np.errstate(all="ignore"):
+        for k in range(n):
+            p = k + _argmax_abs(F[k:, k])
+            ipiv[k] = p
+            if p != k:
+                F[[k, p], :] = F[[p, k], :]
+            piv = F[k, k]
+            if piv == 0:
+                info = info or k + 1
+                continue
+            F[k + 1:, k] = chop(F[k + 1:, k] / piv, fmt_f)
+            prod = chop(np.outer(F[k + 1:, k], F[k, k + 1:]), fmt_f)
+            F[k + 1:, k + 1:] = chop(F[k + 1:, k + 1:] - prod, fmt_f)
     return F, ipiv, info
 
 

@@ -55,6 +55,12 @@ d the solves of the normalised residuals (z and phi keep R2).  With it the
 oracle reproduces the MSIR columns the paper prints for its randsvd
 experiments (Sec. 3.1, Tables 5-10), where a variant usually stops after two
 steps; those printed columns are its pins.
+
+Params.chop (off by default, test use only) replaces the LU and the u_f
+solves (x_0 and the SIR corrections) by the same algorithms with every
+operation rounded once to u_f (lu.lu_factor_chop, trsv.solve_factored_chop):
+Sec. 3 simulates half precision this way, so the printed half-precision
+columns are compared with it on.
 """
 
 import math
@@ -87,6 +93,7 @@ class Params:
     allow_escalation: bool = True
     outer_tc: bool = True     # bf16 / fp16 outer update on tensor cores (lu.lu_factor)
     ratio_scaled: bool = False  # ratio test on the scaled corrections (module docstring)
+    chop: bool = False        # LU and u_f solves with every operation rounded to u_f (module docstring)
 
 
 @dataclass
@@ -99,6 +106,7 @@ class Factorization:
     R: np.ndarray = None
     S: np.ndarray = None
     mu: float = 1.0
+    chop: bool = False        # factored by lu.lu_factor_chop; u_f solves by trsv.solve_factored_chop
     # inverses of the diagonal blocks of L and U (oracle.trsv), filled on
     # first use and kept while these factors are in use
     inv_cache: dict = field(default_factory=dict, repr=False, compare=False)
@@ -131,25 +139,32 @@ class Result:
     history: list
 
 
-def factorize(A_u, fmt_f, nb=0, nbo=0, outer_tc=True):
+def factorize(A_u, fmt_f, nb=0, nbo=0, outer_tc=True, chop=False):
     """LU in u_f with the factor check and one squeezed retry (R10).
+    chop=True: the every-operation-rounded LU (lu.lu_factor_chop).
 
     Returns (Factorization or None, scaled_flag)."""
-    F, ipiv, info = lu_mod.lu_factor(A_u, fmt_f, nb or None, nbo or None, outer_tc=outer_tc)
+    def lu(M):
+        if chop:
+            return lu_mod.lu_factor_chop(M, fmt_f)
+        return lu_mod.lu_factor(M, fmt_f, nb or None, nbo or None, outer_tc=outer_tc)
+    F, ipiv, info = lu(A_u)
     if lu_mod.factors_finite(F) and info == 0:
-        return Factorization(fmt_f, F, ipiv, lu_mod.ipiv_to_perm(ipiv), info), False
+        return Factorization(fmt_f, F, ipiv, lu_mod.ipiv_to_perm(ipiv), info, chop=chop), False
     if fmt_f == FP64:
         return None, False
     R, S, mu = sq_mod.scalings(A_u, fmt_f)
     B = sq_mod.scaled_matrix(A_u, R, S, mu)
-    F, ipiv, info = lu_mod.lu_factor(B.astype(np.float32), fmt_f, nb or None, nbo or None, outer_tc=outer_tc)
+    F, ipiv, info = lu(B if chop else B.astype(np.float32))
     if lu_mod.factors_finite(F) and info == 0:
-        return Factorization(fmt_f, F, ipiv, lu_mod.ipiv_to_perm(ipiv), info, R, S, mu), True
+        return Factorization(fmt_f, F, ipiv, lu_mod.ipiv_to_perm(ipiv), info, R, S, mu, chop=chop), True
     return None, True
 
 
 def uf_solve(fac, c):
     """M_f^{-1} c with the u_f substitution model (SIR correction, x_0)."""
+    if fac.chop:
+        return trsv_mod.solve_factored_chop(fac, c)
     arith = FP64 if fac.fmt_f == FP64 else FP32
     return trsv_mod.solve_factored(fac, c, arith, fac.fmt_f)
 
@@ -288,7 +303,7 @@ def msir(A_in, b_in, triple, params=None, x_ref=None, factor_hook=None):
             if hooked is not None:
                 scaled_flags.append(False)
                 return hooked
-            fac, sc = factorize(A_u.astype(arith_dtype(u0)), fmt, p.nb, p.nbo, p.outer_tc)
+            fac, sc = factorize(A_u.astype(arith_dtype(u0)), fmt, p.nb, p.nbo, p.outer_tc, p.chop)
             scaled_flags.append(sc)
             if fac is not None:
                 return fac

@@ -36,7 +36,7 @@ block holds the remaining n - 64 floor((n-1)/64) rows.
 
 import numpy as np
 
-from .formats import (FP32, FP64, DD, fl, dd, dd_sub, dd_mul, dd_mul_d, dd_div_d,
+from .formats import (FP32, FP64, DD, chop, fl, dd, dd_sub, dd_mul, dd_mul_d, dd_div_d,
                       dd_sum_pairwise, dd_to_fp32)
 
 BLK = 64
@@ -225,6 +225,34 @@ def solve_factored(fac, c, arith, store):
     cc = _round(cc, store)
     y = lower_unit(fac.F, cc[perm], arith, store, cache)
     x = upper(fac.F, y, arith, store, cache)
+    if fac.S is not None:
+        x = x * fac.S
+    return x
+
+
+def solve_factored_chop(fac, c):
+    """x = S U^{-1} L^{-1} P (mu R c) with every operation rounded once to
+    u_f (``formats.chop``), the substitution of the paper's experiments
+    (Sec. 3's simulation by rounding each result): column-oriented, forward
+    y_i = fl(y_i - fl(l_ij y_j)) for j ascending, backward
+    x_j = fl(x_j / u_jj) then x_i = fl(x_i - fl(u_ij x_j)) for j descending.
+    ``fac`` holds the factors of ``lu.lu_factor_chop``.  Returns float64."""
+    fmt = fac.fmt_f
+    F = fac.F
+    n = F.shape[0]
+    scale = fac.R * fac.mu if fac.R is not None else None
+    cc = np.asarray(c, dtype=np.float64)
+    if scale is not None:
+        cc = cc * scale
+    x = chop(cc[fac.perm], fmt)
+    with np.errstate(all="ignore"):
+        for j in range(n):
+            if j + 1 < n:
+                x[j + 1:] = chop(x[j + 1:] - chop(F[j + 1:, j] * x[j], fmt), fmt)
+        for j in range(n - 1, -1, -1):
+            x[j] = chop(x[j] / F[j, j], fmt)
+            if j:
+                x[:j] = chop(x[:j] - chop(F[:j, j] * x[j], fmt), fmt)
     if fac.S is not None:
         x = x * fac.S
     return x

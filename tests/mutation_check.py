@@ -25,7 +25,7 @@ import time
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PIN_TESTS = ["tests/test_oracle_formats.py", "tests/test_oracle_lu.py", "tests/test_oracle_chain.py",
              "tests/test_oracle_solves.py", "tests/test_oracle_msir.py", "tests/test_oracle_helpers.py",
-             "tests/test_arith_identities.py"]
+             "tests/test_arith_identities.py", "tests/test_oracle_chop.py", "tests/test_oracle_paper_tables.py"]
 
 # (file, text, replacement): each text occurs exactly once in its file
 MISTAKES = [
@@ -75,6 +75,16 @@ MISTAKES = [
      "away = tie & (lo != 0) & (np.sign(lo) != np.sign(d))"),
     ("oracle/formats.py", "return {BF16: FP32, FP16: FP32, FP32: FP64, FP64: None}[fmt]",
      "return {BF16: FP16, FP16: FP32, FP32: FP64, FP64: None}[fmt]"),
+    # every-operation-rounded mode (Sec. 3's simulation)
+    ("oracle/formats.py", "half = np.uint64((1 << 44) - 1)", "half = np.uint64(1 << 44)"),
+    ("oracle/formats.py", "r = np.where(tiny, np.round(x * 2.0 ** 133) * 2.0 ** -133, r)", "r = r"),
+    ("oracle/lu.py", "            prod = chop(np.outer(F[k + 1:, k], F[k, k + 1:]), fmt_f)",
+     "            prod = np.outer(F[k + 1:, k], F[k, k + 1:])"),
+    ("oracle/lu.py", "            F[k + 1:, k] = chop(F[k + 1:, k] / piv, fmt_f)", "            F[k + 1:, k] = F[k + 1:, k] / piv"),
+    ("oracle/trsv.py", "                x[:j] = chop(x[:j] - chop(F[:j, j] * x[j], fmt), fmt)",
+     "                x[:j] = chop(x[:j] - F[:j, j] * x[j], fmt)"),
+    ("oracle/trsv.py", "    x = chop(cc[fac.perm], fmt)", "    x = chop(cc, fmt)"),
+    ("oracle/msir.py", "    if fac.chop:\n        return trsv_mod.solve_factored_chop(fac, c)\n", ""),
     # GMRES (Algorithms 2-3)
     ("oracle/gmres.py", "    s = _rnd(g / r, fmt_u)", "    s = _rnd(-g / r, fmt_u)"),
     ("oracle/gmres.py", "            h2 = _ru(Vk.T @ w, fmt_u)\n            w = _ru(w - Vk @ h2, fmt_u)\n"
@@ -100,7 +110,8 @@ MISTAKES = [
     ("oracle/trsv.py", "            if not lower:\n                acc = dd_div_d(acc, B[i, i])\n", ""),
     ("oracle/trsv.py", "            s = M[b] @ x[r1:] if r1 < n else 0.0", "            s = M[b] @ x[r1:] if r1 < n - 1 else 0.0"),
     ("oracle/trsv.py", "    cc = _round(cc, store)\n", ""),
-    ("oracle/trsv.py", "        x = x * fac.S\n    return x", "        x = x\n    return x"),
+    ("oracle/trsv.py", "    x = upper(fac.F, y, arith, store, cache)\n    if fac.S is not None:\n        x = x * fac.S\n",
+     "    x = upper(fac.F, y, arith, store, cache)\n"),
     ("oracle/trsv.py", "            yh[r0:r1], yl[r0:r1] = dd_sub(w, s)", "            yh[r0:r1], yl[r0:r1] = dd_sub(w, (s[0], 0 * s[1]))"),
 ]
 
